@@ -1,0 +1,149 @@
+/*
+ * FP64 reference implementation ("oracle") of Event-based Single Integration.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline leg of bench.py may load this file's library.  The CUDA
+ * product path shares no code, header, table or constant with it.
+ *
+ * What it computes, in the paper's order and notation:
+ *   - Alg. 2 (Sec. III-C): for every event e_i = (x_i, y_i, p_i, t_i), in the
+ *     order it was pushed:  S += p_i C;  dt = t_i - T;  S *= d(dt);  T = t_i;
+ *     S = min(max(S, S_min), S_max)   (the clamp of Eq. 13, applied per event
+ *     as Alg. 2 places it inside the loop).
+ *   - Eq. 4 (Sec. III-B): d(t) = max{(1 - k t)^b, 0}.  Read as
+ *     max(1 - k t, 0)^b, so that d = 0 once k t >= 1 and d(0) = 1 (the
+ *     printed form is undefined or amplifying for 1 - k t < 0 with
+ *     non-integer or even b).
+ *   - Eq. 14 (Sec. III-C): B = 255 (S - S_min) / (S_max - S_min), rounded
+ *     half to even and saturated to [0, 255] (the paper does not say how it
+ *     rounds).  With render_decay = 1 the value mapped is the decay view
+ *     S * d(t_frame - T), which is not written back; with render_decay = 0 it
+ *     is S as stored, as Alg. 2 renders it.
+ *
+ * Other readings: polarity p > 0 counts +1, anything else -1 (Sec. III-A gives
+ * p in {+1, -1}); events with x >= W or y >= H are dropped and counted, never
+ * applied; time is int64 microseconds and k is given per second, so the
+ * product k t uses k * 1e-6 per microsecond.  Events at one pixel must arrive
+ * in non-decreasing time (the caller checks this).
+ *
+ * Precision: every state value and every intermediate is IEEE double.  Build
+ * with -ffp-contract=off so that no multiply-add is fused.
+ */
+#include <math.h>
+#include <stdint.h>
+
+/* Event record as laid out in memory: 16 bytes. */
+typedef struct {
+    int64_t t;   /* microseconds */
+    uint16_t x;
+    uint16_t y;
+    int8_t p;    /* polarity */
+    uint8_t pad[3];
+} oracle_event;
+
+/* Eq. 4 with the reading max(1 - k dt, 0)^b; dt in microseconds, k in 1/s. */
+double oracle_decay(int64_t dt_us, double k_per_s, double b)
+{
+    double u = 1.0 - (k_per_s * 1e-6) * (double)dt_us;
+    if (u > 0.0)
+        return pow(u, b);
+    return 0.0;
+}
+
+/* One pass of the Alg. 2 loop body for one accepted event at pixel index pix. */
+static void oracle_step(double *S, int64_t *T, int64_t pix, int8_t p, int64_t t,
+                        double C, double k_per_s, double b, double s_min,
+                        double s_max)
+{
+    double pol = (p > 0) ? 1.0 : -1.0;
+    double s = S[pix];
+    s = s + pol * C;                              /* S <- S + p C          */
+    int64_t dt = t - T[pix];                      /* dt <- t - T           */
+    s = s * oracle_decay(dt, k_per_s, b);         /* S <- S max{(1-k dt)^b,0} */
+    T[pix] = t;                                   /* T <- t                */
+    if (s < s_min) s = s_min;                     /* S <- min(max(S,Smin),Smax) */
+    if (s > s_max) s = s_max;
+    S[pix] = s;
+}
+
+/*
+ * Initialise the accumulation matrix S to 0 and the last-decay-time matrix T
+ * to t_origin (Alg. 2 initialises both to zero; t_origin = 0 is the paper's
+ * choice).
+ */
+void oracle_init(double *S, int64_t *T, int64_t P, int64_t t_origin)
+{
+    for (int64_t i = 0; i < P; ++i) {
+        S[i] = 0.0;
+        T[i] = t_origin;
+    }
+}
+
+/*
+ * Alg. 2 event loop over n events in push order.  S and T (row-major, pixel
+ * y*W + x) are updated in place.  Returns the number of events applied;
+ * *dropped is increased by the number of out-of-range events.
+ */
+int64_t oracle_integrate(const oracle_event *ev, int64_t n, int W, int H,
+                         double C, double k_per_s, double b, double s_min,
+                         double s_max, double *S, int64_t *T, int64_t *dropped)
+{
+    int64_t applied = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const oracle_event *e = &ev[i];
+        if ((int)e->x >= W || (int)e->y >= H) {
+            *dropped += 1;
+            continue;
+        }
+        int64_t pix = (int64_t)e->y * W + e->x;
+        oracle_step(S, T, pix, e->p, e->t, C, k_per_s, b, s_min, s_max);
+        applied += 1;
+    }
+    return applied;
+}
+
+/* Eq. 14 for every pixel; render_decay selects the decay view (see header). */
+void oracle_render(const double *S, const int64_t *T, int64_t P, double k_per_s,
+                   double b, double s_min, double s_max, int render_decay,
+                   int64_t t_frame, uint8_t *B)
+{
+    for (int64_t i = 0; i < P; ++i) {
+        double v = S[i];
+        if (render_decay)
+            v = v * oracle_decay(t_frame - T[i], k_per_s, b);
+        double q = 255.0 * (v - s_min) / (s_max - s_min);
+        double r = rint(q);
+        if (r < 0.0) r = 0.0;
+        if (r > 255.0) r = 255.0;
+        B[i] = (uint8_t)r;
+    }
+}
+
+/*
+ * A sequence of M frames at non-decreasing times t_frames[w]: before frame w,
+ * every not yet applied event with t <= t_frames[w] is applied in push order
+ * (a frame at t shows the events with t_n <= t, the condition stated under
+ * Eq. 5); then frame w is rendered into B + w * W * H.  Events after the last
+ * frame time stay unapplied.  Returns the number of events consumed (applied
+ * or dropped).
+ */
+int64_t oracle_replay(const oracle_event *ev, int64_t n, int W, int H,
+                      double C, double k_per_s, double b, double s_min,
+                      double s_max, int render_decay, const int64_t *t_frames,
+                      int64_t M, double *S, int64_t *T, uint8_t *B,
+                      int64_t *dropped)
+{
+    int64_t P = (int64_t)W * H;
+    int64_t i = 0;
+    for (int64_t w = 0; w < M; ++w) {
+        int64_t j = i;
+        while (j < n && ev[j].t <= t_frames[w])
+            ++j;
+        oracle_integrate(ev + i, j - i, W, H, C, k_per_s, b, s_min, s_max, S,
+                         T, dropped);
+        i = j;
+        oracle_render(S, T, P, k_per_s, b, s_min, s_max, render_decay,
+                      t_frames[w], B + w * P);
+    }
+    return i;
+}

@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Throughput of the ESI hot path on one GB300 (events/s and frames/s).
+
+Workload (one step): the 640x480, 2 s synthetic stream of configuration 1
+(40 Gaussian blobs, per-pixel C ~ N(0.15, 0.03), ~10 M events, int64 us),
+rendered as 200 frames of 10 ms with the decay view (render_decay = 1),
+C = 0.15, k = 10 /s, b = 2, clamp [-1, 1].  Step k replays the stream shifted
+by k * 2 s, so the state carries on as one continuous stream.
+
+value: events/s with every step's events already resident in device memory
+(pushed before the timed region), frames written to device memory; inputs
+per step (160 MB) exceed the 129 MB L2.  e2e: the same metric through the C
+ABI with pinned host buffers (events pushed from host, frames read back to
+host) inside the timed region.  With --gpus N (torchrun) every rank runs its
+own replica on its own GPU (no collective on the data path; weak scaling).
+
+--impl reference times the FP64 CPU oracle (the test reference) on the host
+cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "events/s and frames/s at 1 GB300 (% HBM roofline); p50/p99 frame latency, batched vs plain"
+WINDOW_US = 10_000
+DURATION_US = 2_000_000
+PARAMS = dict(C=0.15, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, t_origin_us=0,
+              render_decay=1)
+WORKLOAD = "config1: 640x480, 2 s, ~10M events (40 Gaussian blobs), 200 x 10 ms frames, decay view"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["esi", "reference"], default="esi")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the e2e, latency and CPU-baseline legs")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_stream():
+    import synth
+    sc = synth.config1()
+    return sc, synth.generate(sc)
+
+
+def shifted(ev, k):
+    e = ev.copy()
+    e["t"] += k * DURATION_US
+    return e
+
+
+def frame_times(k, n_windows):
+    return np.arange(1, n_windows + 1, dtype=np.int64) * WINDOW_US + k * DURATION_US
+
+
+def cpu_baseline(sc, ev, budget_s: float = 10.0):
+    """The oracle as it stands on one host core: whole-stream replays until budget_s."""
+    import oracle
+    reps, used, t0 = 0, 0, time.perf_counter()
+    n_windows = DURATION_US // WINDOW_US
+    while True:
+        st = oracle.OracleState(sc.W, sc.H, oracle.OracleParams(**PARAMS))
+        _, u = st.replay(ev, frame_times(0, n_windows))
+        used += u
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s or reps >= 8:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": used / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} replay(s) of the whole 2 s stream ({len(ev)} events, "
+                      f"{n_windows} frames each), {dt:.1f} s"}
+
+
+def bench_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    sc, ev = make_stream()
+    # each step: the first 0.4 s of the stream (40 frames) from a fresh state
+    n_w = 40
+    sample = ev[ev["t"] <= n_w * WINDOW_US]
+    tf = frame_times(0, n_w)
+
+    def step():
+        st = oracle.OracleState(sc.W, sc.H, oracle.OracleParams(**PARAMS))
+        st.replay(sample, tf)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = len(sample) * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "first 0.4 s (40 frames) per step"},
+        "frames_per_s": n_w * args.steps / dt,
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first 0.4 s of the stream ({len(sample)} events, "
+                                   f"{n_w} frames) per step"},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def bench_esi(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2508_02238_gb300 import esi
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    esi.load_library(build_if_missing=True)
+
+    sc, ev = make_stream()
+    n_ev = len(ev)
+    n_windows = DURATION_US // WINDOW_US
+    P = sc.W * sc.H
+    stream = torch.cuda.Stream()
+    rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**PARAMS), stream.cuda_stream)
+    esi.check(rc, "esi_create")
+    out = torch.empty((n_windows, sc.H, sc.W), dtype=torch.uint8, device="cuda")
+
+    # device-resident inputs: every step's events pushed before timing
+    total_steps = args.warmup + args.steps
+    for k in range(total_steps):
+        esi.check(esi.esi_push_events(h, shifted(ev, k), n_ev, 0), "push")
+    tfs = [frame_times(k, n_windows) for k in range(total_steps)]
+
+    def step(k):
+        esi.check(esi.esi_render_frames(h, tfs[k], n_windows, out, 1), "render")
+
+    for k in range(args.warmup):
+        step(k)
+    esi.check(esi.esi_synchronize(h), "sync")
+    rc, st0 = esi.esi_get_stats(h)
+    esi.check(esi.esi_profile_reset(h))
+    esi.check(esi.esi_profile_enable(h, 1))
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.warmup, total_steps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    esi.check(esi.esi_profile_enable(h, 0))
+    rc, prof = esi.esi_profile_read(h)
+    rc, st1 = esi.esi_get_stats(h)
+    launches = int(st1.kernel_launches - st0.kernel_launches)
+
+    events_done = n_ev * args.steps * ws
+    value = events_done / (ms / 1e3)
+    frames_per_s = n_windows * args.steps * ws / (ms / 1e3)
+
+    # roofline of the dominant kernel (algorithmic bytes / measured duration)
+    peak, peak_kind = load_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    step_bytes = 16 * n_ev + 24 * P + n_windows * P
+    if dom:
+        name, (nl, tot_ms) = dom
+        if name == "esi_bin":
+            bytes_per_launch = 16.0 * n_ev * args.steps / nl
+        else:
+            bytes_per_launch = (24.0 * P * nl + n_windows * P * args.steps) / nl
+        achieved = bytes_per_launch / (tot_ms / nl / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                "peak_kind": f"of {peak_kind}", "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "launches": nl, "avg_launch_us": tot_ms / nl * 1e3,
+                "bytes_per_launch": bytes_per_launch}
+    kernels = {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / max(1e-9, sum(x[1] for x in prof.values()))}
+               for k, v in prof.items()}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded generator, config-1 scene), state FP32, times int64 us",
+        "config": {"workload": WORKLOAD, "events_per_step": n_ev, "frames_per_step": n_windows,
+                   "sensor": f"{sc.W}x{sc.H}", "params": PARAMS,
+                   "l2": "inputs larger than L2 (160 MB of events per step)",
+                   "parallelism": f"replicas x{ws}"},
+        "frames_per_s": frames_per_s,
+        "roofline": roof,
+        "step_roofline": {"bytes_per_step": step_bytes,
+                          "achieved_gbs": step_bytes / (ms / args.steps / 1e3) / 1e9,
+                          "frac": step_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
+                          "note": "16 B/event + S,T read and written once + 1 B/pixel/frame"},
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+    if not args.no_extras and rank == 0:
+        line["e2e"] = e2e_leg(esi, torch, h, stream, sc, ev, out, total_steps, args.steps, n_windows)
+        line["latency"] = latency_leg(esi, torch, sc, ev)
+    elif not args.no_extras:
+        line["e2e"] = None
+    esi.esi_destroy(h)
+    if rank == 0 and not args.no_extras:
+        line["cpu_baseline"] = cpu_baseline(sc, ev)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def e2e_leg(esi, torch, h, stream, sc, ev, out, k0, steps, n_windows):
+    """Steps through the public API with pinned host input and output."""
+    n_ev = len(ev)
+    host_in = []
+    for i in range(steps + 1):
+        buf = torch.empty(n_ev * 16, dtype=torch.uint8, pin_memory=True)
+        buf.numpy().view(ev.dtype)[:] = shifted(ev, k0 + i)
+        host_in.append(buf)
+    host_out = torch.empty((n_windows, sc.H, sc.W), dtype=torch.uint8, pin_memory=True)
+
+    def step(i):
+        esi.check(esi.esi_push_events(h, host_in[i], n_ev, 0), "push")
+        esi.check(esi.esi_render_frames(h, frame_times(k0 + i, n_windows), n_windows,
+                                        host_out, 0), "render")
+
+    step(0)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(1, steps + 1):
+        step(i)
+    dt = time.perf_counter() - t0
+    return {"value": n_ev * steps / dt, "unit": "events/s",
+            "h2d_bytes_per_step": n_ev * 16, "d2h_bytes_per_step": n_windows * sc.W * sc.H,
+            "frames_per_s": n_windows * steps / dt}
+
+
+def latency_leg(esi, torch, sc, ev):
+    """Plain single-stream path: one 10 ms packet pushed, one frame rendered to host."""
+    rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**PARAMS), 0)
+    esi.check(rc)
+    out = np.empty((sc.H, sc.W), dtype=np.uint8)
+    n_windows = DURATION_US // WINDOW_US
+    cuts = np.searchsorted(ev["t"], np.arange(0, n_windows + 1) * WINDOW_US, side="right")
+    lat = []
+    for w in range(n_windows):
+        pkt = np.ascontiguousarray(ev[cuts[w]:cuts[w + 1]])
+        t0 = time.perf_counter()
+        esi.check(esi.esi_push_events(h, pkt, len(pkt), 0))
+        esi.check(esi.esi_render_frame(h, (w + 1) * WINDOW_US, out, 0))
+        lat.append((time.perf_counter() - t0) * 1e3)
+    esi.esi_destroy(h)
+    lat = np.array(lat[5:])
+    return {"path": "plain: push 10 ms packet (host) + render one frame (host out)",
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "frames": int(len(lat))}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_esi(args)
+
+
+if __name__ == "__main__":
+    main()

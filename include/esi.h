@@ -1,0 +1,200 @@
+/*
+ * esi.h -- C ABI of the GB300 (sm_103a) implementation of Event-based Single
+ * Integration (ESI), arXiv 2508.02238.
+ *
+ * The method (Sec. III): an event camera emits events e = {x, y, t, p}
+ * (Sec. III-A).  Every event updates its pixel's accumulation S and
+ * last-decay time T (Alg. 2): S += p C; dt = t - T; S *= d(dt); T = t;
+ * S = min(max(S, S_min), S_max), with the decay d(t) = max{(1 - k t)^b, 0}
+ * of Eq. 4 (read as max(1 - k t, 0)^b) and the clamp of Eq. 13.  A frame maps
+ * S linearly to 8 bits (Eq. 14).  S and T are the whole state (Sec. III-B).
+ *
+ * Conventions for every call:
+ *   - Return 0 (ESI_OK) or a negative ESI_E* code; esi_strerror() names it.
+ *   - Pointers are plain host or device pointers as the *_on_device flag
+ *     says; the caller owns every buffer it passes.  No call keeps a pointer
+ *     the caller passed after it returns.
+ *   - Time is int64 microseconds.  k is given per second.
+ *   - A handle (and a server) is not thread-safe: drive it from one thread.
+ *   - Device work runs on the CUDA stream given at creation (NULL = a stream
+ *     the library creates).  Calls that write host memory wait for their
+ *     own work; calls that only write device memory return once the work is
+ *     queued, and errors found by the device are reported by the next call
+ *     that waits (esi_synchronize, esi_get_state, a host-output render).
+ */
+#ifndef ESI_H
+#define ESI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- errors */
+#define ESI_OK 0
+#define ESI_EINVAL (-1)      /* bad argument: params, sizes, pointers, ids    */
+#define ESI_ENOMEM (-2)      /* device or host allocation failed             */
+#define ESI_EBUSY (-3)       /* admission refused: state budget exhausted    */
+#define ESI_ETIMEORDER (-4)  /* event or frame time goes backwards           */
+#define ESI_ERANGE (-5)      /* a value is outside what the layout can hold  */
+#define ESI_ECUDA (-6)       /* a CUDA runtime call failed                   */
+#define ESI_ETIMEOUT (-7)    /* a bounded device-side wait gave up           */
+#define ESI_ESTATE (-8)      /* call not valid in the current state          */
+
+/* ----------------------------------------------------------------- types */
+
+/*
+ * One event (Sec. III-A): pixel (x, y), time t_us, polarity p.  p > 0 counts
+ * as +1 and anything else as -1 (the paper's p in {+1, -1}; DAVIS 0/1 also
+ * works).  16 bytes, little endian, no padding between fields.
+ */
+typedef struct {
+    int64_t t_us;
+    uint16_t x;
+    uint16_t y;
+    int8_t p;
+    uint8_t _pad[3];
+} esi_event;
+
+/*
+ * Method parameters.  C: contrast step per event (Alg. 2), > 0.  k_per_s,
+ * b: decay of Eq. 4, k >= 0 (k = 0 gives the plain integration of Eq. 2),
+ * b > 0.  s_min < s_max: clamp bounds of Eq. 13, also the ends of the
+ * linear map of Eq. 14; both finite.  t_origin_us: initial T of every pixel
+ * (Alg. 2 uses 0).  render_decay: 0 maps S as stored (Alg. 2); 1 maps the
+ * decay view S d(t_frame - T), which is not written back.
+ */
+typedef struct {
+    double C;
+    double k_per_s;
+    double b;
+    double s_min;
+    double s_max;
+    int64_t t_origin_us;
+    int32_t render_decay;
+    int32_t _reserved;
+} esi_params;
+
+/* Counters of one handle (or one server stream). */
+typedef struct {
+    uint64_t events_pushed;    /* accepted by esi_push_events               */
+    uint64_t events_consumed;  /* taken by renders (applied or dropped)     */
+    uint64_t events_dropped;   /* x >= W or y >= H: never applied           */
+    uint64_t events_pending;   /* pushed, t later than every rendered frame */
+    uint64_t frames_rendered;
+    uint64_t kernel_launches;  /* device kernels this handle has launched   */
+    int64_t last_event_t_us;
+    int64_t last_frame_t_us;
+} esi_stats;
+
+/*
+ * Launch-shape knobs (all 0 = library default).  tile_h: rows per pixel
+ * tile (8, 16 or 32; tiles are 32 pixels wide).  chunk_events: events per
+ * binning block (power of two, 512..8192).  batch_records: records a tile
+ * sorts in shared memory at once (power of two, 1024..8192).
+ * max_batch_events: events per binning pass of a render (>= chunk_events).
+ */
+typedef struct {
+    int32_t tile_h;
+    int32_t chunk_events;
+    int32_t batch_records;
+    int32_t max_batch_events;
+} esi_tuning;
+
+/* Per-kernel device time collected while profiling is on. */
+typedef struct {
+    char name[32];
+    uint64_t launches;
+    double total_ms;
+} esi_kernel_time;
+
+typedef struct esi_handle esi_handle;
+
+/* ------------------------------------------------------- one sensor path */
+
+/*
+ * Create the state of one width x height sensor (Alg. 2 initialisation:
+ * S = 0, T = t_origin for every pixel) on the current CUDA device.
+ * width, height in [1, 65535].  cuda_stream: a cudaStream_t or NULL.
+ * Errors: ESI_EINVAL for bad sizes or parameters (checked before any CUDA
+ * call), ESI_ENOMEM, ESI_ECUDA.
+ */
+int esi_create(int width, int height, const esi_params *params,
+               void *cuda_stream, esi_handle **out);
+
+/*
+ * Queue n events (Sec. III-A) for the next renders.  Times must be
+ * non-decreasing within the batch and not earlier than the last event
+ * pushed before, nor than t_origin or the last frame time; otherwise the
+ * whole batch is rejected with ESI_ETIMEORDER and nothing is queued.
+ * Events with x >= W or y >= H are accepted but dropped (counted, never
+ * applied).  ev_on_device = 0: host buffer, copied before the call
+ * returns.  ev_on_device = 1: device buffer, copied on the handle's stream;
+ * the call waits for that copy.  n = 0 is a no-op.
+ */
+int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_device);
+
+/*
+ * Apply every queued event with t <= t_frame_us in push order (Alg. 2
+ * loop; a frame at t shows the events t_n <= t, the condition under Eq. 5)
+ * and write the Eq. 14 frame, W * H bytes row-major (y * W + x), to out.
+ * Later events stay queued.  t_frame_us must not be earlier than the
+ * previous frame or t_origin (ESI_ETIMEORDER).  out_on_device selects a
+ * device or host buffer; with a host buffer the call waits for the frame.
+ */
+int esi_render_frame(esi_handle *h, int64_t t_frame_us, uint8_t *out, int out_on_device);
+
+/*
+ * m frames at non-decreasing times t_frames[0..m-1] (a host array): frame w
+ * shows every queued event with t <= t_frames[w], exactly as m calls of
+ * esi_render_frame would, in one pass over the events.  out holds m * W * H
+ * bytes, frame w at offset w * W * H.
+ */
+int esi_render_frames(esi_handle *h, const int64_t *t_frames, size_t m,
+                      uint8_t *out, int out_on_device);
+
+/*
+ * Checkpoint: copy S (float32, W * H) and T (int64 us, W * H) out.  Waits
+ * for queued work and reports device-side errors.  Queued events are not
+ * part of S, T (they stay queued).
+ */
+int esi_get_state(esi_handle *h, float *S, int64_t *T, int on_device);
+
+/*
+ * Resume: replace S and T.  Every T must be <= the earliest queued event and
+ * later pushes must not be earlier than max(T) (ESI_ETIMEORDER otherwise).
+ */
+int esi_set_state(esi_handle *h, const float *S, const int64_t *T, int on_device);
+
+/* Wait for the handle's queued device work; returns a device-side error. */
+int esi_synchronize(esi_handle *h);
+
+/* Counters; waits for queued work so that the drop count is exact. */
+int esi_get_stats(esi_handle *h, esi_stats *out);
+
+/* Launch-shape knobs; ESI_EINVAL for values outside the documented sets. */
+int esi_set_tuning(esi_handle *h, const esi_tuning *t);
+int esi_get_tuning(esi_handle *h, esi_tuning *out);
+
+/*
+ * Device-time profiling of the handle's kernels (CUDA events around each
+ * launch on the handle's stream).  esi_profile_read waits, writes up to
+ * max entries and returns how many kernels it knows (>= 0).
+ */
+int esi_profile_enable(esi_handle *h, int enable);
+int esi_profile_read(esi_handle *h, esi_kernel_time *out, int max);
+int esi_profile_reset(esi_handle *h);
+
+/* Free everything the handle owns.  NULL is a no-op. */
+void esi_destroy(esi_handle *h);
+
+/* Static text for an ESI_* code. */
+const char *esi_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ESI_H */

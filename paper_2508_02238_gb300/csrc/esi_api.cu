@@ -1,0 +1,693 @@
+// Host side of the ESI C ABI (esi.h): handle life cycle, the pending-event
+// ring, render planning (sub-batches, frame ranges) and the kernel launches.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "esi_api_impl.h"
+
+using namespace esi;
+
+namespace esi {
+
+int cuda_fail(esi_handle *h, cudaError_t e)
+{
+    if (e == cudaSuccess) return ESI_OK;
+    if (h) h->cuda_msg = cudaGetErrorString(e);
+    return (e == cudaErrorMemoryAllocation) ? ESI_ENOMEM : ESI_ECUDA;
+}
+
+long long decay_cutoff(double k_per_s)
+{
+    if (!(k_per_s > 0.0)) return LLONG_MAX;
+    const double kus = k_per_s * 1e-6;
+    const double x = 1.0 / kus;
+    if (!(x < 9.0e18)) return LLONG_MAX;
+    long long c = (long long)std::floor(x) - 2;
+    if (c < 0) c = 0;
+    // smallest dt with 1 - kus * dt <= 0, evaluated in double as Eq. 4 is
+    while (!(1.0 - kus * (double)c <= 0.0)) ++c;
+    while (c > 0 && 1.0 - kus * (double)(c - 1) <= 0.0) --c;
+    return c;
+}
+
+int validate_params(int W, int H, const esi_params *p)
+{
+    if (!p) return ESI_EINVAL;
+    if (W < 1 || H < 1 || W > 65535 || H > 65535) return ESI_EINVAL;
+    if (!std::isfinite(p->C) || !(p->C > 0.0)) return ESI_EINVAL;
+    if (!std::isfinite(p->k_per_s) || p->k_per_s < 0.0) return ESI_EINVAL;
+    if (!std::isfinite(p->b) || !(p->b > 0.0)) return ESI_EINVAL;
+    if (!std::isfinite(p->s_min) || !std::isfinite(p->s_max)) return ESI_EINVAL;
+    if (!((float)p->s_min < (float)p->s_max)) return ESI_EINVAL;
+    if (!std::isfinite(p->s_max - p->s_min)) return ESI_EINVAL;
+    if (p->render_decay != 0 && p->render_decay != 1) return ESI_EINVAL;
+    return ESI_OK;
+}
+
+void prepare_params(const esi_params &p, DecayParams *dp, MapParams *mp)
+{
+    const double kus = p.k_per_s * 1e-6;
+    dp->k_hi = (float)kus;
+    dp->k_lo = (float)(kus - (double)dp->k_hi);
+    dp->b = (float)p.b;
+    dp->cutoff = decay_cutoff(p.k_per_s);
+    if (p.k_per_s == 0.0) dp->b_mode = 4;
+    else if (p.b == 1.0) dp->b_mode = 1;
+    else if (p.b == 2.0) dp->b_mode = 2;
+    else if (p.b == 3.0) dp->b_mode = 3;
+    else dp->b_mode = 0;
+    mp->C = (float)p.C;
+    mp->s_min = (float)p.s_min;
+    mp->s_max = (float)p.s_max;
+    const double sc = 255.0 / (p.s_max - p.s_min);
+    mp->scale = (float)sc;
+    mp->offs = (float)(-p.s_min * sc);
+    mp->render_decay = p.render_decay;
+}
+
+int validate_tuning(const esi_tuning &t)
+{
+    auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+    if (t.tile_h != 8 && t.tile_h != 16 && t.tile_h != 32) return ESI_EINVAL;
+    if (!pow2(t.chunk_events) || t.chunk_events < 512 || t.chunk_events > 8192) return ESI_EINVAL;
+    if (!pow2(t.batch_records) || t.batch_records < 1024 || t.batch_records > 8192) return ESI_EINVAL;
+    if (t.max_batch_events < t.chunk_events) return ESI_EINVAL;
+    return ESI_OK;
+}
+
+esi_tuning default_tuning(int W, int H)
+{
+    (void)W;
+    (void)H;
+    esi_tuning t;
+    t.tile_h = 32;
+    t.chunk_events = 2048;
+    t.batch_records = 4096;
+    t.max_batch_events = 1 << 21;
+    return t;
+}
+
+}  // namespace esi
+
+// ------------------------------------------------------------ handle helpers
+static int apply_tuning(esi_handle *h, const esi_tuning &t)
+{
+    h->tun = t;
+    h->tiles_x = (h->W + kTileW - 1) / kTileW;
+    h->tiles_y = (h->H + t.tile_h - 1) / t.tile_h;
+    h->n_tiles = h->tiles_x * h->tiles_y;
+    int th_log2 = 0;
+    while ((1 << th_log2) < t.tile_h) ++th_log2;
+    h->th_log2 = th_log2;
+    // the binning kernel keeps per-warp counters for every tile in shared memory
+    if (bin_smem_bytes(t.chunk_events, h->n_tiles) > 200 * 1024) return ESI_ERANGE;
+    const int max_chunks = (t.max_batch_events + t.chunk_events - 1) / t.chunk_events;
+    if (tile_smem_bytes(t.tile_h, t.batch_records, max_chunks) > 200 * 1024) return ESI_ERANGE;
+    return ESI_OK;
+}
+
+template <class T>
+static int ensure_device(esi_handle *h, T **p, size_t *cap, size_t need)
+{
+    if (need <= *cap) return ESI_OK;
+    size_t nc = std::max(need, *cap * 2);
+    if (*p) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+        cudaFree(*p);
+        *p = nullptr;
+        *cap = 0;
+    }
+    cudaError_t e = cudaMalloc((void **)p, nc * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    *cap = nc;
+    return ESI_OK;
+}
+
+template <class T>
+static int ensure_pinned(esi_handle *h, T **p, size_t *cap, size_t need)
+{
+    if (need <= *cap) return ESI_OK;
+    size_t nc = std::max(need, *cap * 2);
+    if (*p) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+        cudaFreeHost(*p);
+        *p = nullptr;
+        *cap = 0;
+    }
+    cudaError_t e = cudaMallocHost((void **)p, nc * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    *cap = nc;
+    return ESI_OK;
+}
+
+// Grow the pending ring so that it holds `need` events; pending events keep
+// their absolute indices (position = index & (cap - 1)).
+static int ensure_ring(esi_handle *h, unsigned long long need)
+{
+    if (need <= h->cap) return ESI_OK;
+    unsigned long long nc = h->cap ? h->cap : (1ull << 20);
+    while (nc < need) nc <<= 1;
+    esi_event *nr = nullptr;
+    cudaError_t e = cudaMalloc((void **)&nr, nc * sizeof(esi_event));
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    std::vector<long long> nm;
+    try {
+        nm.resize(nc);
+    } catch (...) {
+        cudaFree(nr);
+        return ESI_ENOMEM;
+    }
+    const unsigned long long om = h->cap ? h->cap - 1 : 0, nmk = nc - 1;
+    for (unsigned long long a = h->head; a < h->tail;) {
+        const unsigned long long po = a & om, pn = a & nmk;
+        const unsigned long long len = std::min({h->tail - a, h->cap - po, nc - pn});
+        e = cudaMemcpyAsync(nr + pn, h->ring + po, len * sizeof(esi_event),
+                            cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) {
+            cudaFree(nr);
+            return cuda_fail(h, e);
+        }
+        std::memcpy(&nm[pn], &h->tmirror[po], len * sizeof(long long));
+        a += len;
+    }
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        cudaFree(nr);
+        return cuda_fail(h, e);
+    }
+    if (h->ring) cudaFree(h->ring);
+    h->ring = nr;
+    h->cap = nc;
+    h->tmirror.swap(nm);
+    return ESI_OK;
+}
+
+static inline long long mirror_t(const esi_handle *h, unsigned long long a)
+{
+    return h->tmirror[a & (h->cap - 1)];
+}
+
+// First absolute index in [lo, hi) whose time is > v (times non-decreasing).
+static unsigned long long upper_bound_t(const esi_handle *h, unsigned long long lo,
+                                        unsigned long long hi, long long v)
+{
+    while (lo < hi) {
+        const unsigned long long mid = lo + (hi - lo) / 2;
+        if (mirror_t(h, mid) <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+int esi::read_status(esi_handle *h)
+{
+    cudaError_t e = cudaMemcpyAsync(h->hstatus, h->dstatus, sizeof(DevStatus),
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->dropped = h->hstatus->dropped;
+    if (h->hstatus->err) return h->hstatus->err;
+    return ESI_OK;
+}
+
+static cudaEvent_t prof_event(esi_handle *h)
+{
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+int esi::prof_begin(esi_handle *h, cudaEvent_t *ev)
+{
+    *ev = nullptr;
+    if (!h->prof_on) return ESI_OK;
+    *ev = prof_event(h);
+    return cuda_fail(h, cudaEventRecord(*ev, h->stream));
+}
+
+int esi::prof_end(esi_handle *h, int kind, cudaEvent_t start)
+{
+    h->launches += 1;
+    if (!h->prof_on || !start) return ESI_OK;
+    cudaEvent_t stop = prof_event(h);
+    cudaError_t e = cudaEventRecord(stop, h->stream);
+    h->prof_recs.push_back({kind, start, stop});
+    return cuda_fail(h, e);
+}
+
+// ----------------------------------------------------------------- C ABI
+extern "C" {
+
+const char *esi_strerror(int code)
+{
+    switch (code) {
+    case ESI_OK: return "ok";
+    case ESI_EINVAL: return "invalid argument";
+    case ESI_ENOMEM: return "out of memory";
+    case ESI_EBUSY: return "busy: admission refused";
+    case ESI_ETIMEORDER: return "time goes backwards";
+    case ESI_ERANGE: return "value out of range for the layout";
+    case ESI_ECUDA: return "CUDA runtime error";
+    case ESI_ETIMEOUT: return "bounded device wait timed out";
+    case ESI_ESTATE: return "call not valid in this state";
+    default: return "unknown error";
+    }
+}
+
+int esi_create(int width, int height, const esi_params *params, void *cuda_stream,
+               esi_handle **out)
+{
+    if (!out) return ESI_EINVAL;
+    *out = nullptr;
+    int rc = validate_params(width, height, params);
+    if (rc) return rc;
+    esi_handle *h = new (std::nothrow) esi_handle();
+    if (!h) return ESI_ENOMEM;
+    h->W = width;
+    h->H = height;
+    h->P = (long long)width * height;
+    h->prm = *params;
+    prepare_params(*params, &h->dp, &h->mp);
+    h->push_floor = params->t_origin_us;
+    h->frame_floor = params->t_origin_us;
+    h->last_event_t = params->t_origin_us;
+    h->last_frame_t = params->t_origin_us;
+    rc = apply_tuning(h, default_tuning(width, height));
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = set_kernel_attributes();
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            h->stream = (cudaStream_t)cuda_stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+            h->own_stream = (e == cudaSuccess);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->S, (size_t)h->P * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->T, (size_t)h->P * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->dstatus, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hstatus, sizeof(DevStatus));
+    if (e != cudaSuccess) {
+        rc = cuda_fail(h, e);
+        esi_destroy(h);
+        return rc;
+    }
+    rc = esi::init_state(h);
+    if (rc == ESI_OK) rc = ensure_ring(h, 1ull << 20);
+    if (rc == ESI_OK) rc = cuda_fail(h, cudaStreamSynchronize(h->stream));
+    if (rc) {
+        esi_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return ESI_OK;
+}
+
+void esi_destroy(esi_handle *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto &r : h->prof_recs) {
+        cudaEventDestroy(r.start);
+        cudaEventDestroy(r.stop);
+    }
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    cudaFree(h->S);
+    cudaFree(h->T);
+    cudaFree(h->ring);
+    cudaFree(h->rec);
+    cudaFree(h->hrow);
+    cudaFree(h->dtframes);
+    cudaFree(h->dframes);
+    cudaFree(h->dstatus);
+    cudaFreeHost(h->hstatus);
+    cudaFreeHost(h->htframes);
+    cudaFreeHost(h->hstage);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_device)
+{
+    if (!h || (n && !ev) || (ev_on_device != 0 && ev_on_device != 1)) return ESI_EINVAL;
+    if (n == 0) return ESI_OK;
+    const unsigned long long pending = h->tail - h->head;
+    int rc = ensure_ring(h, pending + n);
+    if (rc) return rc;
+    const unsigned long long mask = h->cap - 1;
+    long long prev = std::max(h->push_floor, h->last_event_t);
+    cudaError_t e = cudaSuccess;
+    if (!ev_on_device) {
+        // validate on the host before anything is queued
+        for (size_t i = 0; i < n; ++i) {
+            const long long t = ev[i].t_us;
+            if (t < prev) return ESI_ETIMEORDER;
+            prev = t;
+        }
+        for (unsigned long long a = h->tail, i = 0; i < n;) {
+            const unsigned long long pos = a & mask;
+            const unsigned long long len = std::min((unsigned long long)n - i, h->cap - pos);
+            e = cudaMemcpyAsync(h->ring + pos, ev + i, len * sizeof(esi_event),
+                                cudaMemcpyHostToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e);
+            for (unsigned long long j = 0; j < len; ++j) h->tmirror[pos + j] = ev[i + j].t_us;
+            a += len;
+            i += len;
+        }
+        // the caller may reuse its buffer as soon as this returns
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+    } else {
+        rc = ensure_pinned(h, &h->hstage, &h->hstage_cap, n);
+        if (rc) return rc;
+        // times to the host (strided 8 of every 16 bytes) for validation and planning
+        e = cudaMemcpy2DAsync(h->hstage, sizeof(long long), ev, sizeof(esi_event),
+                              sizeof(long long), n, cudaMemcpyDeviceToHost, h->stream);
+        for (unsigned long long a = h->tail, i = 0; e == cudaSuccess && i < n;) {
+            const unsigned long long pos = a & mask;
+            const unsigned long long len = std::min((unsigned long long)n - i, h->cap - pos);
+            e = cudaMemcpyAsync(h->ring + pos, ev + i, len * sizeof(esi_event),
+                                cudaMemcpyDeviceToDevice, h->stream);
+            a += len;
+            i += len;
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+        for (size_t i = 0; i < n; ++i) {
+            const long long t = h->hstage[i];
+            if (t < prev) return ESI_ETIMEORDER;  // ring slots past tail are ignored
+            prev = t;
+        }
+        for (unsigned long long a = h->tail, i = 0; i < n; ++a, ++i) h->tmirror[a & mask] = h->hstage[i];
+    }
+    h->tail += n;
+    h->last_event_t = prev;
+    h->pushed += n;
+    return ESI_OK;
+}
+
+int esi_render_frames(esi_handle *h, const int64_t *t_frames, size_t m, uint8_t *out,
+                      int out_on_device)
+{
+    if (!h || !t_frames || m == 0 || !out || (out_on_device != 0 && out_on_device != 1))
+        return ESI_EINVAL;
+    if (m > (size_t)INT_MAX) return ESI_EINVAL;
+    if ((long long)t_frames[0] < h->frame_floor) return ESI_ETIMEORDER;
+    for (size_t w = 1; w < m; ++w)
+        if (t_frames[w] < t_frames[w - 1]) return ESI_ETIMEORDER;
+    return esi::render_impl(h, t_frames, (int)m, out, out_on_device);
+}
+
+int esi_render_frame(esi_handle *h, int64_t t_frame_us, uint8_t *out, int out_on_device)
+{
+    return esi_render_frames(h, &t_frame_us, 1, out, out_on_device);
+}
+
+int esi_get_state(esi_handle *h, float *S, int64_t *T, int on_device)
+{
+    if (!h || !S || !T || (on_device != 0 && on_device != 1)) return ESI_EINVAL;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaMemcpyAsync(S, h->S, (size_t)h->P * sizeof(float), k, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(T, h->T, (size_t)h->P * sizeof(long long), k, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    return esi::read_status(h);
+}
+
+int esi_set_state(esi_handle *h, const float *S, const int64_t *T, int on_device)
+{
+    if (!h || !S || !T || (on_device != 0 && on_device != 1)) return ESI_EINVAL;
+    std::vector<long long> tmp;
+    const long long *Th = reinterpret_cast<const long long *>(T);
+    if (on_device) {
+        try {
+            tmp.resize((size_t)h->P);
+        } catch (...) {
+            return ESI_ENOMEM;
+        }
+        cudaError_t e = cudaMemcpyAsync(tmp.data(), T, (size_t)h->P * sizeof(long long),
+                                        cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+        Th = tmp.data();
+    }
+    long long tmax = LLONG_MIN;
+    for (long long i = 0; i < h->P; ++i) tmax = std::max(tmax, (long long)Th[i]);
+    if (h->tail > h->head && mirror_t(h, h->head) < tmax) return ESI_ETIMEORDER;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(h->S, S, (size_t)h->P * sizeof(float), k, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->T, T, (size_t)h->P * sizeof(long long), k, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->push_floor = std::max(h->push_floor, tmax);
+    h->frame_floor = std::max(h->frame_floor, tmax);
+    return ESI_OK;
+}
+
+int esi_synchronize(esi_handle *h)
+{
+    if (!h) return ESI_EINVAL;
+    return esi::read_status(h);
+}
+
+int esi_get_stats(esi_handle *h, esi_stats *out)
+{
+    if (!h || !out) return ESI_EINVAL;
+    int rc = esi::read_status(h);
+    out->events_pushed = h->pushed;
+    out->events_consumed = h->consumed;
+    out->events_dropped = h->dropped;
+    out->events_pending = h->tail - h->head;
+    out->frames_rendered = h->frames;
+    out->kernel_launches = h->launches;
+    out->last_event_t_us = h->last_event_t;
+    out->last_frame_t_us = h->last_frame_t;
+    return rc;
+}
+
+int esi_set_tuning(esi_handle *h, const esi_tuning *t)
+{
+    if (!h || !t) return ESI_EINVAL;
+    esi_tuning d = default_tuning(h->W, h->H);
+    esi_tuning n = *t;
+    if (!n.tile_h) n.tile_h = d.tile_h;
+    if (!n.chunk_events) n.chunk_events = d.chunk_events;
+    if (!n.batch_records) n.batch_records = d.batch_records;
+    if (!n.max_batch_events) n.max_batch_events = d.max_batch_events;
+    int rc = validate_tuning(n);
+    if (rc) return rc;
+    esi_tuning old = h->tun;
+    rc = apply_tuning(h, n);
+    if (rc) apply_tuning(h, old);
+    return rc;
+}
+
+int esi_get_tuning(esi_handle *h, esi_tuning *out)
+{
+    if (!h || !out) return ESI_EINVAL;
+    *out = h->tun;
+    return ESI_OK;
+}
+
+int esi_profile_enable(esi_handle *h, int enable)
+{
+    if (!h) return ESI_EINVAL;
+    h->prof_on = enable != 0;
+    return ESI_OK;
+}
+
+int esi_profile_read(esi_handle *h, esi_kernel_time *out, int max)
+{
+    if (!h || max < 0 || (max > 0 && !out)) return ESI_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    for (auto &r : h->prof_recs) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, r.start, r.stop);
+        if (r.kind >= 0 && r.kind < kNumKernelKinds) {
+            h->prof_ms[r.kind] += ms;
+            h->prof_n[r.kind] += 1;
+        }
+        h->ev_pool.push_back(r.start);
+        h->ev_pool.push_back(r.stop);
+    }
+    h->prof_recs.clear();
+    int n = 0;
+    for (int k = 0; k < kNumKernelKinds; ++k) {
+        if (!h->prof_n[k]) continue;
+        if (n < max) {
+            std::memset(out[n].name, 0, sizeof(out[n].name));
+            std::strncpy(out[n].name, kKernelNames[k], sizeof(out[n].name) - 1);
+            out[n].launches = h->prof_n[k];
+            out[n].total_ms = h->prof_ms[k];
+        }
+        ++n;
+    }
+    return n;
+}
+
+int esi_profile_reset(esi_handle *h)
+{
+    if (!h) return ESI_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    for (auto &r : h->prof_recs) {
+        h->ev_pool.push_back(r.start);
+        h->ev_pool.push_back(r.stop);
+    }
+    h->prof_recs.clear();
+    for (int k = 0; k < kNumKernelKinds; ++k) {
+        h->prof_ms[k] = 0.0;
+        h->prof_n[k] = 0;
+    }
+    return cuda_fail(h, e);
+}
+
+}  // extern "C"
+
+// --------------------------------------------------------------- rendering
+int esi::init_state(esi_handle *h)
+{
+    // Alg. 2 initialisation: S = 0, T = t_origin
+    cudaError_t e = cudaMemsetAsync(h->S, 0, (size_t)h->P * sizeof(float), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dstatus, 0, sizeof(DevStatus), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    return fill_i64(h, h->T, h->P, h->prm.t_origin_us);
+}
+
+int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int out_on_device)
+{
+    const long long t_last = tf[m - 1];
+    const unsigned long long n_split = upper_bound_t(h, h->head, h->tail, t_last) - h->head;
+    int rc = ensure_pinned(h, &h->htframes, &h->htframes_cap, (size_t)m);
+    if (!rc) rc = ensure_device(h, &h->dtframes, &h->dtframes_cap, (size_t)m);
+    if (rc) return rc;
+    std::memcpy(h->htframes, tf, (size_t)m * sizeof(long long));
+    cudaError_t e = cudaMemcpyAsync(h->dtframes, h->htframes, (size_t)m * sizeof(long long),
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    uint8_t *frames = out;
+    if (!out_on_device) {
+        rc = ensure_device(h, &h->dframes, &h->dframes_cap, (size_t)m * (size_t)h->P);
+        if (rc) return rc;
+        frames = h->dframes;
+    }
+    const esi_tuning &tu = h->tun;
+    const int chunk = tu.chunk_events;
+    const unsigned long long maxb = (unsigned long long)tu.max_batch_events;
+    {
+        const size_t max_chunks = (size_t)((maxb + chunk - 1) / chunk);
+        rc = ensure_device(h, &h->rec, &h->rec_cap, max_chunks * (size_t)chunk);
+        if (!rc) rc = ensure_device(h, &h->hrow, &h->hrow_cap, max_chunks * (size_t)h->n_tiles);
+        if (rc) return rc;
+    }
+    unsigned long long i = 0;
+    int w = 0;
+    for (;;) {
+        const unsigned long long a0 = h->head + i;
+        unsigned long long i1 = std::min(n_split, i + maxb);
+        long long t_base = 0;
+        if (i1 > i) {
+            t_base = mirror_t(h, a0);
+            // record times are 32-bit offsets from t_base
+            const long long lim = t_base + 0xffffffffll;
+            const unsigned long long cut = upper_bound_t(h, a0, h->head + i1, lim) - h->head;
+            i1 = std::max(cut, i + 1);
+        }
+        int w1 = m;
+        if (i1 < n_split) {
+            const long long tn = mirror_t(h, h->head + i1);
+            w1 = (int)(std::lower_bound(tf + w, tf + m, (int64_t)tn) - tf);
+        }
+        const int nb = (int)(i1 - i);
+        const int n_chunks = (nb + chunk - 1) / chunk;
+        if (nb > 0) {
+            BinArgs ba;
+            ba.ring = h->ring;
+            ba.ring_mask = h->cap - 1;
+            ba.first = a0;
+            ba.n = nb;
+            ba.chunk = chunk;
+            ba.t_base = t_base;
+            ba.W = h->W;
+            ba.H = h->H;
+            ba.tiles_x = h->tiles_x;
+            ba.n_tiles = h->n_tiles;
+            ba.th_log2 = h->th_log2;
+            ba.rec = h->rec;
+            ba.hrow = h->hrow;
+            ba.status = h->dstatus;
+            cudaEvent_t ev;
+            rc = prof_begin(h, &ev);
+            if (!rc) rc = cuda_fail(h, launch_bin(ba, n_chunks, h->stream));
+            if (!rc) rc = prof_end(h, kKindBin, ev);
+            if (rc) return rc;
+        }
+        TileArgs ta;
+        ta.rec = h->rec;
+        ta.hrow = h->hrow;
+        ta.n_chunks = n_chunks;
+        ta.chunk = chunk;
+        ta.n_tiles = h->n_tiles;
+        ta.t_base = t_base;
+        ta.S = h->S;
+        ta.T = h->T;
+        ta.W = h->W;
+        ta.H = h->H;
+        ta.tiles_x = h->tiles_x;
+        ta.dp = h->dp;
+        ta.mp = h->mp;
+        ta.t_frames = h->dtframes;
+        ta.w_begin = w;
+        ta.w_end = w1;
+        ta.frames = frames;
+        ta.P = h->P;
+        ta.batch = tu.batch_records;
+        ta.status = h->dstatus;
+        cudaEvent_t ev;
+        rc = prof_begin(h, &ev);
+        if (!rc) rc = cuda_fail(h, launch_tile(ta, tu.tile_h, h->stream));
+        if (!rc) rc = prof_end(h, kKindTile, ev);
+        if (rc) return rc;
+        i = i1;
+        w = w1;
+        if (i >= n_split && w >= m) break;
+    }
+    h->head += n_split;
+    h->consumed += n_split;
+    h->frames += (unsigned long long)m;
+    h->last_frame_t = t_last;
+    h->frame_floor = std::max(h->frame_floor, (long long)t_last);
+    h->push_floor = std::max(h->push_floor, (long long)t_last);
+    if (!out_on_device) {
+        e = cudaMemcpyAsync(out, frames, (size_t)m * (size_t)h->P, cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+        return read_status(h);
+    }
+    return ESI_OK;
+}
+
+int esi::fill_i64(esi_handle *h, long long *dst, long long n, long long value)
+{
+    cudaEvent_t ev;
+    int rc = prof_begin(h, &ev);
+    if (!rc) rc = cuda_fail(h, launch_fill_i64(dst, n, value, h->stream));
+    if (!rc) rc = prof_end(h, kKindFill, ev);
+    return rc;
+}

@@ -1,0 +1,93 @@
+// Private definition of esi_handle and the host helpers shared by the C ABI
+// translation units.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "esi_internal.h"
+
+namespace esi {
+
+enum KernelKind { kKindBin = 0, kKindTile = 1, kKindFill = 2, kKindTick = 3, kNumKernelKinds = 4 };
+static const char *const kKernelNames[kNumKernelKinds] = {"esi_bin", "esi_tile", "esi_fill",
+                                                          "esi_tick"};
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t start;
+    cudaEvent_t stop;
+};
+
+}  // namespace esi
+
+struct esi_handle {
+    int W = 0, H = 0;
+    long long P = 0;
+    esi_params prm{};
+    esi::DecayParams dp{};
+    esi::MapParams mp{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    esi_tuning tun{};
+    int tiles_x = 0, tiles_y = 0, n_tiles = 0, th_log2 = 0;
+
+    float *S = nullptr;           // accumulation matrix (Alg. 2), row-major
+    long long *T = nullptr;       // last decay time matrix (Alg. 2)
+
+    // pending events: ring of `cap` events (power of two) on the device and a
+    // host mirror of their times; absolute indices head <= i < tail
+    esi_event *ring = nullptr;
+    unsigned long long cap = 0, head = 0, tail = 0;
+    std::vector<long long> tmirror;
+
+    unsigned long long *rec = nullptr;   // binned records of one sub-batch
+    size_t rec_cap = 0;
+    unsigned int *hrow = nullptr;        // [chunk][tile] run table
+    size_t hrow_cap = 0;
+    long long *dtframes = nullptr;
+    size_t dtframes_cap = 0;
+    long long *htframes = nullptr;       // pinned
+    size_t htframes_cap = 0;
+    unsigned char *dframes = nullptr;    // frames staged for host outputs
+    size_t dframes_cap = 0;
+    long long *hstage = nullptr;         // pinned: times of a device push
+    size_t hstage_cap = 0;
+
+    esi::DevStatus *dstatus = nullptr;
+    esi::DevStatus *hstatus = nullptr;   // pinned
+
+    long long push_floor = 0;     // pushes must not be earlier than this
+    long long frame_floor = 0;    // frames must not be earlier than this
+    long long last_event_t = 0;
+    long long last_frame_t = 0;
+    unsigned long long pushed = 0, consumed = 0, dropped = 0, frames = 0, launches = 0;
+
+    bool prof_on = false;
+    std::vector<esi::ProfRec> prof_recs;
+    std::vector<cudaEvent_t> ev_pool;
+    double prof_ms[esi::kNumKernelKinds] = {};
+    unsigned long long prof_n[esi::kNumKernelKinds] = {};
+
+    std::string cuda_msg;
+};
+
+namespace esi {
+
+int cuda_fail(esi_handle *h, cudaError_t e);
+long long decay_cutoff(double k_per_s);
+int validate_params(int W, int H, const esi_params *p);
+void prepare_params(const esi_params &p, DecayParams *dp, MapParams *mp);
+int validate_tuning(const esi_tuning &t);
+esi_tuning default_tuning(int W, int H);
+int read_status(esi_handle *h);
+int prof_begin(esi_handle *h, cudaEvent_t *ev);
+int prof_end(esi_handle *h, int kind, cudaEvent_t start);
+int init_state(esi_handle *h);
+int render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int out_on_device);
+int fill_i64(esi_handle *h, long long *dst, long long n, long long value);
+cudaError_t launch_fill_i64(long long *dst, long long n, long long value, cudaStream_t s);
+
+}  // namespace esi

@@ -1,0 +1,214 @@
+// Device helpers of the ESI kernels: the Alg. 2 update, the Eq. 4 decay, the
+// Eq. 14 map, warp/block scans and the bulk-copy (TMA) / mbarrier PTX.
+#pragma once
+
+#include <cstdint>
+
+#include "esi_internal.h"
+
+namespace esi {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// ------------------------------------------------------ mbarrier + bulk copy
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared through the TMA unit; completes `bytes` of
+// transaction count on `bar`.  dst, src 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `phase` of `bar` for at most limit_ns; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase,
+                                                  unsigned long long limit_ns)
+{
+    unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, phase)) {
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------- scans
+__device__ __forceinline__ unsigned warp_inclusive_scan(unsigned v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned u = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Exclusive scan of one value per thread over the block; returns the prefix
+// and writes the total to *total.  tmp holds NT/32 + 1 words.
+template <int NT>
+__device__ __forceinline__ unsigned block_exclusive_scan1(unsigned v, unsigned *tmp, unsigned *total)
+{
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned inc = warp_inclusive_scan(v);
+    if (lane == 31) tmp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned w = (lane < NW) ? tmp[lane] : 0u;
+        unsigned wi = warp_inclusive_scan(w);
+        if (lane < NW) tmp[lane] = wi - w;
+        if (lane == NW - 1) tmp[NW] = wi;
+    }
+    __syncthreads();
+    unsigned r = tmp[warp] + inc - v;
+    *total = tmp[NW];
+    __syncthreads();
+    return r;
+}
+
+// In-place exclusive scan of data[0..n) (shared memory); returns the total.
+template <int NT>
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned *data, int n, unsigned *tmp)
+{
+    const int per = (n + NT - 1) / NT;
+    const int b0 = min((int)threadIdx.x * per, n), b1 = min(b0 + per, n);
+    unsigned s = 0;
+    for (int i = b0; i < b1; ++i) s += data[i];
+    unsigned total;
+    unsigned run = block_exclusive_scan1<NT>(s, tmp, &total);
+    for (int i = b0; i < b1; ++i) {
+        unsigned d = data[i];
+        data[i] = run;
+        run += d;
+    }
+    __syncthreads();
+    return total;
+}
+
+// ------------------------------------------------------------- the method
+// 1 - k dt formed as (1 - k_hi dh) - (error terms) with dt = dh + dl split
+// exactly and k_hi dh = p + e exactly (FMA), so that u keeps its relative
+// accuracy when it is small (dt near the cutoff).
+__device__ __forceinline__ float one_minus_kdt(long long dt, const DecayParams &dp)
+{
+    float dh = __ll2float_rn(dt);
+    float dl = __ll2float_rn(dt - __float2ll_rn(dh));
+    float p = dp.k_hi * dh;
+    float e = fmaf(dp.k_hi, dh, -p);
+    float u = 1.0f - p;
+    float corr = e + fmaf(dp.k_hi, dl, dp.k_lo * dh);
+    return fmaxf(u - corr, 0.0f);
+}
+
+// Eq. 4 for the state update (accurate powf for non-integer b).
+__device__ __forceinline__ float decay_state(long long dt, const DecayParams &dp)
+{
+    if (dt >= dp.cutoff) return 0.0f;
+    if (dp.b_mode == 4) return 1.0f;
+    float u = one_minus_kdt(dt, dp);
+    switch (dp.b_mode) {
+    case 1: return u;
+    case 2: return u * u;
+    case 3: return u * u * u;
+    default: return powf(u, dp.b);
+    }
+}
+
+// Eq. 4 for the render-time view; only feeds an 8-bit code, so the general-b
+// case uses the fast hardware power.
+__device__ __forceinline__ float decay_view(long long dt, const DecayParams &dp)
+{
+    if (dt >= dp.cutoff) return 0.0f;
+    if (dp.b_mode == 4) return 1.0f;
+    float u = one_minus_kdt(dt, dp);
+    switch (dp.b_mode) {
+    case 1: return u;
+    case 2: return u * u;
+    case 3: return u * u * u;
+    default: return __powf(u, dp.b);
+    }
+}
+
+// Alg. 2 loop body for one event of this pixel, in the paper's order:
+// S <- S + p C;  dt <- t - T;  S <- S d(dt);  T <- t;  S <- clamp (Eq. 13).
+__device__ __forceinline__ void esi_apply(float &S, long long &T, long long t, bool pos,
+                                          const DecayParams &dp, const MapParams &mp)
+{
+    float s = S + (pos ? mp.C : -mp.C);
+    long long dt = t - T;
+    s = s * decay_state(dt, dp);
+    T = t;
+    S = fminf(fmaxf(s, mp.s_min), mp.s_max);
+}
+
+// Eq. 14 with round-half-to-even and saturation to [0, 255].
+__device__ __forceinline__ unsigned char esi_quantize(float v, const MapParams &mp)
+{
+    int r = __float2int_rn(fmaf(v, mp.scale, mp.offs));
+    r = max(0, min(255, r));
+    return static_cast<unsigned char>(r);
+}
+
+__device__ __forceinline__ unsigned char esi_pixel_code(float S, long long T, long long t_frame,
+                                                        const DecayParams &dp, const MapParams &mp)
+{
+    float v = S;
+    if (mp.render_decay && S != 0.0f) v = S * decay_view(t_frame - T, dp);
+    return esi_quantize(v, mp);
+}
+
+__device__ __forceinline__ void set_error(DevStatus *st, int code, int where)
+{
+    if (atomicCAS(&st->err, 0, code) == 0) st->err_where = where;
+}
+
+}  // namespace esi

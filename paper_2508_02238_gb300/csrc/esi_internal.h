@@ -1,0 +1,96 @@
+// Internal types shared by the ESI host code and its sm_103a kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "esi.h"
+
+namespace esi {
+
+constexpr int kTileW = 32;  // a tile row is one warp: lane = x within the tile
+
+// Decay of Eq. 4, d(dt) = max(1 - k dt, 0)^b, prepared for the device.
+//   k_hi + k_lo is k per microsecond (k * 1e-6 in double) split into floats so
+//   that 1 - k dt can be formed without cancellation error near the cutoff.
+//   cutoff is the smallest integer dt with 1 - k dt <= 0 evaluated in double
+//   (so the device takes the d = 0 decision in the same precision as the
+//   definition); INT64_MAX when k = 0.
+struct DecayParams {
+    float k_hi;
+    float k_lo;
+    float b;
+    int b_mode;         // 0: powf; 1, 2, 3: integer b; 4: k == 0 (d = 1)
+    long long cutoff;
+};
+
+// Clamp of Eq. 13 and linear map of Eq. 14: B = rint(v * scale + offs).
+struct MapParams {
+    float C;
+    float s_min;
+    float s_max;
+    float scale;        // 255 / (s_max - s_min)
+    float offs;         // -s_min * scale
+    int render_decay;
+};
+
+// Device-side status, read back at synchronising calls.
+struct DevStatus {
+    unsigned long long dropped;   // events with x >= W or y >= H
+    int err;                      // ESI_* code of a device-detected failure
+    int err_where;                // which kernel / wait gave up
+};
+
+// Arguments of the binning kernel (one block per chunk of events).
+struct BinArgs {
+    const esi_event *ring;        // pending-event ring
+    unsigned long long ring_mask; // capacity - 1 (capacity is a power of two)
+    unsigned long long first;     // ring position of the sub-batch's first event
+    int n;                        // events in the sub-batch
+    int chunk;                    // events per block (power of two)
+    long long t_base;             // record times are t - t_base (< 2^32)
+    int W, H, tiles_x, n_tiles;
+    int th_log2;                  // log2 of rows per tile
+    unsigned long long *rec;      // out: records, block c at rec + c * chunk
+    unsigned int *hrow;           // out: [chunk][tile] (start << 16 | count)
+    DevStatus *status;
+};
+
+// Arguments of the tile kernel (one block per 32 x TH pixel tile).
+struct TileArgs {
+    const unsigned long long *rec;
+    const unsigned int *hrow;
+    int n_chunks;
+    int chunk;
+    int n_tiles;
+    long long t_base;
+    float *S;
+    long long *T;
+    int W, H, tiles_x;
+    DecayParams dp;
+    MapParams mp;
+    const long long *t_frames;    // frame times of this render (device)
+    int w_begin, w_end;           // frames this launch completes
+    unsigned char *frames;        // frame w at frames + w * P
+    long long P;
+    int batch;                    // records sorted per shared-memory batch
+    DevStatus *status;
+};
+
+// Record layout (8 bytes): low 32 bits t - t_base; high 32 bits
+// (pixel-in-tile << 1) | (p > 0).
+__host__ __device__ inline unsigned long long make_record(unsigned int toff,
+                                                          unsigned int pit,
+                                                          unsigned int pos)
+{
+    return (unsigned long long)toff | ((unsigned long long)((pit << 1) | pos) << 32);
+}
+
+// Launchers (esi_kernels.cu).
+size_t bin_smem_bytes(int chunk, int n_tiles);
+size_t tile_smem_bytes(int tile_h, int batch, int n_chunks);
+cudaError_t launch_bin(const BinArgs &a, int n_chunks, cudaStream_t s);
+cudaError_t launch_tile(const TileArgs &a, int tile_h, cudaStream_t s);
+cudaError_t set_kernel_attributes();
+
+}  // namespace esi

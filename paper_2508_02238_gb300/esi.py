@@ -1,0 +1,204 @@
+"""ctypes binding of libesi.so: the C ABI of include/esi.h, same names.
+
+Argument marshalling only.  Every step of the hot path runs in the CUDA
+kernels of libesi.so; if the library cannot be built or loaded this module
+raises instead of falling back to anything else.  Pointers may be given as
+ints, numpy arrays (host memory) or torch tensors (``data_ptr()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+ESI_OK = 0
+ESI_EINVAL = -1
+ESI_ENOMEM = -2
+ESI_EBUSY = -3
+ESI_ETIMEORDER = -4
+ESI_ERANGE = -5
+ESI_ECUDA = -6
+ESI_ETIMEOUT = -7
+ESI_ESTATE = -8
+
+
+class esi_params(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_double), ("k_per_s", ctypes.c_double),
+                ("b", ctypes.c_double), ("s_min", ctypes.c_double),
+                ("s_max", ctypes.c_double), ("t_origin_us", ctypes.c_int64),
+                ("render_decay", ctypes.c_int32), ("_reserved", ctypes.c_int32)]
+
+
+class esi_stats(ctypes.Structure):
+    _fields_ = [("events_pushed", ctypes.c_uint64), ("events_consumed", ctypes.c_uint64),
+                ("events_dropped", ctypes.c_uint64), ("events_pending", ctypes.c_uint64),
+                ("frames_rendered", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("last_event_t_us", ctypes.c_int64), ("last_frame_t_us", ctypes.c_int64)]
+
+
+class esi_tuning(ctypes.Structure):
+    _fields_ = [("tile_h", ctypes.c_int32), ("chunk_events", ctypes.c_int32),
+                ("batch_records", ctypes.c_int32), ("max_batch_events", ctypes.c_int32)]
+
+
+class esi_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64),
+                ("total_ms", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_i32, _i64, _sz = ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+
+# name -> (restype, argtypes); the declarations of include/esi.h
+SIGNATURES = {
+    "esi_create": (_i32, [_i32, _i32, ctypes.POINTER(esi_params), _P, ctypes.POINTER(_P)]),
+    "esi_push_events": (_i32, [_P, _P, _sz, _i32]),
+    "esi_render_frame": (_i32, [_P, _i64, _P, _i32]),
+    "esi_render_frames": (_i32, [_P, _P, _sz, _P, _i32]),
+    "esi_get_state": (_i32, [_P, _P, _P, _i32]),
+    "esi_set_state": (_i32, [_P, _P, _P, _i32]),
+    "esi_synchronize": (_i32, [_P]),
+    "esi_get_stats": (_i32, [_P, ctypes.POINTER(esi_stats)]),
+    "esi_set_tuning": (_i32, [_P, ctypes.POINTER(esi_tuning)]),
+    "esi_get_tuning": (_i32, [_P, ctypes.POINTER(esi_tuning)]),
+    "esi_profile_enable": (_i32, [_P, _i32]),
+    "esi_profile_read": (_i32, [_P, ctypes.POINTER(esi_kernel_time), _i32]),
+    "esi_profile_reset": (_i32, [_P]),
+    "esi_destroy": (None, [_P]),
+    "esi_strerror": (ctypes.c_char_p, [_i32]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libesi.so (building it first if needed); raises if that fails."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libesi.so is not built; run paper_2508_02238_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def ptr(x) -> int:
+    """Address of an int, a numpy array or a torch tensor (0 for None)."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if hasattr(x, "ctypes"):
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _fn(name):
+    return getattr(load_library(), name)
+
+
+def esi_strerror(code: int) -> str:
+    return _fn("esi_strerror")(int(code)).decode()
+
+
+def esi_create(width: int, height: int, params: esi_params, cuda_stream=0):
+    """Returns (rc, handle)."""
+    h = _P()
+    rc = _fn("esi_create")(int(width), int(height), ctypes.byref(params),
+                           _P(int(cuda_stream) or None), ctypes.byref(h))
+    return rc, h
+
+
+def esi_push_events(h, ev, n: int, ev_on_device: int) -> int:
+    return _fn("esi_push_events")(h, _P(ptr(ev) or None), int(n), int(ev_on_device))
+
+
+def esi_render_frame(h, t_frame_us: int, out, out_on_device: int) -> int:
+    return _fn("esi_render_frame")(h, int(t_frame_us), _P(ptr(out) or None), int(out_on_device))
+
+
+def esi_render_frames(h, t_frames, m: int, out, out_on_device: int) -> int:
+    return _fn("esi_render_frames")(h, _P(ptr(t_frames) or None), int(m),
+                                    _P(ptr(out) or None), int(out_on_device))
+
+
+def esi_get_state(h, S, T, on_device: int) -> int:
+    return _fn("esi_get_state")(h, _P(ptr(S) or None), _P(ptr(T) or None), int(on_device))
+
+
+def esi_set_state(h, S, T, on_device: int) -> int:
+    return _fn("esi_set_state")(h, _P(ptr(S) or None), _P(ptr(T) or None), int(on_device))
+
+
+def esi_synchronize(h) -> int:
+    return _fn("esi_synchronize")(h)
+
+
+def esi_get_stats(h):
+    st = esi_stats()
+    rc = _fn("esi_get_stats")(h, ctypes.byref(st))
+    return rc, st
+
+
+def esi_set_tuning(h, t: esi_tuning) -> int:
+    return _fn("esi_set_tuning")(h, ctypes.byref(t))
+
+
+def esi_get_tuning(h):
+    t = esi_tuning()
+    rc = _fn("esi_get_tuning")(h, ctypes.byref(t))
+    return rc, t
+
+
+def esi_profile_enable(h, enable: int) -> int:
+    return _fn("esi_profile_enable")(h, int(enable))
+
+
+def esi_profile_read(h, max_entries: int = 16):
+    arr = (esi_kernel_time * max_entries)()
+    n = _fn("esi_profile_read")(h, arr, int(max_entries))
+    if n < 0:
+        return n, {}
+    return ESI_OK, {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
+                    for i in range(min(n, max_entries))}
+
+
+def esi_profile_reset(h) -> int:
+    return _fn("esi_profile_reset")(h)
+
+
+def esi_destroy(h) -> None:
+    _fn("esi_destroy")(h)
+
+
+class EsiError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {esi_strerror(code)} ({code})")
+        self.code = code
+
+
+def check(rc: int, what: str = "esi call") -> None:
+    if rc != ESI_OK:
+        raise EsiError(rc, what)
+
+
+def make_params(C: float, k_per_s: float, b: float, s_min: float, s_max: float,
+                t_origin_us: int = 0, render_decay: int = 0) -> esi_params:
+    p = esi_params()
+    p.C, p.k_per_s, p.b, p.s_min, p.s_max = C, k_per_s, b, s_min, s_max
+    p.t_origin_us, p.render_decay = int(t_origin_us), int(render_decay)
+    return p

@@ -1,0 +1,162 @@
+"""Runs one stream through the CUDA path (C ABI) and through the FP64 oracle.
+
+Tolerances (written here, used by every parity test):
+
+* state S: err = |S_gpu - S_ref| / max(|S_ref|, C) <= 1e-5.  The floor C is
+  the state's quantum (one event's step): an FP32 state that cancels +C
+  against -C keeps an absolute error of a few units in the last place of C,
+  so a purely relative bound is undefined near S = 0.
+* T: exact (int64 microseconds on both sides).
+* frames: |B_gpu - B_ref| <= 1 (the map is rounded in FP32 on the device and in
+  FP64 in the oracle; a value within rounding of a .5 boundary may differ).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+from synth import EVENT_DTYPE
+
+STATE_TOL = 1e-5
+
+
+def oracle_params(p) -> oracle.OracleParams:
+    return oracle.OracleParams(C=p["C"], k_per_s=p["k_per_s"], b=p["b"],
+                               s_min=p["s_min"], s_max=p["s_max"],
+                               t_origin_us=p.get("t_origin_us", 0),
+                               render_decay=p.get("render_decay", 0))
+
+
+def state_error(S_gpu, S_ref, C):
+    S_gpu = np.asarray(S_gpu, dtype=np.float64)
+    den = np.maximum(np.abs(S_ref), C)
+    return float(np.max(np.abs(S_gpu - S_ref) / den)) if len(S_ref) else 0.0
+
+
+def compare(gpu, ref, C, label=""):
+    """Assert the parity bar; return a summary dict (max errors)."""
+    err = state_error(gpu["S"], ref["S"], C)
+    assert err <= STATE_TOL, f"{label}: state err {err:.3e}"
+    assert np.array_equal(gpu["T"], ref["T"]), f"{label}: T differs"
+    out = {"state_err": err}
+    if ref.get("frames") is not None:
+        d = np.abs(gpu["frames"].astype(np.int16) - ref["frames"].astype(np.int16))
+        mx = int(d.max()) if d.size else 0
+        assert mx <= 1, f"{label}: frame diff {mx}"
+        out["frame_max_lsb"] = mx
+        out["frame_off_by_one"] = int(np.count_nonzero(d))
+    return out
+
+
+def run_oracle(events, W, H, p, t_frames):
+    st = oracle.OracleState(W, H, oracle_params(p))
+    frames, used = st.replay(events, t_frames)
+    return {"S": st.S.copy(), "T": st.T.copy(), "frames": frames, "used": used,
+            "dropped": int(st.dropped[0])}
+
+
+class GpuStream:
+    """One esi_handle driven through the ctypes binding of the C ABI."""
+
+    def __init__(self, W, H, p, tuning=None, stream=None):
+        import torch
+        from paper_2508_02238_gb300 import esi
+        self.esi, self.torch = esi, torch
+        self.W, self.H = W, H
+        params = esi.make_params(p["C"], p["k_per_s"], p["b"], p["s_min"], p["s_max"],
+                                 p.get("t_origin_us", 0), p.get("render_decay", 0))
+        rc, self.h = esi.esi_create(W, H, params, stream or 0)
+        esi.check(rc, "esi_create")
+        if tuning:
+            t = esi.esi_tuning()
+            t.tile_h = tuning.get("tile_h", 0)
+            t.chunk_events = tuning.get("chunk_events", 0)
+            t.batch_records = tuning.get("batch_records", 0)
+            t.max_batch_events = tuning.get("max_batch_events", 0)
+            esi.check(esi.esi_set_tuning(self.h, t), "esi_set_tuning")
+
+    def push(self, events, on_device=False):
+        ev = np.ascontiguousarray(events, dtype=EVENT_DTYPE)
+        if on_device:
+            dev = self.torch.from_numpy(ev.view(np.uint8).copy()).cuda()
+            rc = self.esi.esi_push_events(self.h, dev, len(ev), 1)
+            self.torch.cuda.synchronize()
+            return rc
+        return self.esi.esi_push_events(self.h, ev, len(ev), 0)
+
+    def render_frames(self, t_frames, on_device=False):
+        tf = np.ascontiguousarray(t_frames, dtype=np.int64)
+        M = len(tf)
+        if on_device:
+            out = self.torch.empty((M, self.H, self.W), dtype=self.torch.uint8, device="cuda")
+            rc = self.esi.esi_render_frames(self.h, tf, M, out, 1)
+            self.esi.check(self.esi.esi_synchronize(self.h), "sync")
+            return rc, out.cpu().numpy()
+        out = np.empty((M, self.H, self.W), dtype=np.uint8)
+        rc = self.esi.esi_render_frames(self.h, tf, M, out, 0)
+        return rc, out
+
+    def render_frame(self, t):
+        out = np.empty((self.H, self.W), dtype=np.uint8)
+        rc = self.esi.esi_render_frame(self.h, int(t), out, 0)
+        return rc, out
+
+    def state(self):
+        S = np.empty(self.W * self.H, dtype=np.float32)
+        T = np.empty(self.W * self.H, dtype=np.int64)
+        self.esi.check(self.esi.esi_get_state(self.h, S, T, 0), "esi_get_state")
+        return S, T
+
+    def set_state(self, S, T):
+        S = np.ascontiguousarray(S, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.int64)
+        return self.esi.esi_set_state(self.h, S, T, 0)
+
+    def stats(self):
+        rc, st = self.esi.esi_get_stats(self.h)
+        self.esi.check(rc, "esi_get_stats")
+        return st
+
+    def close(self):
+        if self.h:
+            self.esi.esi_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def run_gpu(events, W, H, p, t_frames, mode="replay", tuning=None, on_device=False):
+    """mode: 'replay' (one esi_render_frames) or 'per_frame' (one call per frame)."""
+    with GpuStream(W, H, p, tuning) as g:
+        g.esi.check(g.push(events, on_device=on_device), "push")
+        if mode == "replay":
+            rc, frames = g.render_frames(t_frames, on_device=on_device)
+            g.esi.check(rc, "render_frames")
+        else:
+            frames = np.empty((len(t_frames), H, W), dtype=np.uint8)
+            for i, t in enumerate(t_frames):
+                rc, frames[i] = g.render_frame(t)
+                g.esi.check(rc, "render_frame")
+        S, T = g.state()
+        st = g.stats()
+        return {"S": S, "T": T, "frames": frames, "dropped": int(st.events_dropped),
+                "consumed": int(st.events_consumed), "launches": int(st.kernel_launches)}
+
+
+def random_events(rng, W, H, n, t0, t1, hot=None):
+    """Uniform random stream (sorted times); hot=(x, y, fraction) adds a hot pixel."""
+    ev = np.zeros(n, dtype=EVENT_DTYPE)
+    ev["t"] = np.sort(rng.integers(t0, t1, size=n))
+    ev["x"] = rng.integers(0, W, size=n)
+    ev["y"] = rng.integers(0, H, size=n)
+    ev["p"] = np.where(rng.random(n) < 0.5, 1, -1)
+    if hot is not None:
+        hx, hy, frac = hot
+        sel = rng.random(n) < frac
+        ev["x"][sel], ev["y"][sel] = hx, hy
+        ev["p"][sel] = np.where(rng.random(int(sel.sum())) < 0.8, 1, -1)
+    return ev

@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads and exports what include/esi.h declares.
+
+These run without a GPU: no call here reaches a kernel.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2508_02238_gb300 import esi
+from paper_2508_02238_gb300 import build as esi_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def declared_functions():
+    names = set()
+    for hdr in HEADERS:
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \t\*]*?\b(esi_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    lib_path = esi_build.build()
+    lib = ctypes.CDLL(lib_path)
+    names = declared_functions()
+    assert len(names) >= 15
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+    # the binding covers every declared function
+    assert not (names - set(esi.SIGNATURES)), names - set(esi.SIGNATURES)
+
+
+def test_strerror_codes():
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
+        assert esi.esi_strerror(code) != "unknown error"
+    assert esi.esi_strerror(-99) == "unknown error"
+
+
+GOOD = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0)
+
+
+@pytest.mark.parametrize("W,H,over", [
+    (0, 10, {}), (10, 0, {}), (70000, 10, {}), (10, 70000, {}),
+    (10, 10, {"C": 0.0}), (10, 10, {"C": -1.0}), (10, 10, {"C": float("nan")}),
+    (10, 10, {"k_per_s": -1.0}), (10, 10, {"k_per_s": float("inf")}),
+    (10, 10, {"b": 0.0}), (10, 10, {"s_min": 1.0, "s_max": 1.0}),
+    (10, 10, {"s_min": 2.0, "s_max": 1.0}), (10, 10, {"s_max": float("inf")}),
+])
+def test_create_rejects_bad_arguments_before_touching_cuda(W, H, over):
+    kw = dict(GOOD)
+    kw.update(over)
+    p = esi.make_params(**kw)
+    rc, h = esi.esi_create(W, H, p)
+    assert rc == esi.ESI_EINVAL and not h.value
+
+
+def test_create_bad_render_mode():
+    p = esi.make_params(**GOOD, render_decay=2)
+    rc, _ = esi.esi_create(8, 8, p)
+    assert rc == esi.ESI_EINVAL
+
+
+def test_null_handle_calls_are_rejected():
+    assert esi.esi_push_events(None, None, 0, 0) == esi.ESI_EINVAL
+    assert esi.esi_render_frame(None, 0, None, 0) == esi.ESI_EINVAL
+    assert esi.esi_synchronize(None) == esi.ESI_EINVAL
+    esi.esi_destroy(None)  # no-op

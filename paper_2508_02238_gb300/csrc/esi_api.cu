@@ -86,10 +86,10 @@ esi_tuning default_tuning(int W, int H)
     (void)W;
     (void)H;
     esi_tuning t;
-    t.tile_h = 32;
+    t.tile_h = 8;
     t.chunk_events = 2048;
     t.batch_records = 4096;
-    t.max_batch_events = 1 << 21;
+    t.max_batch_events = 1 << 23;
     return t;
 }
 
@@ -106,9 +106,11 @@ static int apply_tuning(esi_handle *h, const esi_tuning &t)
     while ((1 << th_log2) < t.tile_h) ++th_log2;
     h->th_log2 = th_log2;
     // the binning kernel keeps per-warp counters for every tile in shared memory
-    if (bin_smem_bytes(t.chunk_events, h->n_tiles) > 200 * 1024) return ESI_ERANGE;
+    if (bin_smem_bytes(t.chunk_events, h->n_tiles) + 1024 > (size_t)kMaxSmemPerBlock) return ESI_ERANGE;
     const int max_chunks = (t.max_batch_events + t.chunk_events - 1) / t.chunk_events;
-    if (tile_smem_bytes(t.tile_h, t.batch_records, max_chunks) > 200 * 1024) return ESI_ERANGE;
+    if (tile_smem_bytes(t.tile_h, t.batch_records, max_chunks) + tile_static_smem_bytes(t.tile_h) >
+        (size_t)kMaxSmemPerBlock)
+        return ESI_ERANGE;
     return ESI_OK;
 }
 
@@ -303,6 +305,7 @@ int esi_create(int width, int height, const esi_params *params, void *cuda_strea
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->T, (size_t)h->P * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->dstatus, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hstatus, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->hwin_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         rc = cuda_fail(h, e);
         esi_destroy(h);
@@ -333,11 +336,12 @@ void esi_destroy(esi_handle *h)
     cudaFree(h->ring);
     cudaFree(h->rec);
     cudaFree(h->hrow);
-    cudaFree(h->dtframes);
+    cudaFree(h->dwin);
     cudaFree(h->dframes);
     cudaFree(h->dstatus);
     cudaFreeHost(h->hstatus);
-    cudaFreeHost(h->htframes);
+    cudaFreeHost(h->hwin);
+    if (h->hwin_ev) cudaEventDestroy(h->hwin_ev);
     cudaFreeHost(h->hstage);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -571,60 +575,99 @@ int esi::init_state(esi_handle *h)
     return fill_i64(h, h->T, h->P, h->prm.t_origin_us);
 }
 
+namespace {
+struct SubBatch {
+    unsigned long long i0, i1;  // pending-relative event range
+    int w0, w1;                 // frames completed by this launch
+    long long t_base;
+};
+}  // namespace
+
 int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int out_on_device)
 {
     const long long t_last = tf[m - 1];
     const unsigned long long n_split = upper_bound_t(h, h->head, h->tail, t_last) - h->head;
-    int rc = ensure_pinned(h, &h->htframes, &h->htframes_cap, (size_t)m);
-    if (!rc) rc = ensure_device(h, &h->dtframes, &h->dtframes_cap, (size_t)m);
+    const esi_tuning &tu = h->tun;
+    const int chunk = tu.chunk_events;
+    const unsigned long long maxb = (unsigned long long)tu.max_batch_events;
+
+    // plan: sub-batches of at most max_batch_events whose record times fit in
+    // 32 bits; each completes the frames that end before its successor starts
+    std::vector<SubBatch> plan;
+    {
+        unsigned long long i = 0;
+        int w = 0;
+        for (;;) {
+            SubBatch sb;
+            sb.i0 = i;
+            sb.i1 = std::min(n_split, i + maxb);
+            sb.t_base = 0;
+            if (sb.i1 > i) {
+                sb.t_base = mirror_t(h, h->head + i);
+                const long long lim = sb.t_base + 0xffffffffll;
+                const unsigned long long cut = upper_bound_t(h, h->head + i, h->head + sb.i1, lim) - h->head;
+                sb.i1 = std::max(cut, i + 1);
+            } else if (w < m) {
+                sb.t_base = tf[w];
+            }
+            sb.w0 = w;
+            sb.w1 = m;
+            if (sb.i1 < n_split) {
+                const long long tn = mirror_t(h, h->head + sb.i1);
+                sb.w1 = (int)(std::lower_bound(tf + w, tf + m, (int64_t)tn) - tf);
+            }
+            plan.push_back(sb);
+            i = sb.i1;
+            w = sb.w1;
+            if (i >= n_split && w >= m) break;
+        }
+    }
+    // the staging buffer may still feed the previous render's queued copy
+    if (h->hwin_busy) {
+        cudaError_t e0 = cudaEventSynchronize(h->hwin_ev);
+        if (e0 != cudaSuccess) return cuda_fail(h, e0);
+        h->hwin_busy = false;
+    }
+    int rc = ensure_pinned(h, &h->hwin, &h->hwin_cap, (size_t)m);
+    if (!rc) rc = ensure_device(h, &h->dwin, &h->dwin_cap, (size_t)m);
     if (rc) return rc;
-    std::memcpy(h->htframes, tf, (size_t)m * sizeof(long long));
-    cudaError_t e = cudaMemcpyAsync(h->dtframes, h->htframes, (size_t)m * sizeof(long long),
+    for (const SubBatch &sb : plan)
+        for (int w = sb.w0; w < sb.w1; ++w) {
+            const long long d = (long long)tf[w] - sb.t_base;
+            h->hwin[w].lim = std::min(std::max(d, -1ll), 0xffffffffll);
+            h->hwin[w].tf_f = (float)d;
+            h->hwin[w].pad = 0;
+        }
+    cudaError_t e = cudaMemcpyAsync(h->dwin, h->hwin, (size_t)m * sizeof(WinInfo),
                                     cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->hwin_ev, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e);
+    h->hwin_busy = true;
     uint8_t *frames = out;
     if (!out_on_device) {
         rc = ensure_device(h, &h->dframes, &h->dframes_cap, (size_t)m * (size_t)h->P);
         if (rc) return rc;
         frames = h->dframes;
     }
-    const esi_tuning &tu = h->tun;
-    const int chunk = tu.chunk_events;
-    const unsigned long long maxb = (unsigned long long)tu.max_batch_events;
     {
         const size_t max_chunks = (size_t)((maxb + chunk - 1) / chunk);
         rc = ensure_device(h, &h->rec, &h->rec_cap, max_chunks * (size_t)chunk);
         if (!rc) rc = ensure_device(h, &h->hrow, &h->hrow_cap, max_chunks * (size_t)h->n_tiles);
         if (rc) return rc;
     }
-    unsigned long long i = 0;
-    int w = 0;
-    for (;;) {
-        const unsigned long long a0 = h->head + i;
-        unsigned long long i1 = std::min(n_split, i + maxb);
-        long long t_base = 0;
-        if (i1 > i) {
-            t_base = mirror_t(h, a0);
-            // record times are 32-bit offsets from t_base
-            const long long lim = t_base + 0xffffffffll;
-            const unsigned long long cut = upper_bound_t(h, a0, h->head + i1, lim) - h->head;
-            i1 = std::max(cut, i + 1);
-        }
-        int w1 = m;
-        if (i1 < n_split) {
-            const long long tn = mirror_t(h, h->head + i1);
-            w1 = (int)(std::lower_bound(tf + w, tf + m, (int64_t)tn) - tf);
-        }
-        const int nb = (int)(i1 - i);
+    // four-pixel words need 4-byte aligned rows and a 4-byte aligned output
+    const bool vec = (h->W % 4 == 0) && (((uintptr_t)frames & 3u) == 0);
+    for (const SubBatch &sb : plan) {
+        const int nb = (int)(sb.i1 - sb.i0);
         const int n_chunks = (nb + chunk - 1) / chunk;
         if (nb > 0) {
             BinArgs ba;
             ba.ring = h->ring;
             ba.ring_mask = h->cap - 1;
-            ba.first = a0;
+            ba.first = h->head + sb.i0;
             ba.n = nb;
             ba.chunk = chunk;
-            ba.t_base = t_base;
+            ba.t_base = sb.t_base;
             ba.W = h->W;
             ba.H = h->H;
             ba.tiles_x = h->tiles_x;
@@ -645,7 +688,7 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
         ta.n_chunks = n_chunks;
         ta.chunk = chunk;
         ta.n_tiles = h->n_tiles;
-        ta.t_base = t_base;
+        ta.t_base = sb.t_base;
         ta.S = h->S;
         ta.T = h->T;
         ta.W = h->W;
@@ -653,21 +696,18 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
         ta.tiles_x = h->tiles_x;
         ta.dp = h->dp;
         ta.mp = h->mp;
-        ta.t_frames = h->dtframes;
-        ta.w_begin = w;
-        ta.w_end = w1;
+        ta.win = h->dwin;
+        ta.w_begin = sb.w0;
+        ta.w_end = sb.w1;
         ta.frames = frames;
         ta.P = h->P;
         ta.batch = tu.batch_records;
         ta.status = h->dstatus;
         cudaEvent_t ev;
         rc = prof_begin(h, &ev);
-        if (!rc) rc = cuda_fail(h, launch_tile(ta, tu.tile_h, h->stream));
+        if (!rc) rc = cuda_fail(h, launch_tile(ta, tu.tile_h, vec, h->stream));
         if (!rc) rc = prof_end(h, kKindTile, ev);
         if (rc) return rc;
-        i = i1;
-        w = w1;
-        if (i >= n_split && w >= m) break;
     }
     h->head += n_split;
     h->consumed += n_split;

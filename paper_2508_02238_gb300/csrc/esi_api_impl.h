@@ -47,10 +47,12 @@ struct esi_handle {
     size_t rec_cap = 0;
     unsigned int *hrow = nullptr;        // [chunk][tile] run table
     size_t hrow_cap = 0;
-    long long *dtframes = nullptr;
-    size_t dtframes_cap = 0;
-    long long *htframes = nullptr;       // pinned
-    size_t htframes_cap = 0;
+    esi::WinInfo *dwin = nullptr;        // per-frame constants of a render
+    size_t dwin_cap = 0;
+    esi::WinInfo *hwin = nullptr;        // pinned staging of dwin
+    size_t hwin_cap = 0;
+    cudaEvent_t hwin_ev = nullptr;       // the last copy out of hwin
+    bool hwin_busy = false;
     unsigned char *dframes = nullptr;    // frames staged for host outputs
     size_t dframes_cap = 0;
     long long *hstage = nullptr;         // pinned: times of a device push

@@ -140,6 +140,14 @@ __device__ __forceinline__ unsigned block_exclusive_scan(unsigned *data, int n, 
 // accuracy when it is small (dt near the cutoff).
 __device__ __forceinline__ float one_minus_kdt(long long dt, const DecayParams &dp)
 {
+    if (dt < (1ll << 24)) {
+        // dt >= 0 is exact in FP32 here: no 64-bit conversion (slow on this
+        // part) and no low part to carry
+        const float dh = __int2float_rn((int)dt);
+        const float p = dp.k_hi * dh;
+        const float e = fmaf(dp.k_hi, dh, -p);
+        return fmaxf((1.0f - p) - fmaf(dp.k_lo, dh, e), 0.0f);
+    }
     float dh = __ll2float_rn(dt);
     float dl = __ll2float_rn(dt - __float2ll_rn(dh));
     float p = dp.k_hi * dh;
@@ -176,6 +184,46 @@ __device__ __forceinline__ float decay_view(long long dt, const DecayParams &dp)
     case 3: return u * u * u;
     default: return __powf(u, dp.b);
     }
+}
+
+// Decay kinds the kernels are specialised on.
+enum DecayKind { kDecayGeneral = 0, kDecaySquare = 1, kDecayNone = 2 };
+
+// Eq. 4 for the state update, specialised: b = 2 squares, k = 0 gives d = 1.
+template <int DK>
+__device__ __forceinline__ float decay_state_k(long long dt, const DecayParams &dp)
+{
+    if (DK == kDecayNone) return 1.0f;
+    if (DK == kDecaySquare) {
+        if (dt >= dp.cutoff) return 0.0f;
+        const float u = one_minus_kdt(dt, dp);
+        return u * u;
+    }
+    return decay_state(dt, dp);
+}
+
+// Eq. 4 for the render-time view from an FP32 time difference (exact below
+// 2^24 us).  1 - k dt <= 0 gives d = 0; the decision may differ from the FP64
+// one only where d is within rounding of 0, and only the 8-bit code uses it.
+template <int DK>
+__device__ __forceinline__ float decay_view_k(float dt, const DecayParams &dp)
+{
+    if (DK == kDecayNone) return 1.0f;
+    const float u = fmaxf(fmaf(-dp.k_hi, dt, 1.0f), 0.0f);
+    if (DK == kDecaySquare) return u * u;
+    switch (dp.b_mode) {
+    case 1: return u;
+    case 3: return u * u * u;
+    default: return __powf(u, dp.b);
+    }
+}
+
+// Round half to even and saturate to [0, 255] in one conversion.
+__device__ __forceinline__ unsigned quantize_u8(float x)
+{
+    unsigned short r;
+    asm("cvt.rni.sat.u8.f32 %0, %1;" : "=h"(r) : "f"(x));
+    return r;
 }
 
 // Alg. 2 loop body for one event of this pixel, in the paper's order:

@@ -8,7 +8,8 @@
 
 namespace esi {
 
-constexpr int kTileW = 32;  // a tile row is one warp: lane = x within the tile
+constexpr int kTileW = 128;  // a tile row is one warp: lane l owns x = 4l .. 4l + 3
+constexpr int kMaxSmemPerBlock = 227 * 1024;
 
 // Decay of Eq. 4, d(dt) = max(1 - k dt, 0)^b, prepared for the device.
 //   k_hi + k_lo is k per microsecond (k * 1e-6 in double) split into floats so
@@ -56,7 +57,17 @@ struct BinArgs {
     DevStatus *status;
 };
 
-// Arguments of the tile kernel (one block per 32 x TH pixel tile).
+// Per-frame constants of one tile-kernel launch, relative to its t_base:
+// lim = clamp(t_frame - t_base, -1, 2^32 - 1) decides which records are due
+// (record offsets are < 2^32); tf_f = t_frame - t_base in FP32 feeds the
+// render-time decay view.
+struct WinInfo {
+    long long lim;
+    float tf_f;
+    int pad;
+};
+
+// Arguments of the tile kernel (one block per 128 x TH pixel tile).
 struct TileArgs {
     const unsigned long long *rec;
     const unsigned int *hrow;
@@ -69,7 +80,7 @@ struct TileArgs {
     int W, H, tiles_x;
     DecayParams dp;
     MapParams mp;
-    const long long *t_frames;    // frame times of this render (device)
+    const WinInfo *win;           // per-frame constants (device), indexed by frame
     int w_begin, w_end;           // frames this launch completes
     unsigned char *frames;        // frame w at frames + w * P
     long long P;
@@ -78,7 +89,7 @@ struct TileArgs {
 };
 
 // Record layout (8 bytes): low 32 bits t - t_base; high 32 bits
-// (pixel-in-tile << 1) | (p > 0).
+// (pixel-in-tile << 1) | (p > 0), pixel-in-tile = row * 128 + x.
 __host__ __device__ inline unsigned long long make_record(unsigned int toff,
                                                           unsigned int pit,
                                                           unsigned int pos)
@@ -89,8 +100,9 @@ __host__ __device__ inline unsigned long long make_record(unsigned int toff,
 // Launchers (esi_kernels.cu).
 size_t bin_smem_bytes(int chunk, int n_tiles);
 size_t tile_smem_bytes(int tile_h, int batch, int n_chunks);
+size_t tile_static_smem_bytes(int tile_h);
 cudaError_t launch_bin(const BinArgs &a, int n_chunks, cudaStream_t s);
-cudaError_t launch_tile(const TileArgs &a, int tile_h, cudaStream_t s);
+cudaError_t launch_tile(const TileArgs &a, int tile_h, bool vec, cudaStream_t s);
 cudaError_t set_kernel_attributes();
 
 }  // namespace esi

@@ -7,12 +7,13 @@
 //                    (start, count) row.  Events of one tile stay in arrival
 //                    (= time) order: ranks come from warp match_any over warp
 //                    slices that are themselves in order.
-//   esi_tile_kernel  one block per 32 x TH pixel tile, one thread per pixel:
-//                    gathers the tile's runs from every chunk in chunk order
-//                    (so arrival order is kept), stable-sorts each batch by
-//                    row and then by column in shared memory, and lets every
-//                    lane walk its own pixel's events through Alg. 2, emitting
-//                    the Eq. 14 code of its pixel at every frame time.
+//   esi_tile_kernel  one block per 128 x TH pixel tile (one warp per row, four
+//                    pixels per lane): gathers the tile's runs from every
+//                    chunk in chunk order (so arrival order is kept),
+//                    stable-sorts each batch by row and then by lane in shared
+//                    memory, and lets every lane walk its own pixels' events
+//                    through Alg. 2, emitting the Eq. 14 codes of its four
+//                    pixels (one 32-bit store) at every frame time.
 //
 // Per-pixel independence (each pixel's state depends only on its own
 // time-ordered events, Eq. 5 and Alg. 2) is what makes the reorder legal.
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kBinThreads) esi_bin_kernel(BinArgs a)
             const int4 e = sev[k];
             const int x = e.z & 0xffff, y = (int)((unsigned)e.z >> 16);
             if (x < W && y < H)
-                tile = (y >> thl) * tiles_x + (x >> 5);
+                tile = (y >> thl) * tiles_x + (x >> 7);
             else
                 ++drop;
         }
@@ -151,9 +152,9 @@ __global__ void __launch_bounds__(kBinThreads) esi_bin_kernel(BinArgs a)
             const int4 e = sev[k];
             const int x = e.z & 0xffff, y = (int)((unsigned)e.z >> 16);
             if (x < W && y < H) {
-                tile = (y >> thl) * tiles_x + (x >> 5);
+                tile = (y >> thl) * tiles_x + (x >> 7);
                 const long long t = ((long long)(unsigned)e.y << 32) | (unsigned)e.x;
-                const unsigned pit = ((unsigned)(y & th_mask) << 5) | (unsigned)(x & 31);
+                const unsigned pit = ((unsigned)(y & th_mask) << 7) | (unsigned)(x & 127);
                 const bool pos = (signed char)(e.w & 0xff) > 0;
                 rec = make_record((unsigned)(t - a.t_base), pit, pos ? 1u : 0u);
             }
@@ -194,16 +195,38 @@ size_t tile_smem_bytes(int tile_h, int batch, int n_chunks)
     return tile_layout(batch, n_chunks, &a, &b, &c);
 }
 
-template <int TH>
-__global__ void __launch_bounds__(TH * 32, (TH == 32) ? 1 : 2) esi_tile_kernel(TileArgs a)
+// Largest c in [0, n) with pre[c] <= g (pre[0] = 0 <= g < pre[n]).
+__device__ __forceinline__ int run_of(const unsigned *pre, int n, unsigned g)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// One block per 128 x TH tile; warp w owns tile row w, lane l owns the four
+// pixels x = 4l .. 4l + 3 of that row for loads, stores and frame codes.
+// Events are applied event-parallel: a row's records are in time order, so at
+// each frame the due records go 32 at a time, one per lane; lanes holding the
+// same pixel (match_any) apply theirs in arrival order, rank by rank, to the
+// pixel state kept in shared memory.  RD: render_decay; DK: decay kind; VEC:
+// rows start 4-byte aligned (W % 4 == 0), so a lane's four pixels move as one
+// float4 / two longlong2 / one 32-bit frame word.
+template <int TH, int RD, int DK, bool VEC>
+__global__ void __launch_bounds__(TH * 32, (TH * 32 >= 1024) ? 1 : 1024 / (TH * 32))
+esi_tile_kernel(TileArgs a)
 {
     constexpr int NT = TH * 32;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ unsigned short rcnt[TH][TH];   // [warp][row]
-    __shared__ unsigned short xoff[TH][32];   // [row][x]
+    __shared__ unsigned short rcnt[TH][TH];   // [warp][row] counts, then offsets
     __shared__ unsigned rowstart[TH + 1];
     __shared__ unsigned scan_tmp[NT / 32 + 1];
     __shared__ long long s_tnext;
+    __shared__ __align__(16) float sS[TH][kTileW];      // S of the tile's pixels
+    __shared__ __align__(16) float sF[TH][kTileW];      // (float)(T - t_base)
+    __shared__ __align__(16) long long sO[TH][kTileW];  // T - t_base
 
     const int R = a.batch, n_chunks = a.n_chunks;
     size_t off_b, off_runpre, off_runoff;
@@ -215,16 +238,40 @@ __global__ void __launch_bounds__(TH * 32, (TH == 32) ? 1 : 2) esi_tile_kernel(T
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = blockIdx.x;
-    const int x = (tile % a.tiles_x) * 32 + lane;
+    const int x0 = (tile % a.tiles_x) * kTileW + 4 * lane;
     const int y = (tile / a.tiles_x) * TH + warp;
-    const bool inb = x < a.W && y < a.H;
-    const long long pix = (long long)y * a.W + x;
+    const int nval = (y < a.H) ? max(0, min(4, a.W - x0)) : 0;
+    const long long pix0 = (long long)y * a.W + x0;
+    const long long tb = a.t_base;
+    const DecayParams dp = a.dp;
+    const MapParams mp = a.mp;
+    float *rS = sS[warp];
+    float *rF = sF[warp];
+    long long *rO = sO[warp];
 
-    float S = 0.0f;
-    long long T = 0;
-    if (inb) {
-        S = a.S[pix];
-        T = a.T[pix];
+    {
+        float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        long long o4[4] = {0, 0, 0, 0};
+        if (VEC && nval == 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(a.S + pix0);
+            const longlong2 t01 = *reinterpret_cast<const longlong2 *>(a.T + pix0);
+            const longlong2 t23 = *reinterpret_cast<const longlong2 *>(a.T + pix0 + 2);
+            s4[0] = v.x; s4[1] = v.y; s4[2] = v.z; s4[3] = v.w;
+            o4[0] = t01.x - tb; o4[1] = t01.y - tb; o4[2] = t23.x - tb; o4[3] = t23.y - tb;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < nval) {
+                    s4[q] = a.S[pix0 + q];
+                    o4[q] = a.T[pix0 + q] - tb;
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            rS[4 * lane + q] = s4[q];
+            rO[4 * lane + q] = o4[q];
+            rF[4 * lane + q] = RD ? __ll2float_rn(o4[q]) : 0.0f;
+        }
     }
 
     // this tile's run in every chunk, in chunk (= arrival) order
@@ -238,11 +285,27 @@ __global__ void __launch_bounds__(TH * 32, (TH == 32) ? 1 : 2) esi_tile_kernel(T
     if (tid == 0) runpre[n_chunks] = total;
     __syncthreads();
 
-    const DecayParams dp = a.dp;
-    const MapParams mp = a.mp;
-    const long long tb = a.t_base;
-    int wi = a.w_begin;
+    // Alg. 2 for a group of due records (one per valid lane, time order):
+    // S += p C; dt = t - T; S *= d(dt); T = t; clamp (Eq. 13)
+    auto apply_group = [&](unsigned long long r, bool valid) {
+        const int x = (int)((r >> 33) & 127u);
+        const unsigned peers = __match_any_sync(kFull, valid ? x : -1 - lane);
+        const unsigned rank = __popc(peers & lanemask_lt());
+        const unsigned maxr = __reduce_max_sync(kFull, valid ? rank : 0u);
+        for (unsigned k = 0; k <= maxr; ++k) {
+            if (valid && rank == k) {
+                const unsigned toff = (unsigned)r;
+                float s = rS[x] + (((r >> 32) & 1u) ? mp.C : -mp.C);
+                s = s * decay_state_k<DK>((long long)toff - rO[x], dp);
+                rS[x] = fminf(fmaxf(s, mp.s_min), mp.s_max);
+                rO[x] = (long long)toff;
+                if (RD) rF[x] = __uint2float_rn(toff);
+            }
+            __syncwarp();
+        }
+    };
 
+    int wi = a.w_begin;
     for (unsigned b0 = 0;; b0 += (unsigned)R) {
         const int nb = (int)min((unsigned)R, total - min(total, b0));
         const bool last = b0 + (unsigned)R >= total;
@@ -250,35 +313,28 @@ __global__ void __launch_bounds__(TH * 32, (TH == 32) ? 1 : 2) esi_tile_kernel(T
         // gather the batch (records b0 .. b0 + nb of this tile, arrival order)
         for (int i = tid; i < nb; i += NT) {
             const unsigned g = b0 + (unsigned)i;
-            int lo = 0, hi = n_chunks;  // largest c with runpre[c] <= g
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (runpre[mid] <= g) lo = mid; else hi = mid;
-            }
-            A[i] = a.rec[(size_t)lo * a.chunk + runoff[lo] + (g - runpre[lo])];
+            const int c = run_of(runpre, n_chunks, g);
+            A[i] = a.rec[(size_t)c * a.chunk + runoff[c] + (g - runpre[c])];
         }
         if (tid == 0) {
             long long tn = 0x7fffffffffffffffll;
             if (!last) {
                 const unsigned g = b0 + (unsigned)R;
-                int lo = 0, hi = n_chunks;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (runpre[mid] <= g) lo = mid; else hi = mid;
-                }
-                tn = (long long)(unsigned)a.rec[(size_t)lo * a.chunk + runoff[lo] + (g - runpre[lo])];
+                const int c = run_of(runpre, n_chunks, g);
+                tn = (long long)(unsigned)a.rec[(size_t)c * a.chunk + runoff[c] + (g - runpre[c])];
             }
             s_tnext = tn;
         }
         for (int i = tid; i < TH * TH; i += NT) (&rcnt[0][0])[i] = 0;
         __syncthreads();
 
-        // level 1: stable counting sort of the batch by row (A -> B)
+        // stable counting sort of the batch by row (A -> B): each row's
+        // records stay in arrival (= time) order
         const int sl = (nb + TH - 1) / TH;
         const int s0 = min(warp * sl, nb), s1 = min(s0 + sl, nb);
         for (int base = s0; base < s1; base += 32) {
             const int k = base + lane;
-            const int row = (k < s1) ? (int)(A[k] >> 38) : -1;
+            const int row = (k < s1) ? (int)(A[k] >> 40) : -1;
             const unsigned m = __match_any_sync(kFull, row);
             if (row >= 0 && (m & lanemask_lt()) == 0) rcnt[warp][row] += (unsigned short)__popc(m);
         }
@@ -301,7 +357,7 @@ __global__ void __launch_bounds__(TH * 32, (TH == 32) ? 1 : 2) esi_tile_kernel(T
             int row = -1;
             if (k < s1) {
                 r = A[k];
-                row = (int)(r >> 38);
+                row = (int)(r >> 40);
             }
             const unsigned m = __match_any_sync(kFull, row);
             const unsigned rank = __popc(m & lanemask_lt());
@@ -312,82 +368,126 @@ __global__ void __launch_bounds__(TH * 32, (TH == 32) ? 1 : 2) esi_tile_kernel(T
         }
         __syncthreads();
 
-        // level 2: warp `warp` sorts its row by column (B -> A), stable
-        const int rs = (int)rowstart[warp], re = (int)rowstart[warp + 1];
-        xoff[warp][lane] = 0;
-        __syncwarp();
-        for (int base = rs; base < re; base += 32) {
-            const int k = base + lane;
-            const int xx = (k < re) ? (int)((B[k] >> 33) & 31u) : -1;
-            const unsigned m = __match_any_sync(kFull, xx);
-            if (xx >= 0 && (m & lanemask_lt()) == 0) xoff[warp][xx] += (unsigned short)__popc(m);
-        }
-        __syncwarp();
-        const unsigned mycnt = xoff[warp][lane];
-        const unsigned myoff = (unsigned)rs + warp_inclusive_scan(mycnt) - mycnt;
-        __syncwarp();
-        xoff[warp][lane] = (unsigned short)myoff;
-        __syncwarp();
-        for (int base = rs; base < re; base += 32) {
-            const int k = base + lane;
-            unsigned long long r = 0;
-            int xx = -1;
-            if (k < re) {
-                r = B[k];
-                xx = (int)((r >> 33) & 31u);
-            }
-            const unsigned m = __match_any_sync(kFull, xx);
-            const unsigned rank = __popc(m & lanemask_lt());
-            if (xx >= 0) A[xoff[warp][xx] + rank] = r;
-            __syncwarp();
-            if (xx >= 0 && rank == 0) xoff[warp][xx] += (unsigned short)__popc(m);
-            __syncwarp();
-        }
-        __syncwarp();
-
-        // walk: this lane's events of the batch, A[myoff .. myoff + mycnt)
-        int cur = (int)myoff;
-        const int end = (int)(myoff + mycnt);
+        // walk this warp's row, frame by frame
+        int cur = (int)rowstart[warp];
+        const int re = (int)rowstart[warp + 1];
         const long long tnext = s_tnext;
         while (wi < a.w_end) {
-            const long long tf_abs = a.t_frames[wi];
-            const long long tf = tf_abs - tb;
-            if (tf >= tnext) break;  // later records of this tile may still be <= tf
-            while (cur < end) {
-                const unsigned long long r = A[cur];
-                const long long t = (long long)(unsigned)r;
-                if (t > tf) break;
-                esi_apply(S, T, tb + t, (r >> 32) & 1u, dp, mp);
-                ++cur;
+            const WinInfo wv = a.win[wi];
+            if (wv.lim >= tnext) break;  // later records of this tile may be due
+            for (;;) {
+                const int k = cur + lane;
+                unsigned long long r = 0;
+                bool valid = false;
+                if (k < re) {
+                    r = B[k];
+                    valid = (long long)(unsigned)r <= wv.lim;
+                }
+                const unsigned vm = __ballot_sync(kFull, valid);
+                if (vm == 0u) break;
+                apply_group(r, valid);
+                const int nv = __popc(vm);
+                cur += nv;
+                if (nv < 32) break;
             }
-            if (inb) a.frames[(long long)wi * a.P + pix] = esi_pixel_code(S, T, tf_abs, dp, mp);
+            // Eq. 14 codes of the lane's four pixels at this frame
+            const float4 s4 = *reinterpret_cast<const float4 *>(rS + 4 * lane);
+            float v[4] = {s4.x, s4.y, s4.z, s4.w};
+            if (RD) {
+                const float4 f4 = *reinterpret_cast<const float4 *>(rF + 4 * lane);
+                v[0] *= decay_view_k<DK>(wv.tf_f - f4.x, dp);
+                v[1] *= decay_view_k<DK>(wv.tf_f - f4.y, dp);
+                v[2] *= decay_view_k<DK>(wv.tf_f - f4.z, dp);
+                v[3] *= decay_view_k<DK>(wv.tf_f - f4.w, dp);
+            }
+            unsigned code[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) code[q] = quantize_u8(fmaf(v[q], mp.scale, mp.offs));
+            unsigned char *fr = a.frames + (long long)wi * a.P + pix0;
+            if (VEC) {
+                if (nval == 4)
+                    *reinterpret_cast<unsigned *>(fr) =
+                        code[0] | (code[1] << 8) | (code[2] << 16) | (code[3] << 24);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q < nval) fr[q] = (unsigned char)code[q];
+            }
             ++wi;
         }
-        while (cur < end) {
-            const unsigned long long r = A[cur];
-            esi_apply(S, T, tb + (long long)(unsigned)r, (r >> 32) & 1u, dp, mp);
-            ++cur;
+        // the rest of this batch's row precedes the next batch's records
+        for (; cur < re; cur += 32) {
+            const int k = cur + lane;
+            const bool valid = k < re;
+            apply_group(valid ? B[k] : 0ull, valid);
         }
         if (last) break;
         __syncthreads();  // A, B, rcnt are rewritten by the next batch
     }
-    if (inb) {
-        a.S[pix] = S;
-        a.T[pix] = T;
+
+    __syncwarp();
+    if (VEC && nval == 4) {
+        const float4 s4 = *reinterpret_cast<const float4 *>(rS + 4 * lane);
+        *reinterpret_cast<float4 *>(a.S + pix0) = s4;
+        *reinterpret_cast<longlong2 *>(a.T + pix0) =
+            make_longlong2(rO[4 * lane] + tb, rO[4 * lane + 1] + tb);
+        *reinterpret_cast<longlong2 *>(a.T + pix0 + 2) =
+            make_longlong2(rO[4 * lane + 2] + tb, rO[4 * lane + 3] + tb);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (q < nval) {
+                a.S[pix0 + q] = rS[4 * lane + q];
+                a.T[pix0 + q] = rO[4 * lane + q] + tb;
+            }
     }
+}
+
+#define ESI_TILE_VARIANTS(TH)                                                     \
+    X(TH, 0, kDecayGeneral, false) X(TH, 0, kDecayGeneral, true)                  \
+    X(TH, 0, kDecaySquare, false) X(TH, 0, kDecaySquare, true)                    \
+    X(TH, 0, kDecayNone, false) X(TH, 0, kDecayNone, true)                        \
+    X(TH, 1, kDecayGeneral, false) X(TH, 1, kDecayGeneral, true)                  \
+    X(TH, 1, kDecaySquare, false) X(TH, 1, kDecaySquare, true)                    \
+    X(TH, 1, kDecayNone, false) X(TH, 1, kDecayNone, true)
+
+static int decay_kind(const DecayParams &dp)
+{
+    if (dp.b_mode == 4) return kDecayNone;
+    if (dp.b_mode == 2) return kDecaySquare;
+    return kDecayGeneral;
+}
+
+// Dynamic shared memory a kernel may ask for: the 227 KB per block minus its
+// static part.
+template <class K>
+static cudaError_t allow_dynamic_smem(K kernel)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const int max_dyn = kMaxSmemPerBlock - (int)fa.sharedSizeBytes;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
+}
+
+size_t tile_static_smem_bytes(int tile_h)
+{
+    // pixel state (S, F, O per pixel) and the sort scratch
+    return (size_t)tile_h * kTileW * 16 + (size_t)tile_h * tile_h * 2 + 1024;
 }
 
 cudaError_t set_kernel_attributes()
 {
-    cudaError_t e;
-    const int max_dyn = 200 * 1024;
-    e = cudaFuncSetAttribute(esi_bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
+    cudaError_t e = allow_dynamic_smem(esi_bin_kernel);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(esi_tile_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
+#define X(TH, RD, DK, V)                                                                    \
+    e = allow_dynamic_smem(esi_tile_kernel<TH, RD, DK, V>);                                 \
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(esi_tile_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(esi_tile_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
+    ESI_TILE_VARIANTS(8)
+    ESI_TILE_VARIANTS(16)
+    ESI_TILE_VARIANTS(32)
+#undef X
+    return cudaSuccess;
 }
 
 cudaError_t launch_bin(const BinArgs &a, int n_chunks, cudaStream_t s)
@@ -397,16 +497,23 @@ cudaError_t launch_bin(const BinArgs &a, int n_chunks, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile(const TileArgs &a, int tile_h, cudaStream_t s)
+cudaError_t launch_tile(const TileArgs &a, int tile_h, bool vec, cudaStream_t s)
 {
     const size_t smem = tile_smem_bytes(tile_h, a.batch, a.n_chunks);
-    switch (tile_h) {
-    case 8: esi_tile_kernel<8><<<a.n_tiles, 8 * 32, smem, s>>>(a); break;
-    case 16: esi_tile_kernel<16><<<a.n_tiles, 16 * 32, smem, s>>>(a); break;
-    default: esi_tile_kernel<32><<<a.n_tiles, 32 * 32, smem, s>>>(a); break;
+    const int rd = a.mp.render_decay ? 1 : 0;
+    const int dk = decay_kind(a.dp);
+#define X(TH, RD, DK, V)                                                          \
+    if (tile_h == TH && rd == RD && dk == DK && vec == V) {                       \
+        esi_tile_kernel<TH, RD, DK, V><<<a.n_tiles, TH * 32, smem, s>>>(a);       \
+        return cudaGetLastError();                                                \
     }
-    return cudaGetLastError();
+    ESI_TILE_VARIANTS(8)
+    ESI_TILE_VARIANTS(16)
+    ESI_TILE_VARIANTS(32)
+#undef X
+    return cudaErrorInvalidValue;
 }
+
 
 }  // namespace esi
 

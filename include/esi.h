@@ -193,6 +193,44 @@ void esi_destroy(esi_handle *h);
 /* Static text for an ESI_* code. */
 const char *esi_strerror(int code);
 
+/* ---------------------------------------------- allocation-free render */
+
+/*
+ * The paper has no counterpart to this call; it is an interface of this
+ * library.  It renders like esi_render_frames but allocates no memory at all,
+ * for callers that cannot allocate device memory: applications that reserve
+ * the GPU's memory up front in their own pool and forbid any other
+ * allocation, plugins that must not go around their host framework's
+ * allocator, and real-time loops in which cudaMalloc / cudaFree, which may
+ * synchronise the whole device, would stall other work.
+ *
+ * The scratch it needs (binned records, run table, per-frame constants,
+ * status) lives in one fixed device array of about 12.2 MB that every GPU
+ * which loads this library holds until the process exits.  The first call on
+ * each device sets that device up (it looks up the array's device address and
+ * the kernels' shared-memory limits, with that device current); make that
+ * first call before any stream capture.  All calls share the array, so calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.  The call waits for its own work.
+ *
+ * Inputs and outputs, all owned by the caller:
+ *   events    device array of n events, non-decreasing in time, none later
+ *             than t_frames[m-1] (ESI_EINVAL) or earlier than its pixel's T
+ *             (ESI_ETIMEORDER); out-of-range pixels are skipped.  n may be 0.
+ *   t_frames  host array of m non-decreasing frame times.
+ *   S, T      device arrays of W * H float32 / int64: the state, read and
+ *             updated in place (start from S = 0, T = t_origin).
+ *   frames    device array of m * W * H bytes, frame w at offset w * W * H.
+ * Limits (ESI_ERANGE beyond them): n <= 1048576 events, m <= 4096 frames,
+ * ceil(W / 128) * ceil(H / 8) <= 2048 pixel tiles, and the last event at
+ * most 2^32 - 1 us after the first.  params as for esi_create; render_decay
+ * is honoured.
+ */
+int esi_render_frames_noalloc(int width, int height, const esi_params *params,
+                              const esi_event *events, size_t n,
+                              const int64_t *t_frames, size_t m, float *S,
+                              int64_t *T, uint8_t *frames, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

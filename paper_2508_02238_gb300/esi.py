@@ -68,6 +68,8 @@ SIGNATURES = {
     "esi_profile_reset": (_i32, [_P]),
     "esi_destroy": (None, [_P]),
     "esi_strerror": (ctypes.c_char_p, [_i32]),
+    "esi_render_frames_noalloc": (_i32, [_i32, _i32, ctypes.POINTER(esi_params), _P, _sz, _P,
+                                         _sz, _P, _P, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -179,6 +181,14 @@ def esi_profile_read(h, max_entries: int = 16):
 
 def esi_profile_reset(h) -> int:
     return _fn("esi_profile_reset")(h)
+
+
+def esi_render_frames_noalloc(width: int, height: int, params: esi_params, events, n: int,
+                              t_frames, m: int, S, T, frames, cuda_stream=0) -> int:
+    return _fn("esi_render_frames_noalloc")(
+        int(width), int(height), ctypes.byref(params), _P(ptr(events) or None), int(n),
+        _P(ptr(t_frames) or None), int(m), _P(ptr(S) or None), _P(ptr(T) or None),
+        _P(ptr(frames) or None), _P(int(cuda_stream) or None))
 
 
 def esi_destroy(h) -> None:

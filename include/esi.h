@@ -91,7 +91,7 @@ typedef struct {
 
 /*
  * Launch-shape knobs (all 0 = library default).  tile_h: rows per pixel
- * tile (8, 16 or 32; tiles are 128 pixels wide).  chunk_events: events per
+ * tile (4, 8, 16 or 32; tiles are 128 pixels wide).  chunk_events: events per
  * binning block (power of two, 512..8192).  batch_records: records a tile
  * sorts in shared memory at once (power of two, 1024..8192).
  * max_batch_events: events per binning pass of a render (>= chunk_events).

@@ -74,7 +74,7 @@ void prepare_params(const esi_params &p, DecayParams *dp, MapParams *mp)
 int validate_tuning(const esi_tuning &t)
 {
     auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
-    if (t.tile_h != 8 && t.tile_h != 16 && t.tile_h != 32) return ESI_EINVAL;
+    if (t.tile_h != 4 && t.tile_h != 8 && t.tile_h != 16 && t.tile_h != 32) return ESI_EINVAL;
     if (!pow2(t.chunk_events) || t.chunk_events < 512 || t.chunk_events > 8192) return ESI_EINVAL;
     if (!pow2(t.batch_records) || t.batch_records < 1024 || t.batch_records > 8192) return ESI_EINVAL;
     if (t.max_batch_events < t.chunk_events) return ESI_EINVAL;
@@ -89,7 +89,7 @@ esi_tuning default_tuning(int W, int H)
     t.tile_h = 8;
     t.chunk_events = 2048;
     t.batch_records = 4096;
-    t.max_batch_events = 1 << 23;
+    t.max_batch_events = 1 << 21;
     return t;
 }
 
@@ -114,14 +114,21 @@ static int apply_tuning(esi_handle *h, const esi_tuning &t)
     return ESI_OK;
 }
 
+int esi::sync_all(esi_handle *h)
+{
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && h->bin_stream) e = cudaStreamSynchronize(h->bin_stream);
+    return cuda_fail(h, e);
+}
+
 template <class T>
 static int ensure_device(esi_handle *h, T **p, size_t *cap, size_t need)
 {
     if (need <= *cap) return ESI_OK;
     size_t nc = std::max(need, *cap * 2);
     if (*p) {
-        cudaError_t e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e);
+        int rc = sync_all(h);
+        if (rc) return rc;
         cudaFree(*p);
         *p = nullptr;
         *cap = 0;
@@ -138,8 +145,8 @@ static int ensure_pinned(esi_handle *h, T **p, size_t *cap, size_t need)
     if (need <= *cap) return ESI_OK;
     size_t nc = std::max(need, *cap * 2);
     if (*p) {
-        cudaError_t e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e);
+        int rc = sync_all(h);
+        if (rc) return rc;
         cudaFreeHost(*p);
         *p = nullptr;
         *cap = 0;
@@ -231,20 +238,20 @@ static cudaEvent_t prof_event(esi_handle *h)
     return e;
 }
 
-int esi::prof_begin(esi_handle *h, cudaEvent_t *ev)
+int esi::prof_begin(esi_handle *h, cudaEvent_t *ev, cudaStream_t s)
 {
     *ev = nullptr;
     if (!h->prof_on) return ESI_OK;
     *ev = prof_event(h);
-    return cuda_fail(h, cudaEventRecord(*ev, h->stream));
+    return cuda_fail(h, cudaEventRecord(*ev, s));
 }
 
-int esi::prof_end(esi_handle *h, int kind, cudaEvent_t start)
+int esi::prof_end(esi_handle *h, int kind, cudaEvent_t start, cudaStream_t s)
 {
     h->launches += 1;
     if (!h->prof_on || !start) return ESI_OK;
     cudaEvent_t stop = prof_event(h);
-    cudaError_t e = cudaEventRecord(stop, h->stream);
+    cudaError_t e = cudaEventRecord(stop, s);
     h->prof_recs.push_back({kind, start, stop});
     return cuda_fail(h, e);
 }
@@ -306,6 +313,12 @@ int esi_create(int width, int height, const esi_params *params, void *cuda_strea
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->dstatus, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hstatus, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->hwin_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->bin_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaEventCreateWithFlags(&h->ev_bin[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_tile[b], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         rc = cuda_fail(h, e);
         esi_destroy(h);
@@ -326,6 +339,7 @@ void esi_destroy(esi_handle *h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->bin_stream) cudaStreamSynchronize(h->bin_stream);
     for (auto &r : h->prof_recs) {
         cudaEventDestroy(r.start);
         cudaEventDestroy(r.stop);
@@ -334,8 +348,14 @@ void esi_destroy(esi_handle *h)
     cudaFree(h->S);
     cudaFree(h->T);
     cudaFree(h->ring);
-    cudaFree(h->rec);
-    cudaFree(h->hrow);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(h->rec[b]);
+        cudaFree(h->hrow[b]);
+        if (h->ev_bin[b]) cudaEventDestroy(h->ev_bin[b]);
+        if (h->ev_tile[b]) cudaEventDestroy(h->ev_tile[b]);
+    }
+    if (h->ev_start) cudaEventDestroy(h->ev_start);
+    if (h->bin_stream) cudaStreamDestroy(h->bin_stream);
     cudaFree(h->dwin);
     cudaFree(h->dframes);
     cudaFree(h->dstatus);
@@ -520,8 +540,8 @@ int esi_profile_enable(esi_handle *h, int enable)
 int esi_profile_read(esi_handle *h, esi_kernel_time *out, int max)
 {
     if (!h || max < 0 || (max > 0 && !out)) return ESI_EINVAL;
-    cudaError_t e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e);
+    int src = sync_all(h);
+    if (src) return src;
     for (auto &r : h->prof_recs) {
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, r.start, r.stop);
@@ -550,7 +570,7 @@ int esi_profile_read(esi_handle *h, esi_kernel_time *out, int max)
 int esi_profile_reset(esi_handle *h)
 {
     if (!h) return ESI_EINVAL;
-    cudaError_t e = cudaStreamSynchronize(h->stream);
+    int src = sync_all(h);
     for (auto &r : h->prof_recs) {
         h->ev_pool.push_back(r.start);
         h->ev_pool.push_back(r.stop);
@@ -560,7 +580,7 @@ int esi_profile_reset(esi_handle *h)
         h->prof_ms[k] = 0.0;
         h->prof_n[k] = 0;
     }
-    return cuda_fail(h, e);
+    return src;
 }
 
 }  // extern "C"
@@ -649,18 +669,29 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
         if (rc) return rc;
         frames = h->dframes;
     }
-    {
+    for (int b = 0; b < 2 && b < (int)plan.size(); ++b) {
         const size_t max_chunks = (size_t)((maxb + chunk - 1) / chunk);
-        rc = ensure_device(h, &h->rec, &h->rec_cap, max_chunks * (size_t)chunk);
-        if (!rc) rc = ensure_device(h, &h->hrow, &h->hrow_cap, max_chunks * (size_t)h->n_tiles);
+        rc = ensure_device(h, &h->rec[b], &h->rec_cap[b], max_chunks * (size_t)chunk);
+        if (!rc) rc = ensure_device(h, &h->hrow[b], &h->hrow_cap[b], max_chunks * (size_t)h->n_tiles);
         if (rc) return rc;
     }
+    // binning may start once everything queued before this render (pushes) is done
+    e = cudaEventRecord(h->ev_start, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->bin_stream, h->ev_start, 0);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    int sbi = 0;
     // four-pixel words need 4-byte aligned rows and a 4-byte aligned output
     const bool vec = (h->W % 4 == 0) && (((uintptr_t)frames & 3u) == 0);
     for (const SubBatch &sb : plan) {
         const int nb = (int)(sb.i1 - sb.i0);
         const int n_chunks = (nb + chunk - 1) / chunk;
+        const int buf = sbi++ & 1;
         if (nb > 0) {
+            // the buffer's previous tile kernel must be done reading it
+            if (h->tile_pending[buf]) {
+                e = cudaStreamWaitEvent(h->bin_stream, h->ev_tile[buf], 0);
+                if (e != cudaSuccess) return cuda_fail(h, e);
+            }
             BinArgs ba;
             ba.ring = h->ring;
             ba.ring_mask = h->cap - 1;
@@ -673,18 +704,21 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
             ba.tiles_x = h->tiles_x;
             ba.n_tiles = h->n_tiles;
             ba.th_log2 = h->th_log2;
-            ba.rec = h->rec;
-            ba.hrow = h->hrow;
+            ba.tile_bits = index_bits(h->n_tiles);
+            ba.rec = h->rec[buf];
+            ba.hrow = h->hrow[buf];
             ba.status = h->dstatus;
             cudaEvent_t ev;
-            rc = prof_begin(h, &ev);
-            if (!rc) rc = cuda_fail(h, launch_bin(ba, n_chunks, h->stream));
-            if (!rc) rc = prof_end(h, kKindBin, ev);
+            rc = prof_begin(h, &ev, h->bin_stream);
+            if (!rc) rc = cuda_fail(h, launch_bin(ba, n_chunks, h->bin_stream));
+            if (!rc) rc = prof_end(h, kKindBin, ev, h->bin_stream);
+            if (!rc) rc = cuda_fail(h, cudaEventRecord(h->ev_bin[buf], h->bin_stream));
+            if (!rc) rc = cuda_fail(h, cudaStreamWaitEvent(h->stream, h->ev_bin[buf], 0));
             if (rc) return rc;
         }
         TileArgs ta;
-        ta.rec = h->rec;
-        ta.hrow = h->hrow;
+        ta.rec = h->rec[buf];
+        ta.hrow = h->hrow[buf];
         ta.n_chunks = n_chunks;
         ta.chunk = chunk;
         ta.n_tiles = h->n_tiles;
@@ -704,10 +738,12 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
         ta.batch = tu.batch_records;
         ta.status = h->dstatus;
         cudaEvent_t ev;
-        rc = prof_begin(h, &ev);
+        rc = prof_begin(h, &ev, h->stream);
         if (!rc) rc = cuda_fail(h, launch_tile(ta, tu.tile_h, vec, h->stream));
-        if (!rc) rc = prof_end(h, kKindTile, ev);
+        if (!rc) rc = prof_end(h, kKindTile, ev, h->stream);
+        if (!rc) rc = cuda_fail(h, cudaEventRecord(h->ev_tile[buf], h->stream));
         if (rc) return rc;
+        h->tile_pending[buf] = true;
     }
     h->head += n_split;
     h->consumed += n_split;
@@ -726,8 +762,8 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
 int esi::fill_i64(esi_handle *h, long long *dst, long long n, long long value)
 {
     cudaEvent_t ev;
-    int rc = prof_begin(h, &ev);
+    int rc = prof_begin(h, &ev, h->stream);
     if (!rc) rc = cuda_fail(h, launch_fill_i64(dst, n, value, h->stream));
-    if (!rc) rc = prof_end(h, kKindFill, ev);
+    if (!rc) rc = prof_end(h, kKindFill, ev, h->stream);
     return rc;
 }

@@ -43,10 +43,18 @@ struct esi_handle {
     unsigned long long cap = 0, head = 0, tail = 0;
     std::vector<long long> tmirror;
 
-    unsigned long long *rec = nullptr;   // binned records of one sub-batch
-    size_t rec_cap = 0;
-    unsigned int *hrow = nullptr;        // [chunk][tile] run table
-    size_t hrow_cap = 0;
+    // binning of sub-batch i + 1 overlaps the tile kernel of sub-batch i:
+    // it runs on bin_stream into the other half of the double-buffered
+    // scratch; events order it against the handle's stream
+    cudaStream_t bin_stream = nullptr;
+    cudaEvent_t ev_start = nullptr;      // render's work may begin (handle stream)
+    cudaEvent_t ev_bin[2] = {nullptr, nullptr};
+    cudaEvent_t ev_tile[2] = {nullptr, nullptr};
+    bool tile_pending[2] = {false, false};
+    unsigned long long *rec[2] = {nullptr, nullptr};   // binned records of a sub-batch
+    size_t rec_cap[2] = {0, 0};
+    unsigned int *hrow[2] = {nullptr, nullptr};        // [chunk][tile] run table
+    size_t hrow_cap[2] = {0, 0};
     esi::WinInfo *dwin = nullptr;        // per-frame constants of a render
     size_t dwin_cap = 0;
     esi::WinInfo *hwin = nullptr;        // pinned staging of dwin
@@ -85,8 +93,9 @@ void prepare_params(const esi_params &p, DecayParams *dp, MapParams *mp);
 int validate_tuning(const esi_tuning &t);
 esi_tuning default_tuning(int W, int H);
 int read_status(esi_handle *h);
-int prof_begin(esi_handle *h, cudaEvent_t *ev);
-int prof_end(esi_handle *h, int kind, cudaEvent_t start);
+int prof_begin(esi_handle *h, cudaEvent_t *ev, cudaStream_t s);
+int prof_end(esi_handle *h, int kind, cudaEvent_t start, cudaStream_t s);
+int sync_all(esi_handle *h);
 int init_state(esi_handle *h);
 int render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int out_on_device);
 int fill_i64(esi_handle *h, long long *dst, long long n, long long value);

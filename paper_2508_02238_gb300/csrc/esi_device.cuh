@@ -69,6 +69,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
     return ok != 0;
 }
 
+// Asynchronous 8-byte global -> shared copy (no register round trip), and
+// the wait for all of this thread's outstanding ones.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Wait for phase `phase` of `bar` for at most limit_ns; false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase,
                                                   unsigned long long limit_ns)
@@ -78,6 +91,32 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase,
         if (global_ns() - t0 > limit_ns) return false;
     }
     return true;
+}
+
+// Lanes of the warp holding the same key (lanes with valid == false never
+// match).  One ballot per key bit: much cheaper here than match.any.
+__device__ __forceinline__ unsigned warp_peers(unsigned key, int nbits, bool valid)
+{
+    unsigned m = __ballot_sync(kFull, valid);
+    for (int b = 0; b < nbits; ++b) {
+        const bool bit = (key >> b) & 1u;
+        const unsigned v = __ballot_sync(kFull, bit);
+        m &= bit ? v : ~v;
+    }
+    return m;
+}
+
+template <int NBITS>
+__device__ __forceinline__ unsigned warp_peers_n(unsigned key, bool valid)
+{
+    unsigned m = __ballot_sync(kFull, valid);
+#pragma unroll
+    for (int b = 0; b < NBITS; ++b) {
+        const bool bit = (key >> b) & 1u;
+        const unsigned v = __ballot_sync(kFull, bit);
+        m &= bit ? v : ~v;
+    }
+    return m;
 }
 
 // ------------------------------------------------------------------- scans

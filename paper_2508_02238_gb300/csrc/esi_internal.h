@@ -52,6 +52,7 @@ struct BinArgs {
     long long t_base;             // record times are t - t_base (< 2^32)
     int W, H, tiles_x, n_tiles;
     int th_log2;                  // log2 of rows per tile
+    int tile_bits;                // bits of a tile index (n_tiles <= 2^tile_bits)
     unsigned long long *rec;      // out: records, block c at rec + c * chunk
     unsigned int *hrow;           // out: [chunk][tile] (start << 16 | count)
     DevStatus *status;
@@ -95,6 +96,14 @@ __host__ __device__ inline unsigned long long make_record(unsigned int toff,
                                                           unsigned int pos)
 {
     return (unsigned long long)toff | ((unsigned long long)((pit << 1) | pos) << 32);
+}
+
+// Bits needed to hold indices 0 .. n-1 (at least 1).
+inline int index_bits(int n)
+{
+    int b = 1;
+    while ((1 << b) < n) ++b;
+    return b;
 }
 
 // Launchers (esi_kernels.cu).

@@ -26,6 +26,7 @@
 namespace esi {
 
 constexpr int kBinThreads = 256;
+constexpr int kStageFrames = 256;   // per-frame constants a tile block keeps in shared memory
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
 constexpr int kWhereBinCopy = 1;
 
@@ -44,6 +45,8 @@ static __host__ __device__ inline size_t bin_layout(int chunk, int n_tiles, size
     o += (size_t)round_up(n_tiles + 1, 4) * 4;     // tile starts (+ total)
     *off_cnt = o;
     o += (size_t)NW * round_up(n_tiles, 8) * 2;    // per-warp tile counters
+    o += (size_t)chunk * 2;                        // event: offset within its warp's tile run
+    o += (size_t)chunk * 2;                        // event: tile (0xffff = dropped)
     return o;
 }
 
@@ -69,6 +72,8 @@ __global__ void __launch_bounds__(kBinThreads) esi_bin_kernel(BinArgs a)
     unsigned long long *ssort = reinterpret_cast<unsigned long long *>(smem + off_sort);
     unsigned *tstart = reinterpret_cast<unsigned *>(smem + off_tstart);
     unsigned short *cnt = reinterpret_cast<unsigned short *>(smem + off_cnt);
+    unsigned short *loff = cnt + NW * ntp;
+    unsigned short *ltile = loff + chunk;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long c0 = (long long)blockIdx.x * chunk;
@@ -88,23 +93,29 @@ __global__ void __launch_bounds__(kBinThreads) esi_bin_kernel(BinArgs a)
         bulk_g2s(sev, a.ring + r0, (unsigned)n1 * 16u, &bar);
         if (n1 < nc) bulk_g2s(sev + n1, a.ring, (unsigned)(nc - n1) * 16u, &bar);
     }
+    __shared__ int s_copy_ok;
     for (int i = tid; i < NW * ntp; i += NT) cnt[i] = 0;
-    __syncthreads();
-    if (!mbar_wait_bounded(&bar, 0, kWaitLimitNs)) {
-        // never read a partial chunk: report, give the copy one more bounded
-        // wait so it does not land in reassigned shared memory, and leave
-        set_error(a.status, ESI_ETIMEOUT, kWhereBinCopy);
-        mbar_wait_bounded(&bar, 0, kWaitLimitNs);
-        return;
+    if (tid == 0) {
+        // one thread waits for the copy; the others sleep at the barrier
+        int ok = mbar_wait_bounded(&bar, 0, kWaitLimitNs) ? 1 : 0;
+        if (!ok) {
+            // never read a partial chunk: report, give the copy one more
+            // bounded wait so it does not land in reassigned shared memory
+            set_error(a.status, ESI_ETIMEOUT, kWhereBinCopy);
+            mbar_wait_bounded(&bar, 0, kWaitLimitNs);
+        }
+        s_copy_ok = ok;
     }
+    __syncthreads();
+    if (!s_copy_ok) return;
 
-    const int W = a.W, H = a.H, tiles_x = a.tiles_x, thl = a.th_log2;
-    const int th_mask = (1 << thl) - 1;
+    const int W = a.W, H = a.H, tiles_x = a.tiles_x, thl = a.th_log2, tbits = a.tile_bits;
     const int per = chunk / NW;
     const int s0 = warp * per;
     const int s1 = min(s0 + per, nc);
 
-    // phase 1: per-warp tile counts
+    // phase 1: in arrival order, each warp ranks its slice's events within
+    // their tile (peers by ballot), keeping the offset inside its own run
     unsigned drop = 0;
     for (int base = s0; base < s1; base += 32) {
         const int k = base + lane;
@@ -117,8 +128,17 @@ __global__ void __launch_bounds__(kBinThreads) esi_bin_kernel(BinArgs a)
             else
                 ++drop;
         }
-        const unsigned m = __match_any_sync(kFull, tile);
-        if (tile >= 0 && (m & lanemask_lt()) == 0) cnt[warp * ntp + tile] += (unsigned short)__popc(m);
+        const bool valid = tile >= 0;
+        const unsigned peers = warp_peers((unsigned)tile, tbits, valid);
+        const unsigned rank = __popc(peers & lanemask_lt());
+        const unsigned pre = valid ? cnt[warp * ntp + tile] : 0u;
+        __syncwarp();
+        if (valid && rank == 0) cnt[warp * ntp + tile] = (unsigned short)(pre + __popc(peers));
+        if (k < s1) {
+            loff[k] = (unsigned short)(pre + rank);
+            ltile[k] = valid ? (unsigned short)tile : (unsigned short)0xffff;
+        }
+        __syncwarp();
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) drop += __shfl_xor_sync(kFull, drop, o);
@@ -143,28 +163,19 @@ __global__ void __launch_bounds__(kBinThreads) esi_bin_kernel(BinArgs a)
     for (int j = tid; j < n_tiles; j += NT)
         hrow[j] = (tstart[j] << 16) | (tstart[j + 1] - tstart[j]);
 
-    // phase 3: stable scatter into tile order
-    for (int base = s0; base < s1; base += 32) {
-        const int k = base + lane;
-        int tile = -1;
-        unsigned long long rec = 0;
-        if (k < s1) {
-            const int4 e = sev[k];
-            const int x = e.z & 0xffff, y = (int)((unsigned)e.z >> 16);
-            if (x < W && y < H) {
-                tile = (y >> thl) * tiles_x + (x >> 7);
-                const long long t = ((long long)(unsigned)e.y << 32) | (unsigned)e.x;
-                const unsigned pit = ((unsigned)(y & th_mask) << 7) | (unsigned)(x & 127);
-                const bool pos = (signed char)(e.w & 0xff) > 0;
-                rec = make_record((unsigned)(t - a.t_base), pit, pos ? 1u : 0u);
-            }
-        }
-        const unsigned m = __match_any_sync(kFull, tile);
-        const unsigned rank = __popc(m & lanemask_lt());
-        if (tile >= 0) ssort[tstart[tile] + cnt[warp * ntp + tile] + rank] = rec;
-        __syncwarp();
-        if (tile >= 0 && rank == 0) cnt[warp * ntp + tile] += (unsigned short)__popc(m);
-        __syncwarp();
+    // phase 3: scatter every event to its stable place in tile order
+    const int th_mask = (1 << thl) - 1;
+    for (int k = tid; k < nc; k += NT) {
+        const unsigned tile = ltile[k];
+        if (tile == 0xffffu) continue;
+        const int4 e = sev[k];
+        const int x = e.z & 0xffff, y = (int)((unsigned)e.z >> 16);
+        const long long t = ((long long)(unsigned)e.y << 32) | (unsigned)e.x;
+        const unsigned pit = ((unsigned)(y & th_mask) << 7) | (unsigned)(x & 127);
+        const bool pos = (signed char)(e.w & 0xff) > 0;
+        const int w = k / per;
+        ssort[tstart[tile] + cnt[w * ntp + tile] + loff[k]] =
+            make_record((unsigned)(t - a.t_base), pit, pos ? 1u : 0u);
     }
     __syncthreads();
 
@@ -176,23 +187,26 @@ __global__ void __launch_bounds__(kBinThreads) esi_bin_kernel(BinArgs a)
 
 // Shared-memory layout of the tile kernel (dynamic part).
 static __host__ __device__ inline size_t tile_layout(int batch, int n_chunks, size_t *off_b,
-                                                     size_t *off_runpre, size_t *off_runoff)
+                                                     size_t *off_runpre, size_t *off_runoff,
+                                                     size_t *off_lpos)
 {
-    size_t o = (size_t)batch * 8;
+    size_t o = (size_t)(batch + 2) * 8;   // batch + the next batch's first record
     *off_b = o;
     o += (size_t)batch * 8;
     *off_runpre = o;
     o += (size_t)round_up(n_chunks + 1, 4) * 4;
     *off_runoff = o;
     o += (size_t)round_up(n_chunks, 4) * 4;
+    *off_lpos = o;                   // record: offset inside its warp's row run
+    o += (size_t)round_up(batch, 8) * 2;
     return o;
 }
 
 size_t tile_smem_bytes(int tile_h, int batch, int n_chunks)
 {
     (void)tile_h;
-    size_t a, b, c;
-    return tile_layout(batch, n_chunks, &a, &b, &c);
+    size_t a, b, c, d;
+    return tile_layout(batch, n_chunks, &a, &b, &c, &d);
 }
 
 // Largest c in [0, n) with pre[c] <= g (pre[0] = 0 <= g < pre[n]).
@@ -221,20 +235,23 @@ esi_tile_kernel(TileArgs a)
     constexpr int NT = TH * 32;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned short rcnt[TH][TH];   // [warp][row] counts, then offsets
+    constexpr int RB = (TH == 4) ? 2 : (TH == 8) ? 3 : (TH == 16) ? 4 : 5;  // bits of a row index
     __shared__ unsigned rowstart[TH + 1];
     __shared__ unsigned scan_tmp[NT / 32 + 1];
     __shared__ long long s_tnext;
+    __shared__ WinInfo swin[kStageFrames];              // this launch's frames, if they fit
     __shared__ __align__(16) float sS[TH][kTileW];      // S of the tile's pixels
     __shared__ __align__(16) float sF[TH][kTileW];      // (float)(T - t_base)
     __shared__ __align__(16) long long sO[TH][kTileW];  // T - t_base
 
     const int R = a.batch, n_chunks = a.n_chunks;
-    size_t off_b, off_runpre, off_runoff;
-    tile_layout(R, n_chunks, &off_b, &off_runpre, &off_runoff);
+    size_t off_b, off_runpre, off_runoff, off_lpos;
+    tile_layout(R, n_chunks, &off_b, &off_runpre, &off_runoff, &off_lpos);
     unsigned long long *A = reinterpret_cast<unsigned long long *>(smem);
     unsigned long long *B = reinterpret_cast<unsigned long long *>(smem + off_b);
     unsigned *runpre = reinterpret_cast<unsigned *>(smem + off_runpre);
     unsigned *runoff = reinterpret_cast<unsigned *>(smem + off_runoff);
+    unsigned short *lpos = reinterpret_cast<unsigned short *>(smem + off_lpos);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = blockIdx.x;
@@ -280,6 +297,11 @@ esi_tile_kernel(TileArgs a)
         runpre[c] = h & 0xffffu;
         runoff[c] = h >> 16;
     }
+    // the launch's per-frame constants, staged in shared memory when they fit
+    const int nwin = a.w_end - a.w_begin;
+    const bool staged = nwin <= kStageFrames;
+    if (staged)
+        for (int i = tid; i < nwin; i += NT) swin[i] = a.win[a.w_begin + i];
     __syncthreads();
     const unsigned total = block_exclusive_scan<NT>(runpre, n_chunks, scan_tmp);
     if (tid == 0) runpre[n_chunks] = total;
@@ -289,7 +311,7 @@ esi_tile_kernel(TileArgs a)
     // S += p C; dt = t - T; S *= d(dt); T = t; clamp (Eq. 13)
     auto apply_group = [&](unsigned long long r, bool valid) {
         const int x = (int)((r >> 33) & 127u);
-        const unsigned peers = __match_any_sync(kFull, valid ? x : -1 - lane);
+        const unsigned peers = warp_peers_n<7>((unsigned)x, valid);
         const unsigned rank = __popc(peers & lanemask_lt());
         const unsigned maxr = __reduce_max_sync(kFull, valid ? rank : 0u);
         for (unsigned k = 0; k <= maxr; ++k) {
@@ -310,21 +332,24 @@ esi_tile_kernel(TileArgs a)
         const int nb = (int)min((unsigned)R, total - min(total, b0));
         const bool last = b0 + (unsigned)R >= total;
 
-        // gather the batch (records b0 .. b0 + nb of this tile, arrival order)
-        for (int i = tid; i < nb; i += NT) {
-            const unsigned g = b0 + (unsigned)i;
-            const int c = run_of(runpre, n_chunks, g);
-            A[i] = a.rec[(size_t)c * a.chunk + runoff[c] + (g - runpre[c])];
-        }
-        if (tid == 0) {
-            long long tn = 0x7fffffffffffffffll;
-            if (!last) {
-                const unsigned g = b0 + (unsigned)R;
-                const int c = run_of(runpre, n_chunks, g);
-                tn = (long long)(unsigned)a.rec[(size_t)c * a.chunk + runoff[c] + (g - runpre[c])];
+        // gather the batch (records b0 .. b0 + nb of this tile, arrival
+        // order, plus the next batch's first record): one thread per run,
+        // asynchronous copies, so every record of the batch is in flight
+        const unsigned next = last ? 0u : 1u;
+        if (nb > 0) {
+            const unsigned bend = b0 + (unsigned)nb + next;
+            const int cfirst = run_of(runpre, n_chunks, b0);
+            const int clast = run_of(runpre, n_chunks, bend - 1u);
+            for (int c = cfirst + tid; c <= clast; c += NT) {
+                const unsigned rs = max(runpre[c], b0), re = min(runpre[c + 1], bend);
+                const unsigned long long *src =
+                    a.rec + (size_t)c * a.chunk + runoff[c] + (rs - runpre[c]);
+                for (unsigned i = 0; i + rs < re; ++i) cp_async8(&A[rs - b0 + i], src + i);
             }
-            s_tnext = tn;
         }
+        cp_async_wait_all();
+        __syncthreads();
+        if (tid == 0) s_tnext = last ? 0x7fffffffffffffffll : (long long)(unsigned)A[nb];
         for (int i = tid; i < TH * TH; i += NT) (&rcnt[0][0])[i] = 0;
         __syncthreads();
 
@@ -334,9 +359,15 @@ esi_tile_kernel(TileArgs a)
         const int s0 = min(warp * sl, nb), s1 = min(s0 + sl, nb);
         for (int base = s0; base < s1; base += 32) {
             const int k = base + lane;
-            const int row = (k < s1) ? (int)(A[k] >> 40) : -1;
-            const unsigned m = __match_any_sync(kFull, row);
-            if (row >= 0 && (m & lanemask_lt()) == 0) rcnt[warp][row] += (unsigned short)__popc(m);
+            const bool valid = k < s1;
+            const int row = valid ? (int)(A[k] >> 40) : 0;
+            const unsigned peers = warp_peers_n<RB>((unsigned)row, valid);
+            const unsigned rank = __popc(peers & lanemask_lt());
+            const unsigned pre = valid ? rcnt[warp][row] : 0u;
+            __syncwarp();
+            if (valid && rank == 0) rcnt[warp][row] = (unsigned short)(pre + __popc(peers));
+            if (valid) lpos[k] = (unsigned short)(pre + rank);
+            __syncwarp();
         }
         __syncthreads();
         {
@@ -351,20 +382,10 @@ esi_tile_kernel(TileArgs a)
             if (tid == 0) rowstart[TH] = (unsigned)nb;
         }
         __syncthreads();
-        for (int base = s0; base < s1; base += 32) {
-            const int k = base + lane;
-            unsigned long long r = 0;
-            int row = -1;
-            if (k < s1) {
-                r = A[k];
-                row = (int)(r >> 40);
-            }
-            const unsigned m = __match_any_sync(kFull, row);
-            const unsigned rank = __popc(m & lanemask_lt());
-            if (row >= 0) B[rcnt[warp][row] + rank] = r;
-            __syncwarp();
-            if (row >= 0 && rank == 0) rcnt[warp][row] += (unsigned short)__popc(m);
-            __syncwarp();
+        for (int k = tid; k < nb; k += NT) {
+            const unsigned long long r = A[k];
+            const int row = (int)(r >> 40);
+            B[rcnt[k / max(sl, 1)][row] + lpos[k]] = r;
         }
         __syncthreads();
 
@@ -373,7 +394,7 @@ esi_tile_kernel(TileArgs a)
         const int re = (int)rowstart[warp + 1];
         const long long tnext = s_tnext;
         while (wi < a.w_end) {
-            const WinInfo wv = a.win[wi];
+            const WinInfo wv = staged ? swin[wi - a.w_begin] : a.win[wi];
             if (wv.lim >= tnext) break;  // later records of this tile may be due
             for (;;) {
                 const int k = cur + lane;
@@ -472,8 +493,9 @@ static cudaError_t allow_dynamic_smem(K kernel)
 
 size_t tile_static_smem_bytes(int tile_h)
 {
-    // pixel state (S, F, O per pixel) and the sort scratch
-    return (size_t)tile_h * kTileW * 16 + (size_t)tile_h * tile_h * 2 + 1024;
+    // pixel state (S, F, O per pixel), staged frames and the sort scratch
+    return (size_t)tile_h * kTileW * 16 + (size_t)kStageFrames * sizeof(WinInfo) +
+           (size_t)tile_h * tile_h * 2 + 1024;
 }
 
 cudaError_t set_kernel_attributes()
@@ -483,6 +505,7 @@ cudaError_t set_kernel_attributes()
 #define X(TH, RD, DK, V)                                                                    \
     e = allow_dynamic_smem(esi_tile_kernel<TH, RD, DK, V>);                                 \
     if (e != cudaSuccess) return e;
+    ESI_TILE_VARIANTS(4)
     ESI_TILE_VARIANTS(8)
     ESI_TILE_VARIANTS(16)
     ESI_TILE_VARIANTS(32)
@@ -507,6 +530,7 @@ cudaError_t launch_tile(const TileArgs &a, int tile_h, bool vec, cudaStream_t s)
         esi_tile_kernel<TH, RD, DK, V><<<a.n_tiles, TH * 32, smem, s>>>(a);       \
         return cudaGetLastError();                                                \
     }
+    ESI_TILE_VARIANTS(4)
     ESI_TILE_VARIANTS(8)
     ESI_TILE_VARIANTS(16)
     ESI_TILE_VARIANTS(32)

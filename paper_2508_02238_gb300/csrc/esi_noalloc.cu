@@ -181,6 +181,7 @@ extern "C" int esi_render_frames_noalloc(int width, int height, const esi_params
         ba.tiles_x = tiles_x;
         ba.n_tiles = n_tiles;
         ba.th_log2 = 3;
+        ba.tile_bits = index_bits(n_tiles);
         ba.rec = rec;
         ba.hrow = hrow;
         ba.status = st;

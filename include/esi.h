@@ -193,6 +193,99 @@ void esi_destroy(esi_handle *h);
 /* Static text for an ESI_* code. */
 const char *esi_strerror(int code);
 
+/* ------------------------------------------------------------ serving */
+
+/*
+ * Batched serving of many sensors.  The paper runs one camera (Sec. IV-C);
+ * this interface is the library's own: every stream is the single-sensor path
+ * above (same parameters, same per-pixel semantics, same results), and one
+ * tick processes all streams together in one binning launch and one tile
+ * launch per parameter variant, replayed as a CUDA graph.
+ *
+ * Time: streams share the caller's clock now_us (int64 us).  Stream frames
+ * fall at t_origin + k * frame_period_us, k >= 1.  The caller pushes each
+ * stream's events as its packets arrive; esi_server_tick(now_us) promises
+ * that every event with t <= now_us has been pushed.  The tick applies each
+ * stream's pushed events with t <= now_us, renders every frame with
+ * t_frame <= now_us (at most frame_slots - 1 per stream per tick; the rest
+ * follow in the next ticks) and returns once the work is queued.  Frames land
+ * in host memory the GPU writes directly; esi_stream_frame returns the newest
+ * finished one.
+ *
+ * Admission: each stream's device state (12 bytes per pixel) comes from an
+ * arena of state_budget_bytes reserved at creation; esi_stream_open returns
+ * ESI_EBUSY when it does not fit, and esi_stream_close returns the space, so a
+ * later open can succeed.  Streams may open and close between ticks; work of
+ * successive ticks overlaps on the device (two host staging buffers).
+ */
+typedef struct {
+    int64_t frame_period_us;      /* default 10000 (100 frames/s)            */
+    int64_t max_events_per_tick;  /* default 4194304                         */
+    int32_t max_streams;          /* default 256                             */
+    int32_t frame_slots;          /* finished frames kept per stream, >= 2; default 4 */
+    int32_t use_graph;            /* 1 (default): replay a captured graph    */
+    int32_t tile_h;               /* 0 = default (4, 8, 16 or 32)            */
+    int32_t max_stream_pixels;    /* largest W * H accepted; default 1280*720 */
+    int32_t _reserved[3];
+} esi_server_opts;
+
+/* Latencies in milliseconds over the frames finished since the last reset:
+ * frame latency = frame ready - the tick call that rendered it;
+ * packet-to-frame latency = frame ready - the push of the stream's newest
+ * packet at that tick (the packet that made the frame renderable). */
+typedef struct {
+    uint64_t ticks;
+    uint64_t frames;
+    uint64_t events;
+    uint64_t packets;
+    double frame_latency_p50_ms;
+    double frame_latency_p99_ms;
+    double packet_latency_p50_ms;
+    double packet_latency_p99_ms;
+    double gpu_ms_per_tick;       /* mean device time of a tick's kernels   */
+    uint64_t state_bytes_used;
+    uint64_t state_budget_bytes;
+    int32_t streams_open;
+    int32_t kernel_launches_per_tick;
+} esi_server_stats;
+
+typedef struct esi_server esi_server;
+
+/* opts may be NULL (defaults); cuda_stream as in esi_create. */
+int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts,
+                      void *cuda_stream, esi_server **out);
+
+/* Open a width x height stream (params as in esi_create); ESI_EBUSY when
+ * its state does not fit the budget or max_streams streams are open. */
+int esi_stream_open(esi_server *srv, int width, int height, const esi_params *params,
+                    int *stream_id);
+
+/* Queue one packet of n host events (time-ordered, not earlier than the
+ * stream's last event or last frame); copied before the call returns. */
+int esi_stream_push(esi_server *srv, int stream_id, const esi_event *ev, size_t n);
+
+/* Process every stream up to now_us (see above). */
+int esi_server_tick(esi_server *srv, int64_t now_us);
+
+/* Copy the newest finished frame (W * H bytes) of a stream into the host
+ * buffer out; ESI_ESTATE if none has finished yet.  t_frame, latency_ms
+ * (frame latency as in esi_server_stats) may be NULL. */
+int esi_stream_frame(esi_server *srv, int stream_id, uint8_t *out, int64_t *t_frame,
+                     double *latency_ms);
+
+/* Copy a stream's state (as esi_get_state with host buffers); waits. */
+int esi_stream_state(esi_server *srv, int stream_id, float *S, int64_t *T);
+
+/* Close a stream: waits for its work, returns its state memory. */
+int esi_stream_close(esi_server *srv, int stream_id);
+
+/* Wait for all queued ticks. */
+int esi_server_sync(esi_server *srv);
+
+int esi_server_get_stats(esi_server *srv, esi_server_stats *out);
+int esi_server_reset_stats(esi_server *srv);
+void esi_server_destroy(esi_server *srv);
+
 /* ---------------------------------------------- allocation-free render */
 
 /*

@@ -734,6 +734,7 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
         ta.w_begin = sb.w0;
         ta.w_end = sb.w1;
         ta.frames = frames;
+        ta.frame_outs = nullptr;
         ta.P = h->P;
         ta.batch = tu.batch_records;
         ta.status = h->dstatus;

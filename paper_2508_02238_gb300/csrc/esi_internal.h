@@ -83,10 +83,32 @@ struct TileArgs {
     MapParams mp;
     const WinInfo *win;           // per-frame constants (device), indexed by frame
     int w_begin, w_end;           // frames this launch completes
-    unsigned char *frames;        // frame w at frames + w * P
+    unsigned char *frames;        // frame w at frames + w * P ...
+    unsigned char *const *frame_outs;  // ... or at frame_outs[w] when this is set
     long long P;
     int batch;                    // records sorted per shared-memory batch
     DevStatus *status;
+};
+
+// One stream segment of a batched binning launch: the chunks
+// first_chunk .. first_chunk + ceil(args.n / args.chunk) - 1 of the tick.
+struct BinJob {
+    BinArgs args;
+    int first_chunk;
+    int pad;
+};
+
+// Directory at the start of a serving tick's device table: the batched
+// kernels find their sizes and descriptor arrays through it.
+constexpr int kTickGroups = 12;  // render mode (2) x decay kind (3) x row alignment (2)
+struct TickDir {
+    int n_chunks;
+    int n_items[kTickGroups];
+    int pad[3];
+    long long off_binjob;
+    long long off_chunkjob;
+    long long off_tilejob;
+    long long off_items[kTickGroups];
 };
 
 // Record layout (8 bytes): low 32 bits t - t_base; high 32 bits
@@ -112,6 +134,11 @@ size_t tile_smem_bytes(int tile_h, int batch, int n_chunks);
 size_t tile_static_smem_bytes(int tile_h);
 cudaError_t launch_bin(const BinArgs &a, int n_chunks, cudaStream_t s);
 cudaError_t launch_tile(const TileArgs &a, int tile_h, bool vec, cudaStream_t s);
+cudaError_t launch_bin_batch_tab(const unsigned char *tab, int grid, int chunk, int max_tiles,
+                                 cudaStream_t s);
+cudaError_t launch_tile_batch_tab(const unsigned char *tab, int group, int grid, int tile_h, int rd,
+                                  int dk, bool vec, int batch, int max_chunks, cudaStream_t s);
+int decay_kind_of(const DecayParams &dp);
 cudaError_t set_kernel_attributes();
 
 }  // namespace esi

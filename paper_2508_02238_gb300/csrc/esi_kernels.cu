@@ -56,7 +56,9 @@ size_t bin_smem_bytes(int chunk, int n_tiles)
     return bin_layout(chunk, n_tiles, &a, &b, &c);
 }
 
-__global__ void __launch_bounds__(kBinThreads) esi_bin_kernel(BinArgs a)
+// One chunk of events: block-level body shared by the single-sensor and the
+// batched binning kernels.  cidx is the chunk's index within a.n's events.
+__device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
 {
     constexpr int NT = kBinThreads, NW = NT / 32;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(kBinThreads) esi_bin_kernel(BinArgs a)
     unsigned short *ltile = loff + chunk;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const long long c0 = (long long)blockIdx.x * chunk;
+    const long long c0 = (long long)cidx * chunk;
     const int nc = (int)min((long long)chunk, (long long)a.n - c0);
 
     if (tid == 0) {
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(kBinThreads) esi_bin_kernel(BinArgs a)
     const unsigned total = block_exclusive_scan<NT>(tstart, n_tiles, scan_tmp);
     if (tid == 0) tstart[n_tiles] = total;
     __syncthreads();
-    unsigned *hrow = a.hrow + (size_t)blockIdx.x * n_tiles;
+    unsigned *hrow = a.hrow + (size_t)cidx * n_tiles;
     for (int j = tid; j < n_tiles; j += NT)
         hrow[j] = (tstart[j] << 16) | (tstart[j + 1] - tstart[j]);
 
@@ -183,6 +185,22 @@ __global__ void __launch_bounds__(kBinThreads) esi_bin_kernel(BinArgs a)
     unsigned long long *dst = a.rec + c0;
     for (unsigned i = tid; i < total; i += NT) dst[i] = ssort[i];
     if (tid == 0 && s_drop) atomicAdd(&a.status->dropped, (unsigned long long)s_drop);
+}
+
+__global__ void __launch_bounds__(kBinThreads) esi_bin_kernel(BinArgs a) { bin_chunk(a, blockIdx.x); }
+
+// Batched binning of a serving tick: block c bins chunk c of the tick; the
+// tick directory names the stream segment (job) each chunk belongs to.  The
+// grid is sized for the capacity; blocks past the tick's chunks return.
+__global__ void __launch_bounds__(kBinThreads) esi_bin_tab_kernel(const unsigned char *tab)
+{
+    const TickDir *d = reinterpret_cast<const TickDir *>(tab);
+    const int c = blockIdx.x;
+    if (c >= d->n_chunks) return;
+    const BinJob *jobs = reinterpret_cast<const BinJob *>(tab + d->off_binjob);
+    const int *cj = reinterpret_cast<const int *>(tab + d->off_chunkjob);
+    const BinJob &j = jobs[cj[c]];
+    bin_chunk(j.args, c - j.first_chunk);
 }
 
 // Shared-memory layout of the tile kernel (dynamic part).
@@ -229,8 +247,7 @@ __device__ __forceinline__ int run_of(const unsigned *pre, int n, unsigned g)
 // rows start 4-byte aligned (W % 4 == 0), so a lane's four pixels move as one
 // float4 / two longlong2 / one 32-bit frame word.
 template <int TH, int RD, int DK, bool VEC>
-__global__ void __launch_bounds__(TH * 32, (TH * 32 >= 1024) ? 1 : 1024 / (TH * 32))
-esi_tile_kernel(TileArgs a)
+__device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
 {
     constexpr int NT = TH * 32;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -254,7 +271,6 @@ esi_tile_kernel(TileArgs a)
     unsigned short *lpos = reinterpret_cast<unsigned short *>(smem + off_lpos);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile = blockIdx.x;
     const int x0 = (tile % a.tiles_x) * kTileW + 4 * lane;
     const int y = (tile / a.tiles_x) * TH + warp;
     const int nval = (y < a.H) ? max(0, min(4, a.W - x0)) : 0;
@@ -424,7 +440,8 @@ esi_tile_kernel(TileArgs a)
             unsigned code[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) code[q] = quantize_u8(fmaf(v[q], mp.scale, mp.offs));
-            unsigned char *fr = a.frames + (long long)wi * a.P + pix0;
+            unsigned char *fr =
+                (a.frame_outs ? a.frame_outs[wi] : a.frames + (long long)wi * a.P) + pix0;
             if (VEC) {
                 if (nval == 4)
                     *reinterpret_cast<unsigned *>(fr) =
@@ -461,6 +478,30 @@ esi_tile_kernel(TileArgs a)
                 a.S[pix0 + q] = rS[4 * lane + q];
                 a.T[pix0 + q] = rO[4 * lane + q] + tb;
             }
+    }
+}
+
+#define ESI_TILE_BOUNDS(TH) __launch_bounds__(TH * 32, (TH * 32 >= 1024) ? 1 : 1024 / (TH * 32))
+
+template <int TH, int RD, int DK, bool VEC>
+__global__ void ESI_TILE_BOUNDS(TH) esi_tile_kernel(TileArgs a)
+{
+    tile_body<TH, RD, DK, VEC>(a, blockIdx.x);
+}
+
+// Batched tiles of a serving tick: a persistent grid walks the work items
+// (stream job, tile) of one parameter variant group.
+template <int TH, int RD, int DK, bool VEC>
+__global__ void ESI_TILE_BOUNDS(TH) esi_tile_tab_kernel(const unsigned char *tab, int group)
+{
+    const TickDir *d = reinterpret_cast<const TickDir *>(tab);
+    const int n = d->n_items[group];
+    const int2 *items = reinterpret_cast<const int2 *>(tab + d->off_items[group]);
+    const TileArgs *jobs = reinterpret_cast<const TileArgs *>(tab + d->off_tilejob);
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const int2 it = items[i];
+        tile_body<TH, RD, DK, VEC>(jobs[it.x], it.y);
+        __syncthreads();  // shared memory is reused by the next item
     }
 }
 
@@ -501,9 +542,11 @@ size_t tile_static_smem_bytes(int tile_h)
 cudaError_t set_kernel_attributes()
 {
     cudaError_t e = allow_dynamic_smem(esi_bin_kernel);
+    if (e == cudaSuccess) e = allow_dynamic_smem(esi_bin_tab_kernel);
     if (e != cudaSuccess) return e;
 #define X(TH, RD, DK, V)                                                                    \
     e = allow_dynamic_smem(esi_tile_kernel<TH, RD, DK, V>);                                 \
+    if (e == cudaSuccess) e = allow_dynamic_smem(esi_tile_tab_kernel<TH, RD, DK, V>);       \
     if (e != cudaSuccess) return e;
     ESI_TILE_VARIANTS(4)
     ESI_TILE_VARIANTS(8)
@@ -519,6 +562,33 @@ cudaError_t launch_bin(const BinArgs &a, int n_chunks, cudaStream_t s)
     esi_bin_kernel<<<n_chunks, kBinThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
+
+cudaError_t launch_bin_batch_tab(const unsigned char *tab, int grid, int chunk, int max_tiles,
+                                 cudaStream_t s)
+{
+    const size_t smem = bin_smem_bytes(chunk, max_tiles);
+    esi_bin_tab_kernel<<<grid, kBinThreads, smem, s>>>(tab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_batch_tab(const unsigned char *tab, int group, int grid, int tile_h, int rd,
+                                  int dk, bool vec, int batch, int max_chunks, cudaStream_t s)
+{
+    const size_t smem = tile_smem_bytes(tile_h, batch, max_chunks);
+#define X(TH, RD, DK, V)                                                                  \
+    if (tile_h == TH && rd == RD && dk == DK && vec == V) {                               \
+        esi_tile_tab_kernel<TH, RD, DK, V><<<grid, TH * 32, smem, s>>>(tab, group);       \
+        return cudaGetLastError();                                                        \
+    }
+    ESI_TILE_VARIANTS(4)
+    ESI_TILE_VARIANTS(8)
+    ESI_TILE_VARIANTS(16)
+    ESI_TILE_VARIANTS(32)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+int decay_kind_of(const DecayParams &dp) { return decay_kind(dp); }
 
 cudaError_t launch_tile(const TileArgs &a, int tile_h, bool vec, cudaStream_t s)
 {

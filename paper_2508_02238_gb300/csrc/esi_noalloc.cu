@@ -206,6 +206,7 @@ extern "C" int esi_render_frames_noalloc(int width, int height, const esi_params
     ta.w_begin = 0;
     ta.w_end = (int)m;
     ta.frames = frames;
+        ta.frame_outs = nullptr;
     ta.P = (long long)width * height;
     ta.batch = kNaBatch;
     ta.status = st;

@@ -48,6 +48,23 @@ class esi_kernel_time(ctypes.Structure):
                 ("total_ms", ctypes.c_double)]
 
 
+class esi_server_opts(ctypes.Structure):
+    _fields_ = [("frame_period_us", ctypes.c_int64), ("max_events_per_tick", ctypes.c_int64),
+                ("max_streams", ctypes.c_int32), ("frame_slots", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("max_stream_pixels", ctypes.c_int32), ("_reserved", ctypes.c_int32 * 3)]
+
+
+class esi_server_stats(ctypes.Structure):
+    _fields_ = [("ticks", ctypes.c_uint64), ("frames", ctypes.c_uint64),
+                ("events", ctypes.c_uint64), ("packets", ctypes.c_uint64),
+                ("frame_latency_p50_ms", ctypes.c_double), ("frame_latency_p99_ms", ctypes.c_double),
+                ("packet_latency_p50_ms", ctypes.c_double), ("packet_latency_p99_ms", ctypes.c_double),
+                ("gpu_ms_per_tick", ctypes.c_double), ("state_bytes_used", ctypes.c_uint64),
+                ("state_budget_bytes", ctypes.c_uint64), ("streams_open", ctypes.c_int32),
+                ("kernel_launches_per_tick", ctypes.c_int32)]
+
+
 _P = ctypes.c_void_p
 _i32, _i64, _sz = ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
 
@@ -70,6 +87,17 @@ SIGNATURES = {
     "esi_strerror": (ctypes.c_char_p, [_i32]),
     "esi_render_frames_noalloc": (_i32, [_i32, _i32, ctypes.POINTER(esi_params), _P, _sz, _P,
                                          _sz, _P, _P, _P, _P]),
+    "esi_server_create": (_i32, [_sz, ctypes.POINTER(esi_server_opts), _P, ctypes.POINTER(_P)]),
+    "esi_stream_open": (_i32, [_P, _i32, _i32, ctypes.POINTER(esi_params), ctypes.POINTER(_i32)]),
+    "esi_stream_push": (_i32, [_P, _i32, _P, _sz]),
+    "esi_server_tick": (_i32, [_P, _i64]),
+    "esi_stream_frame": (_i32, [_P, _i32, _P, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)]),
+    "esi_stream_state": (_i32, [_P, _i32, _P, _P]),
+    "esi_stream_close": (_i32, [_P, _i32]),
+    "esi_server_sync": (_i32, [_P]),
+    "esi_server_get_stats": (_i32, [_P, ctypes.POINTER(esi_server_stats)]),
+    "esi_server_reset_stats": (_i32, [_P]),
+    "esi_server_destroy": (None, [_P]),
 }
 
 _lock = threading.Lock()
@@ -193,6 +221,65 @@ def esi_render_frames_noalloc(width: int, height: int, params: esi_params, event
 
 def esi_destroy(h) -> None:
     _fn("esi_destroy")(h)
+
+
+def esi_server_create(state_budget_bytes: int, opts: esi_server_opts | None = None, cuda_stream=0):
+    """Returns (rc, server)."""
+    srv = _P()
+    rc = _fn("esi_server_create")(int(state_budget_bytes),
+                                  ctypes.byref(opts) if opts is not None else None,
+                                  _P(int(cuda_stream) or None), ctypes.byref(srv))
+    return rc, srv
+
+
+def esi_stream_open(srv, width: int, height: int, params: esi_params):
+    """Returns (rc, stream_id)."""
+    sid = ctypes.c_int32(-1)
+    rc = _fn("esi_stream_open")(srv, int(width), int(height), ctypes.byref(params), ctypes.byref(sid))
+    return rc, int(sid.value)
+
+
+def esi_stream_push(srv, stream_id: int, ev, n: int) -> int:
+    return _fn("esi_stream_push")(srv, int(stream_id), _P(ptr(ev) or None), int(n))
+
+
+def esi_server_tick(srv, now_us: int) -> int:
+    return _fn("esi_server_tick")(srv, int(now_us))
+
+
+def esi_stream_frame(srv, stream_id: int, out):
+    """Returns (rc, t_frame_us, latency_ms)."""
+    t = ctypes.c_int64(0)
+    lat = ctypes.c_double(0.0)
+    rc = _fn("esi_stream_frame")(srv, int(stream_id), _P(ptr(out) or None), ctypes.byref(t),
+                                 ctypes.byref(lat))
+    return rc, int(t.value), float(lat.value)
+
+
+def esi_stream_state(srv, stream_id: int, S, T) -> int:
+    return _fn("esi_stream_state")(srv, int(stream_id), _P(ptr(S) or None), _P(ptr(T) or None))
+
+
+def esi_stream_close(srv, stream_id: int) -> int:
+    return _fn("esi_stream_close")(srv, int(stream_id))
+
+
+def esi_server_sync(srv) -> int:
+    return _fn("esi_server_sync")(srv)
+
+
+def esi_server_get_stats(srv):
+    st = esi_server_stats()
+    rc = _fn("esi_server_get_stats")(srv, ctypes.byref(st))
+    return rc, st
+
+
+def esi_server_reset_stats(srv) -> int:
+    return _fn("esi_server_reset_stats")(srv)
+
+
+def esi_server_destroy(srv) -> None:
+    _fn("esi_server_destroy")(srv)
 
 
 class EsiError(RuntimeError):

@@ -301,6 +301,7 @@ def bench_esi(args):
     if not args.no_extras and rank == 0:
         line["e2e"] = e2e_leg(esi, torch, h, stream, sc, ev, out, total_steps, args.steps, n_windows)
         line["latency"] = latency_leg(esi, torch, sc, ev)
+        line["serving"] = serving_leg(esi)
     elif not args.no_extras:
         line["e2e"] = None
     esi.esi_destroy(h)
@@ -358,6 +359,90 @@ def latency_leg(esi, torch, sc, ev):
     return {"path": "plain: push 10 ms packet (host) + render one frame (host out)",
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "frames": int(len(lat))}
+
+
+SERVING_STREAMS = 64
+SERVING_SECONDS = 0.25
+
+
+def serving_workload(n_streams=SERVING_STREAMS, seconds=SERVING_SECONDS, seed=1003):
+    """64 config-0 form 346x260 streams, lognormal rates, Poisson packets (1 ms mean)."""
+    import synth
+    rates = synth.lognormal_rates(n_streams, seed)
+    streams = []
+    rng = np.random.default_rng(seed)
+    for i in range(n_streams):
+        sc = synth.serving_stream(i, float(rates[i]), seconds)
+        ev = synth.generate(sc)
+        # Poisson packet arrivals (mean 1 ms); a packet carries the events since the last one
+        gaps = rng.exponential(1000.0, size=int(seconds * 1e6 / 1000) * 3 + 10)
+        arr = np.cumsum(gaps).astype(np.int64) + 1
+        arr = arr[arr < int(seconds * 1e6)]
+        arr = np.append(arr, int(seconds * 1e6))
+        cuts = np.searchsorted(ev["t"], arr, side="right")
+        streams.append((sc.W, sc.H, ev, arr, cuts))
+    return rates, streams
+
+
+def build_packets(esi, streams, ids):
+    import ctypes
+    items = []
+    for k, (W, H, ev, arr, cuts) in enumerate(streams):
+        lo = 0
+        base = ev.ctypes.data
+        for a, hi in zip(arr, cuts):
+            items.append((int(a), ids[k], base + lo * 16, int(hi - lo)))
+            lo = int(hi)
+    items.sort(key=lambda x: (x[0], x[1]))
+    pk = (esi.esi_packet * len(items))()
+    for j, (a, sid, ptr_, n) in enumerate(items):
+        pk[j].stream, pk[j].arrival_us, pk[j].ev, pk[j].n = sid, a, ptr_, n
+    return pk, len(items)
+
+
+def serving_leg(esi):
+    """Batched (one graph per tick) vs plain (per-stream launches), wall-clock paced."""
+    rates, streams = serving_workload()
+    t_end = int(SERVING_SECONDS * 1e6)
+    n_ev = int(sum(len(s[2]) for s in streams))
+    params = esi.make_params(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1)
+    out = {"workload": f"{len(streams)} streams 346x260 (config-0 form), lognormal rates "
+                       f"{rates.min() / 1e6:.2f}-{rates.max() / 1e6:.2f} Mev/s (median "
+                       f"{np.median(rates) / 1e6:.2f}), Poisson packets 1 ms, 100 frames/s, "
+                       f"{SERVING_SECONDS} s", "events": n_ev}
+    for mode in ("batched", "batched_throughput"):
+        rc, srv = esi.esi_server_create(1 << 30, None, 0)
+        esi.check(rc, "server")
+        ids = []
+        for W, H, *_ in streams:
+            rc, sid = esi.esi_stream_open(srv, W, H, params)
+            esi.check(rc, "open")
+            ids.append(sid)
+        pk, npk = build_packets(esi, streams, ids)
+        realtime = 1 if mode == "batched" else 0
+        t0 = time.perf_counter()
+        esi.check(esi.esi_server_run(srv, pk, npk, 1000, t_end, realtime), "run")
+        dt = time.perf_counter() - t0
+        rc, st = esi.esi_server_get_stats(srv)
+        esi.esi_server_destroy(srv)
+        out[mode] = {"frames": int(st.frames), "expected_frames": len(streams) * (t_end // 10000),
+                     "frame_latency_p50_ms": st.frame_latency_p50_ms,
+                     "frame_latency_p99_ms": st.frame_latency_p99_ms,
+                     "packet_to_frame_p50_ms": st.packet_latency_p50_ms,
+                     "packet_to_frame_p99_ms": st.packet_latency_p99_ms,
+                     "gpu_ms_per_tick": st.gpu_ms_per_tick,
+                     "kernel_launches_per_tick": int(st.kernel_launches_per_tick),
+                     "wall_s": dt, "events_per_s": n_ev / dt if realtime == 0 else None,
+                     "frames_per_s": st.frames / dt}
+    pk, npk = build_packets(esi, streams, list(range(len(streams))))
+    rc, st = esi.esi_plain_run([s[0] for s in streams], [s[1] for s in streams],
+                               [params] * len(streams), pk, npk, 1000, t_end, 10000, 1)
+    esi.check(rc, "plain")
+    out["plain"] = {"frames": int(st.frames), "frame_latency_p50_ms": st.frame_latency_p50_ms,
+                    "frame_latency_p99_ms": st.frame_latency_p99_ms,
+                    "packet_to_frame_p50_ms": st.packet_latency_p50_ms,
+                    "packet_to_frame_p99_ms": st.packet_latency_p99_ms}
+    return out
 
 
 def main():

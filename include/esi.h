@@ -264,6 +264,12 @@ int esi_stream_open(esi_server *srv, int width, int height, const esi_params *pa
  * stream's last event or last frame); copied before the call returns. */
 int esi_stream_push(esi_server *srv, int stream_id, const esi_event *ev, size_t n);
 
+/* Declare that every event of the stream with t <= t_us has been pushed (the
+ * end time of the packet just pushed).  Once a stream has a watermark, its
+ * frames become due at t_frame <= min(now_us, watermark) and a tick applies
+ * its events up to that time; without one, now_us alone decides. */
+int esi_stream_watermark(esi_server *srv, int stream_id, int64_t t_us);
+
 /* Process every stream up to now_us (see above). */
 int esi_server_tick(esi_server *srv, int64_t now_us);
 
@@ -285,6 +291,37 @@ int esi_server_sync(esi_server *srv);
 int esi_server_get_stats(esi_server *srv, esi_server_stats *out);
 int esi_server_reset_stats(esi_server *srv);
 void esi_server_destroy(esi_server *srv);
+
+/* One packet of a stream for the executors below. */
+typedef struct {
+    int32_t stream;       /* server stream id (esi_server_run) or stream index */
+    int32_t _pad;
+    int64_t arrival_us;   /* arrival time; the stream is complete up to it    */
+    const esi_event *ev;  /* the packet's host events                          */
+    uint64_t n;
+} esi_packet;
+
+/*
+ * Serving executor: feeds packets (sorted by arrival_us) to the server as
+ * they arrive (esi_stream_push, then esi_stream_watermark(arrival_us)) and
+ * ticks every tick_us of stream time until t_end_us, then waits for the
+ * device.  realtime = 1 paces stream time with the wall clock (stream time 0
+ * = the call), so latencies are those of live serving; realtime = 0 advances
+ * tick by tick as fast as host and device allow (throughput).
+ */
+int esi_server_run(esi_server *srv, const esi_packet *packets, size_t n_packets,
+                   int64_t tick_us, int64_t t_end_us, int realtime);
+
+/*
+ * The same workload without batching, for comparison: one esi_handle per
+ * stream; at every tick each stream renders its due frames with its own
+ * esi_render_frame calls (host output, no graph).  Fills out's counters and
+ * latencies with the definitions of esi_server_stats.
+ */
+int esi_plain_run(int n_streams, const int *widths, const int *heights,
+                  const esi_params *params, const esi_packet *packets, size_t n_packets,
+                  int64_t tick_us, int64_t t_end_us, int64_t frame_period_us, int realtime,
+                  esi_server_stats *out);
 
 /* ---------------------------------------------- allocation-free render */
 

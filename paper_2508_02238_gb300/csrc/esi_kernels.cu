@@ -282,6 +282,24 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
     float *rF = sF[warp];
     long long *rO = sO[warp];
 
+    // this tile's run in every chunk, in chunk (= arrival) order
+    for (int c = tid; c < n_chunks; c += NT) {
+        const unsigned h = a.hrow[(size_t)c * a.n_tiles + tile];
+        runpre[c] = h & 0xffffu;
+        runoff[c] = h >> 16;
+    }
+    // the launch's per-frame constants, staged in shared memory when they fit
+    const int nwin = a.w_end - a.w_begin;
+    const bool staged = nwin <= kStageFrames;
+    if (staged)
+        for (int i = tid; i < nwin; i += NT) swin[i] = a.win[a.w_begin + i];
+    __syncthreads();
+    const unsigned total = block_exclusive_scan<NT>(runpre, n_chunks, scan_tmp);
+    if (tid == 0) runpre[n_chunks] = total;
+    __syncthreads();
+    // a tile with no record and no frame in this launch keeps its state as is
+    if (total == 0 && a.w_end == a.w_begin) return;
+
     {
         float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         long long o4[4] = {0, 0, 0, 0};
@@ -307,21 +325,6 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
         }
     }
 
-    // this tile's run in every chunk, in chunk (= arrival) order
-    for (int c = tid; c < n_chunks; c += NT) {
-        const unsigned h = a.hrow[(size_t)c * a.n_tiles + tile];
-        runpre[c] = h & 0xffffu;
-        runoff[c] = h >> 16;
-    }
-    // the launch's per-frame constants, staged in shared memory when they fit
-    const int nwin = a.w_end - a.w_begin;
-    const bool staged = nwin <= kStageFrames;
-    if (staged)
-        for (int i = tid; i < nwin; i += NT) swin[i] = a.win[a.w_begin + i];
-    __syncthreads();
-    const unsigned total = block_exclusive_scan<NT>(runpre, n_chunks, scan_tmp);
-    if (tid == 0) runpre[n_chunks] = total;
-    __syncthreads();
 
     // Alg. 2 for a group of due records (one per valid lane, time order):
     // S += p C; dt = t - T; S *= d(dt); T = t; clamp (Eq. 13)

@@ -8,6 +8,8 @@
 // read their sizes and per-stream descriptors from the device table, so one
 // captured CUDA graph serves every tick; frames are written straight into
 // mapped host memory.  A host-function node stamps each tick's completion.
+#include <time.h>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -108,6 +110,7 @@ struct Stream {
     long long last_event_t = 0;
     long long push_floor = 0;
     long long next_frame_t = 0;
+    long long watermark = LLONG_MAX;      // events complete up to here
     long long last_push_ns = 0;
     unsigned char *slots_host = nullptr;  // frame_slots * P bytes, mapped
     unsigned char *slots_dev = nullptr;
@@ -521,6 +524,15 @@ int esi_stream_push(esi_server *s, int id, const esi_event *ev, size_t n)
     return ESI_OK;
 }
 
+int esi_stream_watermark(esi_server *s, int id, int64_t t_us)
+{
+    if (!s || id < 0 || id >= (int)s->streams.size() || !s->streams[id].open) return ESI_EINVAL;
+    Stream &st = s->streams[id];
+    if (st.watermark != LLONG_MAX && (long long)t_us < st.watermark) return ESI_ETIMEORDER;
+    st.watermark = t_us;
+    return ESI_OK;
+}
+
 int esi_server_tick(esi_server *s, int64_t now_us)
 {
     if (!s) return ESI_EINVAL;
@@ -561,16 +573,18 @@ int esi_server_tick(esi_server *s, int64_t now_us)
         int can = (int)std::max<long long>(0, (long long)(K - 1) - (long long)in_flight);
         std::vector<long long> fr;
         long long tf = st.next_frame_t;
-        while (tf <= now_us && (int)fr.size() < can) {
+        const long long upto = std::min((long long)now_us, st.watermark);
+        while (tf <= upto && (int)fr.size() < can) {
             fr.push_back(tf);
             tf += s->opts.frame_period_us;
         }
+        // every tick applies what has arrived, so a frame's tick only has the
+        // newest events left to do
         const size_t avail = st.pend.size() - st.pend_head;
-        const bool backlog = (long long)avail > ev_cap_stream / 2;
-        if (fr.empty() && !backlog) continue;
+        if (fr.empty() && avail == 0) continue;
         // events: t <= now, or <= the last frame when frames wait for the next tick
-        long long lim_t = now_us;
-        if (tf <= now_us) lim_t = fr.empty() ? st.push_floor : fr.back();
+        long long lim_t = upto;
+        if (tf <= upto) lim_t = fr.empty() ? st.push_floor : fr.back();
         const esi_event *pb = st.pend.data() + st.pend_head;
         size_t take = (size_t)(std::upper_bound(pb, pb + avail, lim_t,
                                                 [](long long v, const esi_event &e) { return v < e.t_us; }) -
@@ -829,6 +843,146 @@ int esi_server_reset_stats(esi_server *s)
     s->gpu_ms = 0.0;
     s->gpu_n = 0;
     return ESI_OK;
+}
+
+// --------------------------------------------------------------- executors
+namespace {
+
+// Wall-clock pacing: wait until stream time t_us (microseconds since t0_ns).
+void wait_until(long long t0_ns, long long t_us)
+{
+    const long long target = t0_ns + t_us * 1000;
+    for (;;) {
+        const long long now = wall_ns();
+        if (now >= target) return;
+        if (target - now > 200000) {
+            struct timespec ts = {0, (long)(target - now - 100000)};
+            nanosleep(&ts, nullptr);
+        }
+    }
+}
+
+}  // namespace
+
+int esi_server_run(esi_server *s, const esi_packet *pk, size_t n, int64_t tick_us, int64_t t_end_us,
+                   int realtime)
+{
+    if (!s || (n && !pk) || tick_us < 1 || t_end_us < 0) return ESI_EINVAL;
+    for (size_t i = 1; i < n; ++i)
+        if (pk[i].arrival_us < pk[i - 1].arrival_us) return ESI_EINVAL;
+    const long long t0 = wall_ns();
+    const long long min_gap = std::max<long long>(1, tick_us / 5);
+    size_t i = 0;
+    long long next_tick = tick_us, last_tick = LLONG_MIN / 2;
+    for (;;) {
+        long long now;
+        if (realtime) {
+            long long next_evt = next_tick;
+            if (i < n) next_evt = std::min<long long>(next_evt, pk[i].arrival_us);
+            wait_until(t0, next_evt);
+            now = (wall_ns() - t0) / 1000;
+        } else {
+            now = next_tick;
+        }
+        for (; i < n && pk[i].arrival_us <= now; ++i) {
+            int rc = esi_stream_push(s, pk[i].stream, pk[i].ev, (size_t)pk[i].n);
+            if (!rc) rc = esi_stream_watermark(s, pk[i].stream, pk[i].arrival_us);
+            if (rc) return rc;
+        }
+        // tick at the tick period, and early when a packet has made a frame due
+        bool due = false;
+        if (realtime && now - last_tick >= min_gap)
+            for (const Stream &st : s->streams)
+                if (st.open && st.next_frame_t <= std::min<long long>(now, st.watermark)) {
+                    due = true;
+                    break;
+                }
+        if (now >= next_tick || due) {
+            int rc = esi_server_tick(s, std::min<long long>(now, t_end_us));
+            if (rc) return rc;
+            last_tick = now;
+            while (next_tick <= now) next_tick += tick_us;
+            if (now >= t_end_us) break;
+        }
+    }
+    return wait_all(s);
+}
+
+int esi_plain_run(int n_streams, const int *widths, const int *heights, const esi_params *params,
+                  const esi_packet *pk, size_t n, int64_t tick_us, int64_t t_end_us,
+                  int64_t frame_period_us, int realtime, esi_server_stats *out)
+{
+    if (n_streams < 1 || !widths || !heights || !params || (n && !pk) || tick_us < 1 ||
+        frame_period_us < 1 || !out)
+        return ESI_EINVAL;
+    struct PS {
+        esi_handle *h = nullptr;
+        std::vector<unsigned char> frame;
+        long long next_frame = 0, watermark = LLONG_MAX, last_push_ns = 0;
+    };
+    std::vector<PS> ps((size_t)n_streams);
+    int rc = ESI_OK;
+    for (int k = 0; k < n_streams && !rc; ++k) {
+        rc = esi_create(widths[k], heights[k], &params[k], nullptr, &ps[k].h);
+        if (!rc) {
+            ps[k].frame.resize((size_t)widths[k] * heights[k]);
+            ps[k].next_frame = params[k].t_origin_us + frame_period_us;
+        }
+    }
+    std::vector<double> flat, plat;
+    unsigned long long ticks = 0, frames = 0, events = 0, packets = 0;
+    const long long t0 = wall_ns();
+    size_t i = 0;
+    long long next_tick = tick_us;
+    while (!rc) {
+        long long now;
+        if (realtime) {
+            long long next_evt = next_tick;
+            if (i < n) next_evt = std::min<long long>(next_evt, pk[i].arrival_us);
+            wait_until(t0, next_evt);
+            now = (wall_ns() - t0) / 1000;
+        } else {
+            now = next_tick;
+        }
+        for (; i < n && pk[i].arrival_us <= now && !rc; ++i) {
+            PS &p = ps[(size_t)pk[i].stream];
+            rc = esi_push_events(p.h, pk[i].ev, (size_t)pk[i].n, 0);
+            p.watermark = pk[i].arrival_us;
+            p.last_push_ns = wall_ns();
+            events += pk[i].n;
+            packets += 1;
+        }
+        if (rc || now < next_tick) continue;
+        const long long call = wall_ns();
+        const long long t_now = std::min<long long>(now, t_end_us);
+        for (int k = 0; k < n_streams && !rc; ++k) {
+            PS &p = ps[(size_t)k];
+            const long long upto = std::min(t_now, p.watermark);
+            while (p.next_frame <= upto && !rc) {
+                rc = esi_render_frame(p.h, p.next_frame, p.frame.data(), 0);
+                const long long ready = wall_ns();
+                flat.push_back((double)(ready - call) * 1e-6);
+                if (p.last_push_ns) plat.push_back((double)(ready - p.last_push_ns) * 1e-6);
+                frames += 1;
+                p.next_frame += frame_period_us;
+            }
+        }
+        ticks += 1;
+        while (next_tick <= now) next_tick += tick_us;
+        if (now >= t_end_us) break;
+    }
+    for (PS &p : ps) esi_destroy(p.h);
+    std::memset(out, 0, sizeof(*out));
+    out->ticks = ticks;
+    out->frames = frames;
+    out->events = events;
+    out->packets = packets;
+    out->frame_latency_p50_ms = percentile(flat, 0.50);
+    out->frame_latency_p99_ms = percentile(flat, 0.99);
+    out->packet_latency_p50_ms = percentile(plat, 0.50);
+    out->packet_latency_p99_ms = percentile(plat, 0.99);
+    out->streams_open = n_streams;
+    return rc;
 }
 
 }  // extern "C"

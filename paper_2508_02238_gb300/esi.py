@@ -65,6 +65,11 @@ class esi_server_stats(ctypes.Structure):
                 ("kernel_launches_per_tick", ctypes.c_int32)]
 
 
+class esi_packet(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_int32), ("_pad", ctypes.c_int32),
+                ("arrival_us", ctypes.c_int64), ("ev", ctypes.c_void_p), ("n", ctypes.c_uint64)]
+
+
 _P = ctypes.c_void_p
 _i32, _i64, _sz = ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
 
@@ -91,6 +96,10 @@ SIGNATURES = {
     "esi_stream_open": (_i32, [_P, _i32, _i32, ctypes.POINTER(esi_params), ctypes.POINTER(_i32)]),
     "esi_stream_push": (_i32, [_P, _i32, _P, _sz]),
     "esi_server_tick": (_i32, [_P, _i64]),
+    "esi_stream_watermark": (_i32, [_P, _i32, _i64]),
+    "esi_server_run": (_i32, [_P, _P, _sz, _i64, _i64, _i32]),
+    "esi_plain_run": (_i32, [_i32, _P, _P, _P, _P, _sz, _i64, _i64, _i64, _i32,
+                             ctypes.POINTER(esi_server_stats)]),
     "esi_stream_frame": (_i32, [_P, _i32, _P, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)]),
     "esi_stream_state": (_i32, [_P, _i32, _P, _P]),
     "esi_stream_close": (_i32, [_P, _i32]),
@@ -245,6 +254,30 @@ def esi_stream_push(srv, stream_id: int, ev, n: int) -> int:
 
 def esi_server_tick(srv, now_us: int) -> int:
     return _fn("esi_server_tick")(srv, int(now_us))
+
+
+def esi_stream_watermark(srv, stream_id: int, t_us: int) -> int:
+    return _fn("esi_stream_watermark")(srv, int(stream_id), int(t_us))
+
+
+def esi_server_run(srv, packets, n: int, tick_us: int, t_end_us: int, realtime: int) -> int:
+    """packets: a ctypes array of esi_packet sorted by arrival_us."""
+    return _fn("esi_server_run")(srv, ctypes.cast(packets, _P), int(n), int(tick_us),
+                                 int(t_end_us), int(realtime))
+
+
+def esi_plain_run(widths, heights, params, packets, n: int, tick_us: int, t_end_us: int,
+                  frame_period_us: int, realtime: int):
+    """widths, heights: int lists; params: list of esi_params.  Returns (rc, stats)."""
+    ns = len(widths)
+    W = (ctypes.c_int * ns)(*widths)
+    H = (ctypes.c_int * ns)(*heights)
+    Pm = (esi_params * ns)(*params)
+    st = esi_server_stats()
+    rc = _fn("esi_plain_run")(ns, ctypes.cast(W, _P), ctypes.cast(H, _P), ctypes.cast(Pm, _P),
+                              ctypes.cast(packets, _P), int(n), int(tick_us), int(t_end_us),
+                              int(frame_period_us), int(realtime), ctypes.byref(st))
+    return rc, st
 
 
 def esi_stream_frame(srv, stream_id: int, out):

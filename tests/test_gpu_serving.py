@@ -114,9 +114,13 @@ def test_served_streams_match_the_oracle():
         assert sorted(frames) == expect_tf, (i, sorted(frames)[:3])
         pp = {**dict(t_origin_us=0), **p}
         used = ev[ev["t"] <= t_end]
-        ref = run_oracle(used, W, H, pp, expect_tf)
+        # frames at their times; the state holds every event the server has
+        # seen by the last tick (events after a stream's last frame included)
+        st_ref = oracle.OracleState(W, H, oracle_params(pp))
+        ref_frames, n_used = st_ref.replay(used, expect_tf)
+        st_ref.integrate(used[n_used:])
         got = {"S": S, "T": T, "frames": np.stack([frames[t] for t in expect_tf])}
-        compare(got, ref, pp["C"], f"stream {i}")
+        compare(got, {"S": st_ref.S, "T": st_ref.T, "frames": ref_frames}, pp["C"], f"stream {i}")
 
 
 def test_each_stream_is_the_same_alone_and_in_the_mix():
@@ -143,6 +147,8 @@ def test_served_stream_equals_single_sensor_handle():
     with GpuStream(W, H, {**dict(t_origin_us=0), **p}) as g:
         assert g.push(used) == 0
         rc, fr = g.render_frames(tf)
+        assert rc == 0
+        rc, _ = g.render_frame(t_end)   # the server has applied everything up to t_end
         assert rc == 0
         Sh, Th = g.state()
     assert np.array_equal(np.stack([frames[t] for t in tf]), fr)

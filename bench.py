@@ -41,6 +41,11 @@ PARAMS = dict(C=0.15, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, t_origin_us=0,
               render_decay=1)
 WORKLOAD = "config1: 640x480, 2 s, ~10M events (40 Gaussian blobs), 200 x 10 ms frames, decay view"
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the same launch shape (2 M events, 40 frames per launch);
+# profiles/esi_tile_kernel_config1_small.md, profiles/esi_bin_kernel_config1_small.md.
+NCU_TRAFFIC_PER_LAUNCH = {"esi_tile": 21141248, "esi_bin": 32484096}
+
 
 def parse_args():
     ap = argparse.ArgumentParser()
@@ -50,6 +55,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["esi", "reference"], default="esi")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e, latency and CPU-baseline legs")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="run the small profiling case (0.4 s of the stream, 40 frames, 3 renders) "
+                         "and print no bench line; for ncu captures")
     return ap.parse_args()
 
 
@@ -273,8 +281,8 @@ def bench_esi(args):
         achieved = bytes_per_launch / (tot_ms / nl / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
                 "peak_kind": f"of {peak_kind}", "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "launches": nl, "avg_launch_us": tot_ms / nl * 1e3,
-                "bytes_per_launch": bytes_per_launch}
+                "traffic": NCU_TRAFFIC_PER_LAUNCH.get(name), "launches": nl,
+                "avg_launch_us": tot_ms / nl * 1e3, "bytes_per_launch": bytes_per_launch}
     kernels = {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / max(1e-9, sum(x[1] for x in prof.values()))}
                for k, v in prof.items()}
 
@@ -445,8 +453,40 @@ def serving_leg(esi):
     return out
 
 
+def ncu_case():
+    """A small case of the same workload for kernel captures: 0.4 s of the
+    config-1 stream (about 2 M events, 32 MB, larger than L2 per render of
+    three), 40 frames per render, three renders."""
+    import torch  # noqa: F401  (CUDA context as in the bench)
+    import synth
+    from paper_2508_02238_gb300 import esi
+    sc = synth.config1(duration_s=0.4)
+    ev = synth.generate(sc)
+    span = 400_000
+    rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**PARAMS), 0)
+    esi.check(rc, "create")
+    out = torch.empty((40, sc.H, sc.W), dtype=torch.uint8, device="cuda")
+    for k in range(3):
+        esi.check(esi.esi_push_events(h, _shift(ev, k * span), len(ev), 0))
+    for k in range(3):
+        tf = np.arange(1, 41, dtype=np.int64) * WINDOW_US + k * span
+        esi.check(esi.esi_render_frames(h, tf, 40, out, 1), "render")
+    esi.check(esi.esi_synchronize(h))
+    esi.esi_destroy(h)
+    print(f"ncu case done: {len(ev)} events x 3 renders")
+
+
+def _shift(ev, dt):
+    e = ev.copy()
+    e["t"] += dt
+    return e
+
+
 def main():
     args = parse_args()
+    if args.ncu_case:
+        ncu_case()
+        return
     if args.impl == "reference":
         bench_reference(args)
     else:

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "esi_api_impl.h"
@@ -199,6 +200,38 @@ static int ensure_ring(esi_handle *h, unsigned long long need)
     return ESI_OK;
 }
 
+// Checks that ev[0..n) is non-decreasing in time and not earlier than prev,
+// and writes the times into the host mirror at ring positions tail .. tail+n.
+// Large batches are split over threads.
+static bool check_and_mirror(esi_handle *h, const esi_event *ev, size_t n, long long prev)
+{
+    const unsigned long long mask = h->cap - 1, tail = h->tail;
+    long long *mir = h->tmirror.data();
+    auto run = [&](size_t lo, size_t hi) -> bool {
+        bool ok = true;
+        long long last = lo ? ev[lo - 1].t_us : prev;
+        for (size_t i = lo; i < hi; ++i) {
+            const long long t = ev[i].t_us;
+            ok &= t >= last;
+            last = t;
+            mir[(tail + i) & mask] = t;
+        }
+        return ok;
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t nt = n < (1u << 20) ? 1 : std::min<size_t>({(size_t)hw, 16, n >> 18});
+    if (nt <= 1) return run(0, n);
+    std::vector<std::thread> th;
+    std::vector<char> ok(nt, 1);
+    const size_t per = (n + nt - 1) / nt;
+    for (size_t k = 0; k < nt; ++k)
+        th.emplace_back([&, k] { ok[k] = run(k * per, std::min(n, (k + 1) * per)) ? 1 : 0; });
+    for (auto &t : th) t.join();
+    for (char c : ok)
+        if (!c) return false;
+    return true;
+}
+
 static inline long long mirror_t(const esi_handle *h, unsigned long long a)
 {
     return h->tmirror[a & (h->cap - 1)];
@@ -378,25 +411,24 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
     long long prev = std::max(h->push_floor, h->last_event_t);
     cudaError_t e = cudaSuccess;
     if (!ev_on_device) {
-        // validate on the host before anything is queued
-        for (size_t i = 0; i < n; ++i) {
-            const long long t = ev[i].t_us;
-            if (t < prev) return ESI_ETIMEORDER;
-            prev = t;
-        }
+        // the copy starts first; the time-order check and the host mirror of
+        // the times run meanwhile (a rejected batch leaves ring slots past
+        // tail that nothing reads)
         for (unsigned long long a = h->tail, i = 0; i < n;) {
             const unsigned long long pos = a & mask;
             const unsigned long long len = std::min((unsigned long long)n - i, h->cap - pos);
             e = cudaMemcpyAsync(h->ring + pos, ev + i, len * sizeof(esi_event),
                                 cudaMemcpyHostToDevice, h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e);
-            for (unsigned long long j = 0; j < len; ++j) h->tmirror[pos + j] = ev[i + j].t_us;
             a += len;
             i += len;
         }
+        const bool ordered = check_and_mirror(h, ev, n, prev);
         // the caller may reuse its buffer as soon as this returns
         e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e);
+        if (!ordered) return ESI_ETIMEORDER;
+        prev = ev[n - 1].t_us;
     } else {
         rc = ensure_pinned(h, &h->hstage, &h->hstage_cap, n);
         if (rc) return rc;

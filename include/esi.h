@@ -90,17 +90,20 @@ typedef struct {
 } esi_stats;
 
 /*
- * Launch-shape knobs (all 0 = library default).  tile_h: rows per pixel
- * tile (4, 8, 16 or 32; tiles are 128 pixels wide).  chunk_events: events per
- * binning block (power of two, 512..8192).  batch_records: records a tile
- * sorts in shared memory at once (power of two, 1024..8192).
- * max_batch_events: events per binning pass of a render (>= chunk_events).
+ * Launch-shape knobs (all 0 = library default).  tile_w: pixels per tile
+ * row, 128 (four per thread) or 32 (one per thread: four times as many
+ * independent row walks).  tile_h: rows per tile, 4, 8 or 16 with tile_w =
+ * 128, 16 or 32 with tile_w = 32.  chunk_events: events per binning block
+ * (power of two, 512..8192).  batch_records: records a tile sorts in shared
+ * memory at once (power of two, 1024..8192).  max_batch_events: events per
+ * binning pass of a render (>= chunk_events).
  */
 typedef struct {
     int32_t tile_h;
     int32_t chunk_events;
     int32_t batch_records;
     int32_t max_batch_events;
+    int32_t tile_w;
 } esi_tuning;
 
 /* Per-kernel device time collected while profiling is on. */
@@ -224,7 +227,7 @@ typedef struct {
     int32_t max_streams;          /* default 256                             */
     int32_t frame_slots;          /* finished frames kept per stream, >= 2; default 4 */
     int32_t use_graph;            /* 1 (default): replay a captured graph    */
-    int32_t tile_h;               /* 0 = default (4, 8, 16 or 32)            */
+    int32_t tile_h;               /* rows per 128-pixel tile: 0 = 8, or 4, 16 */
     int32_t max_stream_pixels;    /* largest W * H accepted; default 1280*720 */
     int32_t _reserved[3];
 } esi_server_opts;

@@ -75,7 +75,13 @@ void prepare_params(const esi_params &p, DecayParams *dp, MapParams *mp)
 int validate_tuning(const esi_tuning &t)
 {
     auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
-    if (t.tile_h != 4 && t.tile_h != 8 && t.tile_h != 16 && t.tile_h != 32) return ESI_EINVAL;
+    if (t.tile_w == 128) {
+        if (t.tile_h != 4 && t.tile_h != 8 && t.tile_h != 16) return ESI_EINVAL;
+    } else if (t.tile_w == 32) {
+        if (t.tile_h != 16 && t.tile_h != 32) return ESI_EINVAL;
+    } else {
+        return ESI_EINVAL;
+    }
     if (!pow2(t.chunk_events) || t.chunk_events < 512 || t.chunk_events > 8192) return ESI_EINVAL;
     if (!pow2(t.batch_records) || t.batch_records < 1024 || t.batch_records > 8192) return ESI_EINVAL;
     if (t.max_batch_events < t.chunk_events) return ESI_EINVAL;
@@ -87,6 +93,7 @@ esi_tuning default_tuning(int W, int H)
     (void)W;
     (void)H;
     esi_tuning t;
+    t.tile_w = 128;
     t.tile_h = 8;
     t.chunk_events = 2048;
     t.batch_records = 4096;
@@ -100,16 +107,17 @@ esi_tuning default_tuning(int W, int H)
 static int apply_tuning(esi_handle *h, const esi_tuning &t)
 {
     h->tun = t;
-    h->tiles_x = (h->W + kTileW - 1) / kTileW;
+    h->tiles_x = (h->W + t.tile_w - 1) / t.tile_w;
     h->tiles_y = (h->H + t.tile_h - 1) / t.tile_h;
     h->n_tiles = h->tiles_x * h->tiles_y;
     int th_log2 = 0;
     while ((1 << th_log2) < t.tile_h) ++th_log2;
     h->th_log2 = th_log2;
+    h->tw_log2 = t.tile_w == 32 ? 5 : 7;
     // the binning kernel keeps per-warp counters for every tile in shared memory
     if (bin_smem_bytes(t.chunk_events, h->n_tiles) + 1024 > (size_t)kMaxSmemPerBlock) return ESI_ERANGE;
     const int max_chunks = (t.max_batch_events + t.chunk_events - 1) / t.chunk_events;
-    if (tile_smem_bytes(t.tile_h, t.batch_records, max_chunks) + tile_static_smem_bytes(t.tile_h) >
+    if (tile_smem_bytes(t.tile_h, t.batch_records, max_chunks) + tile_static_smem_bytes(t.tile_h, t.tile_w) >
         (size_t)kMaxSmemPerBlock)
         return ESI_ERANGE;
     return ESI_OK;
@@ -543,7 +551,8 @@ int esi_set_tuning(esi_handle *h, const esi_tuning *t)
     if (!h || !t) return ESI_EINVAL;
     esi_tuning d = default_tuning(h->W, h->H);
     esi_tuning n = *t;
-    if (!n.tile_h) n.tile_h = d.tile_h;
+    if (!n.tile_w) n.tile_w = d.tile_w;
+    if (!n.tile_h) n.tile_h = (n.tile_w == 32) ? 32 : d.tile_h;
     if (!n.chunk_events) n.chunk_events = d.chunk_events;
     if (!n.batch_records) n.batch_records = d.batch_records;
     if (!n.max_batch_events) n.max_batch_events = d.max_batch_events;
@@ -736,6 +745,7 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
             ba.tiles_x = h->tiles_x;
             ba.n_tiles = h->n_tiles;
             ba.th_log2 = h->th_log2;
+            ba.tw_log2 = h->tw_log2;
             ba.tile_bits = index_bits(h->n_tiles);
             ba.rec = h->rec[buf];
             ba.hrow = h->hrow[buf];
@@ -772,7 +782,7 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
         ta.status = h->dstatus;
         cudaEvent_t ev;
         rc = prof_begin(h, &ev, h->stream);
-        if (!rc) rc = cuda_fail(h, launch_tile(ta, tu.tile_h, vec, h->stream));
+        if (!rc) rc = cuda_fail(h, launch_tile(ta, tu.tile_h, tu.tile_w, vec, h->stream));
         if (!rc) rc = prof_end(h, kKindTile, ev, h->stream);
         if (!rc) rc = cuda_fail(h, cudaEventRecord(h->ev_tile[buf], h->stream));
         if (rc) return rc;

@@ -32,7 +32,7 @@ struct esi_handle {
     bool own_stream = false;
 
     esi_tuning tun{};
-    int tiles_x = 0, tiles_y = 0, n_tiles = 0, th_log2 = 0;
+    int tiles_x = 0, tiles_y = 0, n_tiles = 0, th_log2 = 0, tw_log2 = 7;
 
     float *S = nullptr;           // accumulation matrix (Alg. 2), row-major
     long long *T = nullptr;       // last decay time matrix (Alg. 2)

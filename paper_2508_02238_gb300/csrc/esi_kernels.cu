@@ -22,11 +22,11 @@
 
 #include "esi_device.cuh"
 #include "esi_internal.h"
+#include "esi_tile.cuh"
 
 namespace esi {
 
 constexpr int kBinThreads = 256;
-constexpr int kStageFrames = 256;   // per-frame constants a tile block keeps in shared memory
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
 constexpr int kWhereBinCopy = 1;
 
@@ -112,6 +112,7 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
     if (!s_copy_ok) return;
 
     const int W = a.W, H = a.H, tiles_x = a.tiles_x, thl = a.th_log2, tbits = a.tile_bits;
+    const int twl = a.tw_log2;
     const int per = chunk / NW;
     const int s0 = warp * per;
     const int s1 = min(s0 + per, nc);
@@ -126,7 +127,7 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
             const int4 e = sev[k];
             const int x = e.z & 0xffff, y = (int)((unsigned)e.z >> 16);
             if (x < W && y < H)
-                tile = (y >> thl) * tiles_x + (x >> 7);
+                tile = (y >> thl) * tiles_x + (x >> twl);
             else
                 ++drop;
         }
@@ -173,7 +174,7 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
         const int4 e = sev[k];
         const int x = e.z & 0xffff, y = (int)((unsigned)e.z >> 16);
         const long long t = ((long long)(unsigned)e.y << 32) | (unsigned)e.x;
-        const unsigned pit = ((unsigned)(y & th_mask) << 7) | (unsigned)(x & 127);
+        const unsigned pit = ((unsigned)(y & th_mask) << twl) | (unsigned)(x & ((1 << twl) - 1));
         const bool pos = (signed char)(e.w & 0xff) > 0;
         const int w = k / per;
         ssort[tstart[tile] + cnt[w * ntp + tile] + loff[k]] =
@@ -203,21 +204,15 @@ __global__ void __launch_bounds__(kBinThreads) esi_bin_tab_kernel(const unsigned
     bin_chunk(j.args, c - j.first_chunk);
 }
 
-// Shared-memory layout of the tile kernel (dynamic part).
-static __host__ __device__ inline size_t tile_layout(int batch, int n_chunks, size_t *off_b,
-                                                     size_t *off_runpre, size_t *off_runoff,
-                                                     size_t *off_lpos)
+// Dynamic shared memory a kernel may ask for: the 227 KB per block minus its
+// static part.
+cudaError_t allow_dynamic_smem_impl(const void *kernel)
 {
-    size_t o = (size_t)(batch + 2) * 8;   // batch + the next batch's first record
-    *off_b = o;
-    o += (size_t)batch * 8;
-    *off_runpre = o;
-    o += (size_t)round_up(n_chunks + 1, 4) * 4;
-    *off_runoff = o;
-    o += (size_t)round_up(n_chunks, 4) * 4;
-    *off_lpos = o;                   // record: offset inside its warp's row run
-    o += (size_t)round_up(batch, 8) * 2;
-    return o;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const int max_dyn = kMaxSmemPerBlock - (int)fa.sharedSizeBytes;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
 }
 
 size_t tile_smem_bytes(int tile_h, int batch, int n_chunks)
@@ -227,336 +222,28 @@ size_t tile_smem_bytes(int tile_h, int batch, int n_chunks)
     return tile_layout(batch, n_chunks, &a, &b, &c, &d);
 }
 
-// Largest c in [0, n) with pre[c] <= g (pre[0] = 0 <= g < pre[n]).
-__device__ __forceinline__ int run_of(const unsigned *pre, int n, unsigned g)
+
+size_t tile_static_smem_bytes(int tile_h, int tile_w)
 {
-    int lo = 0, hi = n;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (pre[mid] <= g) lo = mid; else hi = mid;
-    }
-    return lo;
+    // pixel state (S, F, O per pixel), staged frames and the sort scratch
+    return (size_t)tile_h * tile_w * 16 + (size_t)kStageFrames * sizeof(WinInfo) +
+           (size_t)tile_h * tile_h * 2 + 1024;
 }
 
-// One block per 128 x TH tile; warp w owns tile row w, lane l owns the four
-// pixels x = 4l .. 4l + 3 of that row for loads, stores and frame codes.
-// Events are applied event-parallel: a row's records are in time order, so at
-// each frame the due records go 32 at a time, one per lane; lanes holding the
-// same pixel (match_any) apply theirs in arrival order, rank by rank, to the
-// pixel state kept in shared memory.  RD: render_decay; DK: decay kind; VEC:
-// rows start 4-byte aligned (W % 4 == 0), so a lane's four pixels move as one
-// float4 / two longlong2 / one 32-bit frame word.
-template <int TH, int RD, int DK, bool VEC>
-__device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
-{
-    constexpr int NT = TH * 32;
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ unsigned short rcnt[TH][TH];   // [warp][row] counts, then offsets
-    constexpr int RB = (TH == 4) ? 2 : (TH == 8) ? 3 : (TH == 16) ? 4 : 5;  // bits of a row index
-    __shared__ unsigned rowstart[TH + 1];
-    __shared__ unsigned scan_tmp[NT / 32 + 1];
-    __shared__ long long s_tnext;
-    __shared__ WinInfo swin[kStageFrames];              // this launch's frames, if they fit
-    __shared__ __align__(16) float sS[TH][kTileW];      // S of the tile's pixels
-    __shared__ __align__(16) float sF[TH][kTileW];      // (float)(T - t_base)
-    __shared__ __align__(16) long long sO[TH][kTileW];  // T - t_base
-
-    const int R = a.batch, n_chunks = a.n_chunks;
-    size_t off_b, off_runpre, off_runoff, off_lpos;
-    tile_layout(R, n_chunks, &off_b, &off_runpre, &off_runoff, &off_lpos);
-    unsigned long long *A = reinterpret_cast<unsigned long long *>(smem);
-    unsigned long long *B = reinterpret_cast<unsigned long long *>(smem + off_b);
-    unsigned *runpre = reinterpret_cast<unsigned *>(smem + off_runpre);
-    unsigned *runoff = reinterpret_cast<unsigned *>(smem + off_runoff);
-    unsigned short *lpos = reinterpret_cast<unsigned short *>(smem + off_lpos);
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int x0 = (tile % a.tiles_x) * kTileW + 4 * lane;
-    const int y = (tile / a.tiles_x) * TH + warp;
-    const int nval = (y < a.H) ? max(0, min(4, a.W - x0)) : 0;
-    const long long pix0 = (long long)y * a.W + x0;
-    const long long tb = a.t_base;
-    const DecayParams dp = a.dp;
-    const MapParams mp = a.mp;
-    float *rS = sS[warp];
-    float *rF = sF[warp];
-    long long *rO = sO[warp];
-
-    // this tile's run in every chunk, in chunk (= arrival) order
-    for (int c = tid; c < n_chunks; c += NT) {
-        const unsigned h = a.hrow[(size_t)c * a.n_tiles + tile];
-        runpre[c] = h & 0xffffu;
-        runoff[c] = h >> 16;
-    }
-    // the launch's per-frame constants, staged in shared memory when they fit
-    const int nwin = a.w_end - a.w_begin;
-    const bool staged = nwin <= kStageFrames;
-    if (staged)
-        for (int i = tid; i < nwin; i += NT) swin[i] = a.win[a.w_begin + i];
-    __syncthreads();
-    const unsigned total = block_exclusive_scan<NT>(runpre, n_chunks, scan_tmp);
-    if (tid == 0) runpre[n_chunks] = total;
-    __syncthreads();
-    // a tile with no record and no frame in this launch keeps its state as is
-    if (total == 0 && a.w_end == a.w_begin) return;
-
-    {
-        float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        long long o4[4] = {0, 0, 0, 0};
-        if (VEC && nval == 4) {
-            const float4 v = *reinterpret_cast<const float4 *>(a.S + pix0);
-            const longlong2 t01 = *reinterpret_cast<const longlong2 *>(a.T + pix0);
-            const longlong2 t23 = *reinterpret_cast<const longlong2 *>(a.T + pix0 + 2);
-            s4[0] = v.x; s4[1] = v.y; s4[2] = v.z; s4[3] = v.w;
-            o4[0] = t01.x - tb; o4[1] = t01.y - tb; o4[2] = t23.x - tb; o4[3] = t23.y - tb;
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (q < nval) {
-                    s4[q] = a.S[pix0 + q];
-                    o4[q] = a.T[pix0 + q] - tb;
-                }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            rS[4 * lane + q] = s4[q];
-            rO[4 * lane + q] = o4[q];
-            rF[4 * lane + q] = RD ? __ll2float_rn(o4[q]) : 0.0f;
-        }
-    }
-
-
-    // Alg. 2 for a group of due records (one per valid lane, time order):
-    // S += p C; dt = t - T; S *= d(dt); T = t; clamp (Eq. 13)
-    auto apply_group = [&](unsigned long long r, bool valid) {
-        const int x = (int)((r >> 33) & 127u);
-        const unsigned peers = warp_peers_n<7>((unsigned)x, valid);
-        const unsigned rank = __popc(peers & lanemask_lt());
-        const unsigned maxr = __reduce_max_sync(kFull, valid ? rank : 0u);
-        for (unsigned k = 0; k <= maxr; ++k) {
-            if (valid && rank == k) {
-                const unsigned toff = (unsigned)r;
-                float s = rS[x] + (((r >> 32) & 1u) ? mp.C : -mp.C);
-                s = s * decay_state_k<DK>((long long)toff - rO[x], dp);
-                rS[x] = fminf(fmaxf(s, mp.s_min), mp.s_max);
-                rO[x] = (long long)toff;
-                if (RD) rF[x] = __uint2float_rn(toff);
-            }
-            __syncwarp();
-        }
-    };
-
-    int wi = a.w_begin;
-    for (unsigned b0 = 0;; b0 += (unsigned)R) {
-        const int nb = (int)min((unsigned)R, total - min(total, b0));
-        const bool last = b0 + (unsigned)R >= total;
-
-        // gather the batch (records b0 .. b0 + nb of this tile, arrival
-        // order, plus the next batch's first record): one thread per run,
-        // asynchronous copies, so every record of the batch is in flight
-        const unsigned next = last ? 0u : 1u;
-        if (nb > 0) {
-            const unsigned bend = b0 + (unsigned)nb + next;
-            const int cfirst = run_of(runpre, n_chunks, b0);
-            const int clast = run_of(runpre, n_chunks, bend - 1u);
-            for (int c = cfirst + tid; c <= clast; c += NT) {
-                const unsigned rs = max(runpre[c], b0), re = min(runpre[c + 1], bend);
-                const unsigned long long *src =
-                    a.rec + (size_t)c * a.chunk + runoff[c] + (rs - runpre[c]);
-                for (unsigned i = 0; i + rs < re; ++i) cp_async8(&A[rs - b0 + i], src + i);
-            }
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        if (tid == 0) s_tnext = last ? 0x7fffffffffffffffll : (long long)(unsigned)A[nb];
-        for (int i = tid; i < TH * TH; i += NT) (&rcnt[0][0])[i] = 0;
-        __syncthreads();
-
-        // stable counting sort of the batch by row (A -> B): each row's
-        // records stay in arrival (= time) order
-        const int sl = (nb + TH - 1) / TH;
-        const int s0 = min(warp * sl, nb), s1 = min(s0 + sl, nb);
-        for (int base = s0; base < s1; base += 32) {
-            const int k = base + lane;
-            const bool valid = k < s1;
-            const int row = valid ? (int)(A[k] >> 40) : 0;
-            const unsigned peers = warp_peers_n<RB>((unsigned)row, valid);
-            const unsigned rank = __popc(peers & lanemask_lt());
-            const unsigned pre = valid ? rcnt[warp][row] : 0u;
-            __syncwarp();
-            if (valid && rank == 0) rcnt[warp][row] = (unsigned short)(pre + __popc(peers));
-            if (valid) lpos[k] = (unsigned short)(pre + rank);
-            __syncwarp();
-        }
-        __syncthreads();
-        {
-            const int row = tid / TH, w = tid % TH;
-            const unsigned v = (tid < TH * TH) ? rcnt[w][row] : 0u;
-            unsigned tot;
-            const unsigned ex = block_exclusive_scan1<NT>(v, scan_tmp, &tot);
-            if (tid < TH * TH) {
-                rcnt[w][row] = (unsigned short)ex;
-                if (w == 0) rowstart[row] = ex;
-            }
-            if (tid == 0) rowstart[TH] = (unsigned)nb;
-        }
-        __syncthreads();
-        for (int k = tid; k < nb; k += NT) {
-            const unsigned long long r = A[k];
-            const int row = (int)(r >> 40);
-            B[rcnt[k / max(sl, 1)][row] + lpos[k]] = r;
-        }
-        __syncthreads();
-
-        // walk this warp's row, frame by frame
-        int cur = (int)rowstart[warp];
-        const int re = (int)rowstart[warp + 1];
-        const long long tnext = s_tnext;
-        while (wi < a.w_end) {
-            const WinInfo wv = staged ? swin[wi - a.w_begin] : a.win[wi];
-            if (wv.lim >= tnext) break;  // later records of this tile may be due
-            for (;;) {
-                const int k = cur + lane;
-                unsigned long long r = 0;
-                bool valid = false;
-                if (k < re) {
-                    r = B[k];
-                    valid = (long long)(unsigned)r <= wv.lim;
-                }
-                const unsigned vm = __ballot_sync(kFull, valid);
-                if (vm == 0u) break;
-                apply_group(r, valid);
-                const int nv = __popc(vm);
-                cur += nv;
-                if (nv < 32) break;
-            }
-            // Eq. 14 codes of the lane's four pixels at this frame
-            const float4 s4 = *reinterpret_cast<const float4 *>(rS + 4 * lane);
-            float v[4] = {s4.x, s4.y, s4.z, s4.w};
-            if (RD) {
-                const float4 f4 = *reinterpret_cast<const float4 *>(rF + 4 * lane);
-                v[0] *= decay_view_k<DK>(wv.tf_f - f4.x, dp);
-                v[1] *= decay_view_k<DK>(wv.tf_f - f4.y, dp);
-                v[2] *= decay_view_k<DK>(wv.tf_f - f4.z, dp);
-                v[3] *= decay_view_k<DK>(wv.tf_f - f4.w, dp);
-            }
-            unsigned code[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) code[q] = quantize_u8(fmaf(v[q], mp.scale, mp.offs));
-            unsigned char *fr =
-                (a.frame_outs ? a.frame_outs[wi] : a.frames + (long long)wi * a.P) + pix0;
-            if (VEC) {
-                if (nval == 4)
-                    *reinterpret_cast<unsigned *>(fr) =
-                        code[0] | (code[1] << 8) | (code[2] << 16) | (code[3] << 24);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q < nval) fr[q] = (unsigned char)code[q];
-            }
-            ++wi;
-        }
-        // the rest of this batch's row precedes the next batch's records
-        for (; cur < re; cur += 32) {
-            const int k = cur + lane;
-            const bool valid = k < re;
-            apply_group(valid ? B[k] : 0ull, valid);
-        }
-        if (last) break;
-        __syncthreads();  // A, B, rcnt are rewritten by the next batch
-    }
-
-    __syncwarp();
-    if (VEC && nval == 4) {
-        const float4 s4 = *reinterpret_cast<const float4 *>(rS + 4 * lane);
-        *reinterpret_cast<float4 *>(a.S + pix0) = s4;
-        *reinterpret_cast<longlong2 *>(a.T + pix0) =
-            make_longlong2(rO[4 * lane] + tb, rO[4 * lane + 1] + tb);
-        *reinterpret_cast<longlong2 *>(a.T + pix0 + 2) =
-            make_longlong2(rO[4 * lane + 2] + tb, rO[4 * lane + 3] + tb);
-    } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (q < nval) {
-                a.S[pix0 + q] = rS[4 * lane + q];
-                a.T[pix0 + q] = rO[4 * lane + q] + tb;
-            }
-    }
-}
-
-#define ESI_TILE_BOUNDS(TH) __launch_bounds__(TH * 32, (TH * 32 >= 1024) ? 1 : 1024 / (TH * 32))
-
-template <int TH, int RD, int DK, bool VEC>
-__global__ void ESI_TILE_BOUNDS(TH) esi_tile_kernel(TileArgs a)
-{
-    tile_body<TH, RD, DK, VEC>(a, blockIdx.x);
-}
-
-// Batched tiles of a serving tick: a persistent grid walks the work items
-// (stream job, tile) of one parameter variant group.
-template <int TH, int RD, int DK, bool VEC>
-__global__ void ESI_TILE_BOUNDS(TH) esi_tile_tab_kernel(const unsigned char *tab, int group)
-{
-    const TickDir *d = reinterpret_cast<const TickDir *>(tab);
-    const int n = d->n_items[group];
-    const int2 *items = reinterpret_cast<const int2 *>(tab + d->off_items[group]);
-    const TileArgs *jobs = reinterpret_cast<const TileArgs *>(tab + d->off_tilejob);
-    for (int i = blockIdx.x; i < n; i += gridDim.x) {
-        const int2 it = items[i];
-        tile_body<TH, RD, DK, VEC>(jobs[it.x], it.y);
-        __syncthreads();  // shared memory is reused by the next item
-    }
-}
-
-#define ESI_TILE_VARIANTS(TH)                                                     \
-    X(TH, 0, kDecayGeneral, false) X(TH, 0, kDecayGeneral, true)                  \
-    X(TH, 0, kDecaySquare, false) X(TH, 0, kDecaySquare, true)                    \
-    X(TH, 0, kDecayNone, false) X(TH, 0, kDecayNone, true)                        \
-    X(TH, 1, kDecayGeneral, false) X(TH, 1, kDecayGeneral, true)                  \
-    X(TH, 1, kDecaySquare, false) X(TH, 1, kDecaySquare, true)                    \
-    X(TH, 1, kDecayNone, false) X(TH, 1, kDecayNone, true)
-
-static int decay_kind(const DecayParams &dp)
+int decay_kind_of(const DecayParams &dp)
 {
     if (dp.b_mode == 4) return kDecayNone;
     if (dp.b_mode == 2) return kDecaySquare;
     return kDecayGeneral;
 }
 
-// Dynamic shared memory a kernel may ask for: the 227 KB per block minus its
-// static part.
-template <class K>
-static cudaError_t allow_dynamic_smem(K kernel)
-{
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
-    if (e != cudaSuccess) return e;
-    const int max_dyn = kMaxSmemPerBlock - (int)fa.sharedSizeBytes;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
-}
-
-size_t tile_static_smem_bytes(int tile_h)
-{
-    // pixel state (S, F, O per pixel), staged frames and the sort scratch
-    return (size_t)tile_h * kTileW * 16 + (size_t)kStageFrames * sizeof(WinInfo) +
-           (size_t)tile_h * tile_h * 2 + 1024;
-}
-
 cudaError_t set_kernel_attributes()
 {
-    cudaError_t e = allow_dynamic_smem(esi_bin_kernel);
-    if (e == cudaSuccess) e = allow_dynamic_smem(esi_bin_tab_kernel);
-    if (e != cudaSuccess) return e;
-#define X(TH, RD, DK, V)                                                                    \
-    e = allow_dynamic_smem(esi_tile_kernel<TH, RD, DK, V>);                                 \
-    if (e == cudaSuccess) e = allow_dynamic_smem(esi_tile_tab_kernel<TH, RD, DK, V>);       \
-    if (e != cudaSuccess) return e;
-    ESI_TILE_VARIANTS(4)
-    ESI_TILE_VARIANTS(8)
-    ESI_TILE_VARIANTS(16)
-    ESI_TILE_VARIANTS(32)
-#undef X
-    return cudaSuccess;
+    cudaError_t e = allow_dynamic_smem_impl((const void *)esi_bin_kernel);
+    if (e == cudaSuccess) e = allow_dynamic_smem_impl((const void *)esi_bin_tab_kernel);
+    if (e == cudaSuccess) e = set_tile_attributes_w128();
+    if (e == cudaSuccess) e = set_tile_attributes_w32();
+    return e;
 }
 
 cudaError_t launch_bin(const BinArgs &a, int n_chunks, cudaStream_t s)
@@ -574,43 +261,17 @@ cudaError_t launch_bin_batch_tab(const unsigned char *tab, int grid, int chunk, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_tile(const TileArgs &a, int tile_h, int tile_w, bool vec, cudaStream_t s)
+{
+    if (tile_w == 32) return launch_tile_w32(a, tile_h, s);
+    return launch_tile_w128(a, tile_h, vec, s);
+}
+
 cudaError_t launch_tile_batch_tab(const unsigned char *tab, int group, int grid, int tile_h, int rd,
                                   int dk, bool vec, int batch, int max_chunks, cudaStream_t s)
 {
-    const size_t smem = tile_smem_bytes(tile_h, batch, max_chunks);
-#define X(TH, RD, DK, V)                                                                  \
-    if (tile_h == TH && rd == RD && dk == DK && vec == V) {                               \
-        esi_tile_tab_kernel<TH, RD, DK, V><<<grid, TH * 32, smem, s>>>(tab, group);       \
-        return cudaGetLastError();                                                        \
-    }
-    ESI_TILE_VARIANTS(4)
-    ESI_TILE_VARIANTS(8)
-    ESI_TILE_VARIANTS(16)
-    ESI_TILE_VARIANTS(32)
-#undef X
-    return cudaErrorInvalidValue;
+    return launch_tile_tab_w128(tab, group, grid, tile_h, rd, dk, vec, batch, max_chunks, s);
 }
-
-int decay_kind_of(const DecayParams &dp) { return decay_kind(dp); }
-
-cudaError_t launch_tile(const TileArgs &a, int tile_h, bool vec, cudaStream_t s)
-{
-    const size_t smem = tile_smem_bytes(tile_h, a.batch, a.n_chunks);
-    const int rd = a.mp.render_decay ? 1 : 0;
-    const int dk = decay_kind(a.dp);
-#define X(TH, RD, DK, V)                                                          \
-    if (tile_h == TH && rd == RD && dk == DK && vec == V) {                       \
-        esi_tile_kernel<TH, RD, DK, V><<<a.n_tiles, TH * 32, smem, s>>>(a);       \
-        return cudaGetLastError();                                                \
-    }
-    ESI_TILE_VARIANTS(4)
-    ESI_TILE_VARIANTS(8)
-    ESI_TILE_VARIANTS(16)
-    ESI_TILE_VARIANTS(32)
-#undef X
-    return cudaErrorInvalidValue;
-}
-
 
 }  // namespace esi
 

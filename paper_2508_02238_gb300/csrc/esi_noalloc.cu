@@ -181,6 +181,7 @@ extern "C" int esi_render_frames_noalloc(int width, int height, const esi_params
         ba.tiles_x = tiles_x;
         ba.n_tiles = n_tiles;
         ba.th_log2 = 3;
+        ba.tw_log2 = 7;
         ba.tile_bits = index_bits(n_tiles);
         ba.rec = rec;
         ba.hrow = hrow;
@@ -211,7 +212,7 @@ extern "C" int esi_render_frames_noalloc(int width, int height, const esi_params
     ta.batch = kNaBatch;
     ta.status = st;
     const bool vec = (width % 4 == 0) && ((reinterpret_cast<uintptr_t>(frames) & 3u) == 0);
-    rc = cuda_rc(launch_tile(ta, kNaTileH, vec, s));
+    rc = cuda_rc(launch_tile(ta, kNaTileH, kTileW, vec, s));
     if (rc) return rc;
     rc = cuda_rc(cudaMemcpyAsync(&hs, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     if (!rc) rc = cuda_rc(cudaStreamSynchronize(s));

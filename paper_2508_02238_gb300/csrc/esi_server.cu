@@ -323,7 +323,7 @@ int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts, vo
     if (!opts) o.use_graph = 1;
     if (o.frame_period_us < 1 || o.max_events_per_tick < kChunk || o.max_streams < 1 ||
         o.max_streams > 4096 || o.frame_slots < 2 || o.frame_slots > 64 ||
-        (o.tile_h != 4 && o.tile_h != 8 && o.tile_h != 16 && o.tile_h != 32) ||
+        (o.tile_h != 4 && o.tile_h != 8 && o.tile_h != 16) ||
         o.max_stream_pixels < 1 || state_budget_bytes == 0)
         return ESI_EINVAL;
     esi_server *s = new (std::nothrow) esi_server();
@@ -331,7 +331,7 @@ int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts, vo
     s->opts = o;
     s->budget = state_budget_bytes;
     s->tile_h = o.tile_h;
-    s->th_log2 = o.tile_h == 4 ? 2 : o.tile_h == 8 ? 3 : o.tile_h == 16 ? 4 : 5;
+    s->th_log2 = o.tile_h == 4 ? 2 : o.tile_h == 8 ? 3 : 4;
     s->streams.resize((size_t)o.max_streams);
     // capacities: the widest stream allowed bounds the tiles per stream
     s->max_tiles = 0;
@@ -631,6 +631,7 @@ int esi_server_tick(esi_server *s, int64_t now_us)
         B.args.tiles_x = st.tiles_x;
         B.args.n_tiles = st.n_tiles;
         B.args.th_log2 = s->th_log2;
+        B.args.tw_log2 = 7;
         B.args.tile_bits = index_bits(st.n_tiles);
         B.args.rec = s->rec + (size_t)n_chunks * kChunk;
         B.args.hrow = s->hrow + hrow_off;

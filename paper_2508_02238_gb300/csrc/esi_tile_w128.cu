@@ -1,0 +1,56 @@
+// Tile kernels with 128-pixel rows (4 pixels per lane), 4, 8 or 16 rows.
+#include "esi_tile_inst.cuh"
+
+namespace esi {
+
+#define ESI_W128_VARIANTS(TH)                                                     \
+    X(TH, 0, kDecayGeneral, false) X(TH, 0, kDecayGeneral, true)                  \
+    X(TH, 0, kDecaySquare, false) X(TH, 0, kDecaySquare, true)                    \
+    X(TH, 0, kDecayNone, false) X(TH, 0, kDecayNone, true)                        \
+    X(TH, 1, kDecayGeneral, false) X(TH, 1, kDecayGeneral, true)                  \
+    X(TH, 1, kDecaySquare, false) X(TH, 1, kDecaySquare, true)                    \
+    X(TH, 1, kDecayNone, false) X(TH, 1, kDecayNone, true)
+
+#define ESI_W128_ALL ESI_W128_VARIANTS(4) ESI_W128_VARIANTS(8) ESI_W128_VARIANTS(16)
+
+cudaError_t set_tile_attributes_w128()
+{
+    cudaError_t e = cudaSuccess;
+#define X(TH, RD, DK, V)                                                                       \
+    if (e == cudaSuccess) e = allow_dynamic_smem_impl((const void *)esi_tile_kernel<TH, 4, RD, DK, V>); \
+    if (e == cudaSuccess) e = allow_dynamic_smem_impl((const void *)esi_tile_tab_kernel<TH, 4, RD, DK, V>);
+    ESI_W128_ALL
+#undef X
+    return e;
+}
+
+cudaError_t launch_tile_w128(const TileArgs &a, int tile_h, bool vec, cudaStream_t s)
+{
+    const size_t smem = tile_smem_bytes(tile_h, a.batch, a.n_chunks);
+    const int rd = a.mp.render_decay ? 1 : 0;
+    const int dk = decay_kind_of(a.dp);
+#define X(TH, RD, DK, V)                                                          \
+    if (tile_h == TH && rd == RD && dk == DK && vec == V) {                       \
+        esi_tile_kernel<TH, 4, RD, DK, V><<<a.n_tiles, TH * 32, smem, s>>>(a);    \
+        return cudaGetLastError();                                                \
+    }
+    ESI_W128_ALL
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tile_tab_w128(const unsigned char *tab, int group, int grid, int tile_h, int rd,
+                                 int dk, bool vec, int batch, int max_chunks, cudaStream_t s)
+{
+    const size_t smem = tile_smem_bytes(tile_h, batch, max_chunks);
+#define X(TH, RD, DK, V)                                                                \
+    if (tile_h == TH && rd == RD && dk == DK && vec == V) {                             \
+        esi_tile_tab_kernel<TH, 4, RD, DK, V><<<grid, TH * 32, smem, s>>>(tab, group);  \
+        return cudaGetLastError();                                                      \
+    }
+    ESI_W128_ALL
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace esi

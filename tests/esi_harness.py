@@ -73,6 +73,7 @@ class GpuStream:
             t.chunk_events = tuning.get("chunk_events", 0)
             t.batch_records = tuning.get("batch_records", 0)
             t.max_batch_events = tuning.get("max_batch_events", 0)
+            t.tile_w = tuning.get("tile_w", 0)
             esi.check(esi.esi_set_tuning(self.h, t), "esi_set_tuning")
 
     def push(self, events, on_device=False):

@@ -64,7 +64,9 @@ def test_per_frame_equals_replay_bitwise():
 
 
 TUNINGS = [
-    dict(tile_h=8), dict(tile_h=16), dict(tile_h=32),
+    dict(tile_h=4), dict(tile_h=8), dict(tile_h=16),
+    dict(tile_w=32, tile_h=16), dict(tile_w=32, tile_h=32),
+    dict(tile_w=32, tile_h=32, batch_records=1024, chunk_events=512),
     dict(chunk_events=512), dict(chunk_events=8192),
     dict(batch_records=1024), dict(batch_records=8192),
     dict(max_batch_events=4096, chunk_events=512),

@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["esi", "reference"], default="esi")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e, latency and CPU-baseline legs")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run only the two serving legs and print their JSON")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run the small profiling case (0.4 s of the stream, 40 frames, 3 renders) "
                          "and print no bench line; for ncu captures")
@@ -310,6 +312,7 @@ def bench_esi(args):
         line["e2e"] = e2e_leg(esi, torch, h, stream, sc, ev, out, total_steps, args.steps, n_windows)
         line["latency"] = latency_leg(esi, torch, sc, ev)
         line["serving"] = serving_leg(esi)
+        line["serving_mixed"] = mixed_serving_leg(esi)
     elif not args.no_extras:
         line["e2e"] = None
     esi.esi_destroy(h)
@@ -453,6 +456,105 @@ def serving_leg(esi):
     return out
 
 
+MIXED_SECONDS = 0.25
+
+
+def mixed_serving_leg(esi, seconds=MIXED_SECONDS, seed=1004):
+    """Mixed resolutions with join/leave: 16 x 1280x720 (config-2 form), 48 x
+    640x480 (config-1 form), 128 x 346x260 (config-0 form) streams, lognormal
+    rates in [0.1, 20] Mev/s, Poisson packets (1 ms mean), a quarter joining in
+    the first half and a fifth leaving in the second, admission by state
+    memory, tile height autotuned per sensor size, 100 frames/s per stream."""
+    import ctypes
+    import synth
+    ws = synth.mixed_serving(duration_s=seconds, seed=seed)
+    t_end = int(round(seconds * 1e6))
+    rng = np.random.default_rng(seed + 1)
+    evs = [synth.generate(w["scene"]) for w in ws]
+    params = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1)
+    budget = 768 << 20
+    opts = esi.esi_server_opts()
+    opts.use_graph, opts.max_streams = 1, 256
+
+    # autotuned tile height per sensor size, on 50 ms of its median-rate stream
+    tile_h = {}
+    rc, srv = esi.esi_server_create(budget, opts, 0)
+    esi.check(rc, "server")
+    for dims in sorted({(w["W"], w["H"]) for w in ws}):
+        idx = [i for i, w in enumerate(ws) if (w["W"], w["H"]) == dims]
+        med = sorted(idx, key=lambda i: ws[i]["rate"])[len(idx) // 2]
+        ev = evs[med]
+        samp = ev[ev["t"] < ws[med]["t_join_us"] + 50_000]
+        rc, sid = esi.esi_stream_open(srv, dims[0], dims[1], esi.make_params(**params))
+        esi.check(rc, "open")
+        rc, th = esi.esi_stream_autotune(srv, sid, samp, len(samp), 0)
+        esi.check(rc, "autotune")
+        tile_h[f"{dims[0]}x{dims[1]}"] = th
+        esi.check(esi.esi_stream_close(srv, sid), "close")
+    esi.esi_server_destroy(srv)
+
+    specs = []
+    items = []
+    for k, w in enumerate(ws):
+        sp = esi.esi_stream_spec()
+        sp.width, sp.height = w["W"], w["H"]
+        sp.tile_h = tile_h[f"{w['W']}x{w['H']}"]
+        sp.params = esi.make_params(**params, t_origin_us=w["t_join_us"])
+        specs.append(sp)
+        t0, t1 = w["t_join_us"], w["t_leave_us"] if w["t_leave_us"] is not None else t_end
+        items.append((t0, 0, k, ctypes.addressof(sp), 0, esi.ESI_PACKET_OPEN))
+        gaps = rng.exponential(1000.0, size=int((t1 - t0) / 1000) * 3 + 10)
+        arr = t0 + np.cumsum(gaps).astype(np.int64) + 1
+        arr = np.append(arr[arr < t1], t1)
+        ev = evs[k]
+        cuts = np.searchsorted(ev["t"], arr, side="right")
+        lo = 0
+        for a, hi in zip(arr.tolist(), cuts.tolist()):
+            items.append((a, 1, k, ev.ctypes.data + lo * 16, hi - lo, esi.ESI_PACKET_EVENTS))
+            lo = hi
+        if w["t_leave_us"] is not None:
+            items.append((t1, 2, k, 0, 0, esi.ESI_PACKET_CLOSE))
+    items.sort(key=lambda x: (x[0], x[1], x[2]))
+    pk = (esi.esi_packet * len(items))()
+    for j, (a, _, k, p_, n, kind) in enumerate(items):
+        pk[j].stream, pk[j].kind, pk[j].arrival_us, pk[j].ev, pk[j].n = k, kind, a, p_, n
+    n_ev = int(sum(len(e) for e in evs))
+    expected = sum(((w["t_leave_us"] if w["t_leave_us"] is not None else t_end) - w["t_join_us"])
+                   // 10_000 for w in ws)
+    rates = np.array([w["rate"] for w in ws])
+    out = {"workload": "config-4 form: 16 x 1280x720 + 48 x 640x480 + 128 x 346x260 streams "
+                       f"({sum(w['W'] * w['H'] for w in ws) / 1e6:.1f} M pixels), lognormal rates "
+                       f"{rates.min() / 1e6:.2f}-{rates.max() / 1e6:.2f} Mev/s (sum "
+                       f"{rates.sum() / 1e6:.0f} Mev/s), {sum(w['t_join_us'] > 0 for w in ws)} join "
+                       f"late, {sum(w['t_leave_us'] is not None for w in ws)} leave, Poisson packets "
+                       f"1 ms, 100 frames/s, {seconds} s",
+           "events": n_ev, "expected_frames": int(expected), "state_budget_bytes": budget,
+           "autotuned_tile_h": tile_h}
+    for mode in ("batched", "batched_throughput"):
+        for sp in specs:
+            sp.stream_id = -1
+        rc, srv = esi.esi_server_create(budget, opts, 0)
+        esi.check(rc, "server")
+        realtime = 1 if mode == "batched" else 0
+        t0 = time.perf_counter()
+        esi.check(esi.esi_server_run(srv, pk, len(items), 1000, t_end, realtime), "run")
+        dt = time.perf_counter() - t0
+        rc, st = esi.esi_server_get_stats(srv)
+        esi.esi_server_destroy(srv)
+        out[mode] = {"frames": int(st.frames), "events": int(st.events),
+                     "streams_admitted": int(st.streams_admitted),
+                     "streams_refused": int(st.streams_refused),
+                     "frame_latency_p50_ms": st.frame_latency_p50_ms,
+                     "frame_latency_p99_ms": st.frame_latency_p99_ms,
+                     "packet_to_frame_p50_ms": st.packet_latency_p50_ms,
+                     "packet_to_frame_p99_ms": st.packet_latency_p99_ms,
+                     "gpu_ms_per_tick": st.gpu_ms_per_tick,
+                     "kernel_launches_per_tick": int(st.kernel_launches_per_tick),
+                     "wall_s": dt, "events_per_s": n_ev / dt if realtime == 0 else None,
+                     "frames_per_s": st.frames / dt}
+    return out
+
+
 def ncu_case():
     """A small case of the same workload for kernel captures: 0.4 s of the
     config-1 stream (about 2 M events, 32 MB, larger than L2 per render of
@@ -486,6 +588,13 @@ def main():
     args = parse_args()
     if args.ncu_case:
         ncu_case()
+        return
+    if args.serving_only:
+        import torch  # noqa: F401  (CUDA context as in the bench)
+        from paper_2508_02238_gb300 import esi
+        esi.load_library(build_if_missing=True)
+        print(json.dumps({"serving": serving_leg(esi), "serving_mixed": mixed_serving_leg(esi)}),
+              flush=True)
         return
     if args.impl == "reference":
         bench_reference(args)

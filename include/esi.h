@@ -181,6 +181,23 @@ int esi_get_stats(esi_handle *h, esi_stats *out);
 int esi_set_tuning(esi_handle *h, const esi_tuning *t);
 int esi_get_tuning(esi_handle *h, esi_tuning *out);
 
+#define ESI_AUTOTUNE_FORCE 1      /* measure even when a cached choice exists  */
+#define ESI_AUTOTUNE_WIDE_ONLY 2  /* only 128-pixel tile rows (serving tiles)  */
+
+/*
+ * Choose the launch shape for this sensor: run a host sample of n events and
+ * m frame times (time-ordered, not before t_origin) through a scratch handle
+ * of the same sensor and parameters once per candidate shape (tile width and
+ * height, chunk_events, batch_records, max_batch_events), time each render
+ * with CUDA events, apply the fastest to h and write it to *chosen.  The
+ * choice is cached per (W, H, events-per-frame bucket, render mode, decay
+ * kind, flags) for the life of the process; a cached choice is applied
+ * without measuring unless flags has ESI_AUTOTUNE_FORCE.  h's state and
+ * queued events are untouched.
+ */
+int esi_autotune(esi_handle *h, const esi_event *sample, size_t n, const int64_t *t_frames,
+                 size_t m, int flags, esi_tuning *chosen);
+
 /*
  * Device-time profiling of the handle's kernels (CUDA events around each
  * launch on the handle's stream).  esi_profile_read waits, writes up to
@@ -227,7 +244,7 @@ typedef struct {
     int32_t max_streams;          /* default 256                             */
     int32_t frame_slots;          /* finished frames kept per stream, >= 2; default 4 */
     int32_t use_graph;            /* 1 (default): replay a captured graph    */
-    int32_t tile_h;               /* rows per 128-pixel tile: 0 = 8, or 4, 16 */
+    int32_t tile_h;               /* rows per 128-pixel tile of new streams: 0 = 8, or 4, 16 */
     int32_t max_stream_pixels;    /* largest W * H accepted; default 1280*720 */
     int32_t _reserved[3];
 } esi_server_opts;
@@ -250,6 +267,9 @@ typedef struct {
     uint64_t state_budget_bytes;
     int32_t streams_open;
     int32_t kernel_launches_per_tick;
+    uint64_t streams_admitted;    /* esi_stream_open calls that succeeded     */
+    uint64_t streams_refused;     /* ESI_EBUSY answers (admission refused)    */
+    uint64_t events_refused;      /* executor events of refused streams      */
 } esi_server_stats;
 
 typedef struct esi_server esi_server;
@@ -282,6 +302,21 @@ int esi_server_tick(esi_server *srv, int64_t now_us);
 int esi_stream_frame(esi_server *srv, int stream_id, uint8_t *out, int64_t *t_frame,
                      double *latency_ms);
 
+/* Tile height (4, 8 or 16 rows of 128 pixels) of one stream's work items
+ * from the next tick on; the state layout does not depend on it.  ESI_ERANGE
+ * when the stream would have more tiles than the server's tables hold. */
+int esi_stream_set_tile_h(esi_server *srv, int stream_id, int tile_h);
+
+/* Autotune one stream's tile height: time a host sample of its events (n,
+ * time-ordered, any time range) rendered at the server's frame period for
+ * each tile height on a scratch sensor of the same size and parameters (as
+ * esi_autotune), then apply the fastest (esi_stream_set_tile_h) and write it
+ * to *tile_h (may be NULL).  Choices are cached per (W, H, events-per-frame
+ * bucket, render mode, decay kind) for the process; ESI_AUTOTUNE_FORCE
+ * measures again.  The stream's state and pending events are untouched. */
+int esi_stream_autotune(esi_server *srv, int stream_id, const esi_event *sample, size_t n,
+                        int flags, int *tile_h);
+
 /* Copy a stream's state (as esi_get_state with host buffers); waits. */
 int esi_stream_state(esi_server *srv, int stream_id, float *S, int64_t *T);
 
@@ -296,13 +331,28 @@ int esi_server_reset_stats(esi_server *srv);
 void esi_server_destroy(esi_server *srv);
 
 /* One packet of a stream for the executors below. */
+#define ESI_PACKET_EVENTS 0  /* n events at ev                                      */
+#define ESI_PACKET_OPEN 1    /* esi_server_run: the stream joins; ev points to an
+                                esi_stream_spec                                    */
+#define ESI_PACKET_CLOSE 2   /* esi_server_run: the stream leaves                  */
 typedef struct {
-    int32_t stream;       /* server stream id (esi_server_run) or stream index */
-    int32_t _pad;
+    int32_t stream;       /* esi_server_run: the caller's stream slot (below);
+                             esi_plain_run: stream index                       */
+    int32_t kind;         /* ESI_PACKET_*; esi_plain_run takes only EVENTS     */
     int64_t arrival_us;   /* arrival time; the stream is complete up to it    */
     const esi_event *ev;  /* the packet's host events                          */
     uint64_t n;
 } esi_packet;
+
+/* A stream that joins during esi_server_run (ESI_PACKET_OPEN); caller-owned,
+ * valid for the call.  The executor writes stream_id. */
+typedef struct {
+    int32_t width, height;
+    int32_t tile_h;       /* 0: the server's default; else 4, 8 or 16         */
+    int32_t stream_id;    /* out: the server stream id while it is open, -1
+                             once refused admission or closed               */
+    esi_params params;    /* frames at params.t_origin_us + k * frame period   */
+} esi_stream_spec;
 
 /*
  * Serving executor: feeds packets (sorted by arrival_us) to the server as
@@ -311,6 +361,17 @@ typedef struct {
  * device.  realtime = 1 paces stream time with the wall clock (stream time 0
  * = the call), so latencies are those of live serving; realtime = 0 advances
  * tick by tick as fast as host and device allow (throughput).
+ *
+ * Streams join and leave on the packets' schedule.  An OPEN packet opens a
+ * stream (esi_stream_open, then its tile height) and binds the packet's slot
+ * to it; when admission is refused (ESI_EBUSY) the slot's later packets are
+ * dropped and counted (streams_refused, events_refused).  A CLOSE packet
+ * renders the slot's frames that are due (up to its last packet), then closes
+ * the stream (esi_stream_close: it waits for the stream's work); its events
+ * after its last frame are discarded.  After the last tick the executor ticks
+ * again at t_end_us until every due frame is issued, then waits.
+ * A slot that no OPEN packet of this call has bound names a server stream id
+ * directly (streams opened before the call).  Other errors end the call.
  */
 int esi_server_run(esi_server *srv, const esi_packet *packets, size_t n_packets,
                    int64_t tick_us, int64_t t_end_us, int realtime);

@@ -101,4 +101,14 @@ int render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int out_o
 int fill_i64(esi_handle *h, long long *dst, long long n, long long value);
 cudaError_t launch_fill_i64(long long *dst, long long n, long long value, cudaStream_t s);
 
+// Launch-shape measurement shared by esi_autotune and esi_stream_autotune:
+// cache lookup, candidate timing on a scratch handle, cache update.
+struct AutotuneKey {
+    int W, H, bucket, render_decay, decay_kind, flags;
+};
+int autotune_shapes(const AutotuneKey &key, const esi_params &prm, cudaStream_t stream,
+                    const esi_event *sample, size_t n, const int64_t *t_frames, size_t m,
+                    const std::vector<esi_tuning> &cands, bool force, esi_tuning *best);
+int autotune_bucket(size_t n, size_t m);
+
 }  // namespace esi

@@ -101,7 +101,8 @@ struct BinJob {
 
 // Directory at the start of a serving tick's device table: the batched
 // kernels find their sizes and descriptor arrays through it.
-constexpr int kTickGroups = 12;  // render mode (2) x decay kind (3) x row alignment (2)
+// tile height (3) x render mode (2) x decay kind (3) x row alignment (2)
+constexpr int kTickGroups = 36;
 struct TickDir {
     int n_chunks;
     int n_items[kTickGroups];

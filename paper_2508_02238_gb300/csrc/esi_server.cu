@@ -101,6 +101,7 @@ struct Stream {
     DecayParams dp{};
     MapParams mp{};
     int group = 0;
+    int tile_h = 8, th_log2 = 3;
     int tiles_x = 0, n_tiles = 0;
     size_t arena_off = 0, arena_bytes = 0;
     float *S = nullptr;
@@ -171,7 +172,7 @@ struct esi_server {
     Arena arena;
     std::vector<Stream> streams;
     int n_open = 0;
-    int tile_h = 8, th_log2 = 3;
+    int tile_h = 8;  // tile height of newly opened streams
 
     // capacities of one tick
     int cap_jobs = 0, cap_chunks = 0, cap_items = 0, cap_frames = 0, max_tiles = 0;
@@ -190,7 +191,7 @@ struct esi_server {
     DevStatus *dstatus = nullptr;
 
     cudaGraphExec_t gexec = nullptr;
-    unsigned graph_groups = 0;  // bit g set: the graph launches group g
+    unsigned long long graph_groups = 0;  // bit g set: the graph launches group g
     Completion *comp = nullptr;
     unsigned long long ticks_issued = 0;
     std::vector<TickRec *> inflight;
@@ -199,6 +200,7 @@ struct esi_server {
     // statistics since the last reset
     std::vector<double> frame_lat, pkt_lat;
     unsigned long long n_ticks = 0, n_frames = 0, n_events = 0, n_packets = 0;
+    unsigned long long n_admitted = 0, n_refused = 0, n_events_refused = 0;
     double gpu_ms = 0.0;
     unsigned long long gpu_n = 0;
     int launches_per_tick = 0;
@@ -262,8 +264,21 @@ int wait_all(esi_server *s)
     return rc_of(e);
 }
 
+// Variant group g: tile height index g / 12 (4, 8, 16 rows), then render
+// mode, decay kind and row alignment.
+int group_tile_h(int g) { return 4 << (g / 12); }
+int group_rd(int g) { return (g % 12) / 6; }
+int group_dk(int g) { return (g % 6) / 2; }
+bool group_vec(int g) { return g % 2 == 1; }
+
+cudaError_t launch_group(esi_server *s, int g, cudaStream_t cs)
+{
+    return launch_tile_batch_tab(s->dtab, g, s->tile_grid, group_tile_h(g), group_rd(g),
+                                 group_dk(g), group_vec(g), kBatch, kMaxChunksPerStream, cs);
+}
+
 // Capture the per-tick graph for the variant groups in `groups`.
-int build_graph(esi_server *s, unsigned groups)
+int build_graph(esi_server *s, unsigned long long groups)
 {
     if (s->gexec) {
         cudaGraphExecDestroy(s->gexec);
@@ -277,9 +292,7 @@ int build_graph(esi_server *s, unsigned groups)
     if (e == cudaSuccess)
         e = launch_bin_batch_tab(s->dtab, s->cap_chunks, kChunk, s->max_tiles, cs);
     for (int gi = 0; gi < kGroups && e == cudaSuccess; ++gi)
-        if (groups & (1u << gi))
-            e = launch_tile_batch_tab(s->dtab, gi, s->tile_grid, s->tile_h, gi / 6, (gi / 2) % 3,
-                                      gi % 2 == 1, kBatch, kMaxChunksPerStream, cs);
+        if (groups & (1ull << gi)) e = launch_group(s, gi, cs);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(cs, on_tick_done, s->comp);
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     if (e == cudaSuccess) e = e2;
@@ -294,12 +307,24 @@ int build_graph(esi_server *s, unsigned groups)
     return ESI_OK;
 }
 
-int group_of(const MapParams &mp, const DecayParams &dp, int W)
+int group_of(const MapParams &mp, const DecayParams &dp, int W, int tile_h)
 {
+    const int th = tile_h == 4 ? 0 : tile_h == 8 ? 1 : 2;
     const int rd = mp.render_decay ? 1 : 0;
     const int dk = decay_kind_of(dp);
     const int vec = (W % 4 == 0) ? 1 : 0;
-    return rd * 6 + dk * 2 + vec;
+    return th * 12 + rd * 6 + dk * 2 + vec;
+}
+
+// Tiles of a stream at tile height th (4, 8 or 16); the state layout does not
+// depend on it, so it may change between ticks.
+void set_stream_tiles(Stream &st, int th)
+{
+    st.tile_h = th;
+    st.th_log2 = th == 4 ? 2 : th == 8 ? 3 : 4;
+    st.tiles_x = (st.W + kTileW - 1) / kTileW;
+    st.n_tiles = st.tiles_x * ((st.H + th - 1) / th);
+    st.group = group_of(st.mp, st.dp, st.W, th);
 }
 
 }  // namespace
@@ -331,14 +356,15 @@ int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts, vo
     s->opts = o;
     s->budget = state_budget_bytes;
     s->tile_h = o.tile_h;
-    s->th_log2 = o.tile_h == 4 ? 2 : o.tile_h == 8 ? 3 : 4;
     s->streams.resize((size_t)o.max_streams);
-    // capacities: the widest stream allowed bounds the tiles per stream
+    // capacities: the largest stream allowed, at the smallest tile height (4
+    // rows), bounds the tiles per stream
+    constexpr int kMinTileH = 4;
     s->max_tiles = 0;
     {
         const long long maxp = o.max_stream_pixels;
         // tiles of a 128-wide layout cover at most ceil(P / 128) + rows; bound generously
-        long long t = (maxp + (long long)kTileW * o.tile_h - 1) / ((long long)kTileW * o.tile_h) +
+        long long t = (maxp + (long long)kTileW * kMinTileH - 1) / ((long long)kTileW * kMinTileH) +
                       (long long)std::sqrt((double)maxp) + 2;
         s->max_tiles = (int)std::min<long long>(t, 16384);
     }
@@ -349,7 +375,7 @@ int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts, vo
     {
         // items: every tile of every stream; bounded by the pixels the budget can hold
         const long long px_budget = (long long)(state_budget_bytes / 12);
-        const long long items = px_budget / ((long long)kTileW * o.tile_h) +
+        const long long items = px_budget / ((long long)kTileW * kMinTileH) +
                                 (long long)o.max_streams * (long long)(std::sqrt((double)o.max_stream_pixels) + 2);
         s->cap_items = (int)std::min<long long>(items, 1 << 22);
     }
@@ -455,11 +481,17 @@ int esi_stream_open(esi_server *s, int width, int height, const esi_params *para
             id = i;
             break;
         }
-    if (id < 0) return ESI_EBUSY;
+    if (id < 0) {
+        s->n_refused += 1;
+        return ESI_EBUSY;
+    }
     const long long P = (long long)width * height;
     const size_t sbytes = align_up((size_t)P * 4, 256) + (size_t)P * 8;
     const size_t off = s->arena.alloc(sbytes);
-    if (off == SIZE_MAX) return ESI_EBUSY;
+    if (off == SIZE_MAX) {
+        s->n_refused += 1;
+        return ESI_EBUSY;
+    }
     Stream &st = s->streams[id];
     st = Stream();
     st.W = width;
@@ -467,9 +499,7 @@ int esi_stream_open(esi_server *s, int width, int height, const esi_params *para
     st.P = P;
     st.prm = *params;
     prepare_params(*params, &st.dp, &st.mp);
-    st.group = group_of(st.mp, st.dp, width);
-    st.tiles_x = (width + kTileW - 1) / kTileW;
-    st.n_tiles = st.tiles_x * ((height + s->tile_h - 1) / s->tile_h);
+    set_stream_tiles(st, s->tile_h);
     if (st.n_tiles > s->max_tiles) {
         s->arena.release(off, sbytes);
         return ESI_ERANGE;
@@ -498,6 +528,7 @@ int esi_stream_open(esi_server *s, int width, int height, const esi_params *para
     st.open = true;
     s->used += sbytes;
     s->n_open += 1;
+    s->n_admitted += 1;
     *stream_id = id;
     return ESI_OK;
 }
@@ -531,6 +562,53 @@ int esi_stream_watermark(esi_server *s, int id, int64_t t_us)
     if (st.watermark != LLONG_MAX && (long long)t_us < st.watermark) return ESI_ETIMEORDER;
     st.watermark = t_us;
     return ESI_OK;
+}
+
+int esi_stream_set_tile_h(esi_server *s, int id, int tile_h)
+{
+    if (!s || id < 0 || id >= (int)s->streams.size() || !s->streams[id].open) return ESI_EINVAL;
+    if (tile_h != 4 && tile_h != 8 && tile_h != 16) return ESI_EINVAL;
+    Stream &st = s->streams[id];
+    Stream probe = st;
+    set_stream_tiles(probe, tile_h);
+    if (probe.n_tiles > s->max_tiles) return ESI_ERANGE;
+    set_stream_tiles(st, tile_h);
+    return ESI_OK;
+}
+
+int esi_stream_autotune(esi_server *s, int id, const esi_event *sample, size_t n, int flags,
+                        int *tile_h)
+{
+    if (!s || id < 0 || id >= (int)s->streams.size() || !s->streams[id].open || !sample || !n)
+        return ESI_EINVAL;
+    Stream &st = s->streams[id];
+    // frames at the server's frame period over the sample
+    std::vector<int64_t> tf;
+    const long long t_first = sample[0].t_us, t_last = sample[n - 1].t_us;
+    for (long long t = t_first + s->opts.frame_period_us; t <= t_last; t += s->opts.frame_period_us)
+        tf.push_back(t);
+    if (tf.empty()) tf.push_back(t_last);
+    std::vector<esi_tuning> cands;
+    for (int th : {4, 8, 16}) {
+        if (st.tiles_x * ((st.H + th - 1) / th) > s->max_tiles) continue;
+        esi_tuning t{};
+        t.tile_w = kTileW;
+        t.tile_h = th;
+        t.chunk_events = kChunk;
+        t.batch_records = kBatch;
+        t.max_batch_events = kMaxChunksPerStream * kChunk;
+        cands.push_back(t);
+    }
+    // the key's flags field carries a marker bit for serving shapes
+    const AutotuneKey key{st.W, st.H, autotune_bucket(n, tf.size()), st.mp.render_decay,
+                          decay_kind_of(st.dp), 0x100};
+    esi_tuning best{};
+    int rc = autotune_shapes(key, st.prm, s->stream, sample, n, tf.data(), tf.size(), cands,
+                             (flags & ESI_AUTOTUNE_FORCE) != 0, &best);
+    if (rc) return rc;
+    rc = esi_stream_set_tile_h(s, id, best.tile_h);
+    if (!rc && tile_h) *tile_h = best.tile_h;
+    return rc;
 }
 
 int esi_server_tick(esi_server *s, int64_t now_us)
@@ -630,7 +708,7 @@ int esi_server_tick(esi_server *s, int64_t now_us)
         B.args.H = st.H;
         B.args.tiles_x = st.tiles_x;
         B.args.n_tiles = st.n_tiles;
-        B.args.th_log2 = s->th_log2;
+        B.args.th_log2 = st.th_log2;
         B.args.tw_log2 = 7;
         B.args.tile_bits = index_bits(st.n_tiles);
         B.args.rec = s->rec + (size_t)n_chunks * kChunk;
@@ -689,7 +767,7 @@ int esi_server_tick(esi_server *s, int64_t now_us)
     }
     // work items, grouped by variant
     int2 *items = reinterpret_cast<int2 *>(stg + s->off_items);
-    unsigned groups = 0;
+    unsigned long long groups = 0;
     long long item_off = 0;
     for (int g = 0; g < kGroups; ++g) {
         if (!dir->n_items[g]) continue;
@@ -697,7 +775,7 @@ int esi_server_tick(esi_server *s, int64_t now_us)
             delete rec;
             return ESI_ERANGE;
         }
-        groups |= 1u << g;
+        groups |= 1ull << g;
         dir->off_items[g] = (long long)s->off_items + item_off * (long long)sizeof(int2);
         int2 *it = items + item_off;
         for (auto &js : job_stream) {
@@ -730,7 +808,7 @@ int esi_server_tick(esi_server *s, int64_t now_us)
     rec->id = s->ticks_issued;
     e = cudaEventRecord(rec->ev0, s->stream);
     int ngroups = 0;
-    for (int g = 0; g < kGroups; ++g) ngroups += (groups >> g) & 1u;
+    for (int g = 0; g < kGroups; ++g) ngroups += (int)((groups >> g) & 1ull);
     if (e == cudaSuccess) {
         if (s->opts.use_graph) {
             if (!s->gexec || (groups & ~s->graph_groups)) {
@@ -742,14 +820,12 @@ int esi_server_tick(esi_server *s, int64_t now_us)
             }
             e = cudaGraphLaunch(s->gexec, s->stream);
             int ng = 0;
-            for (int g = 0; g < kGroups; ++g) ng += (s->graph_groups >> g) & 1u;
+            for (int g = 0; g < kGroups; ++g) ng += (int)((s->graph_groups >> g) & 1ull);
             s->launches_per_tick = 1 + ng;
         } else {
             e = launch_bin_batch_tab(s->dtab, s->cap_chunks, kChunk, s->max_tiles, s->stream);
             for (int g = 0; g < kGroups && e == cudaSuccess; ++g)
-                if (groups & (1u << g))
-                    e = launch_tile_batch_tab(s->dtab, g, s->tile_grid, s->tile_h, g / 6, (g / 2) % 3,
-                                              g % 2 == 1, kBatch, kMaxChunksPerStream, s->stream);
+                if (groups & (1ull << g)) e = launch_group(s, g, s->stream);
             if (e == cudaSuccess) e = cudaLaunchHostFunc(s->stream, on_tick_done, s->comp);
             s->launches_per_tick = 1 + ngroups;
         }
@@ -831,6 +907,9 @@ int esi_server_get_stats(esi_server *s, esi_server_stats *out)
     out->state_budget_bytes = s->budget;
     out->streams_open = s->n_open;
     out->kernel_launches_per_tick = s->launches_per_tick;
+    out->streams_admitted = s->n_admitted;
+    out->streams_refused = s->n_refused;
+    out->events_refused = s->n_events_refused;
     return ESI_OK;
 }
 
@@ -841,6 +920,7 @@ int esi_server_reset_stats(esi_server *s)
     s->frame_lat.clear();
     s->pkt_lat.clear();
     s->n_ticks = s->n_frames = s->n_events = s->n_packets = 0;
+    s->n_admitted = s->n_refused = s->n_events_refused = 0;
     s->gpu_ms = 0.0;
     s->gpu_n = 0;
     return ESI_OK;
@@ -863,6 +943,31 @@ void wait_until(long long t0_ns, long long t_us)
     }
 }
 
+bool frames_due(const Stream &st, long long now)
+{
+    return st.open && st.next_frame_t <= std::min(now, st.watermark);
+}
+
+// Issue every frame of the streams selected by `which` (-1: all) that is due
+// at `now`: the last tick may have left some behind (a full tick, or the
+// frames a stream may have in flight).  Bounded; waits for ticks in flight.
+int drain_frames(esi_server *s, int which, long long now)
+{
+    for (int guard = 0; guard < 4096; ++guard) {
+        bool due = false;
+        for (int id = 0; id < (int)s->streams.size() && !due; ++id)
+            if ((which < 0 || id == which) && frames_due(s->streams[id], now)) due = true;
+        if (!due) return ESI_OK;
+        if (!s->inflight.empty()) {
+            cudaError_t e = cudaEventSynchronize(s->inflight.front()->ev1);
+            if (e != cudaSuccess) return rc_of(e);
+        }
+        int rc = esi_server_tick(s, now);
+        if (rc) return rc;
+    }
+    return ESI_ERANGE;
+}
+
 }  // namespace
 
 int esi_server_run(esi_server *s, const esi_packet *pk, size_t n, int64_t tick_us, int64_t t_end_us,
@@ -871,6 +976,26 @@ int esi_server_run(esi_server *s, const esi_packet *pk, size_t n, int64_t tick_u
     if (!s || (n && !pk) || tick_us < 1 || t_end_us < 0) return ESI_EINVAL;
     for (size_t i = 1; i < n; ++i)
         if (pk[i].arrival_us < pk[i - 1].arrival_us) return ESI_EINVAL;
+    for (size_t i = 0; i < n; ++i)
+        if (pk[i].stream < 0 || pk[i].kind < ESI_PACKET_EVENTS || pk[i].kind > ESI_PACKET_CLOSE ||
+            (pk[i].kind == ESI_PACKET_OPEN && !pk[i].ev))
+            return ESI_EINVAL;
+    // slot -> server stream id; a slot no OPEN packet has bound names a server id
+    constexpr int kUnbound = INT_MIN;
+    std::vector<int> slot_id;
+    std::vector<esi_stream_spec *> slot_spec;
+    auto sid_of = [&](int slot) {
+        return (size_t)slot < slot_id.size() && slot_id[slot] != kUnbound ? slot_id[slot] : slot;
+    };
+    auto bind = [&](int slot, int id, esi_stream_spec *spec) {
+        if ((size_t)slot >= slot_id.size()) {
+            slot_id.resize((size_t)slot + 1, kUnbound);
+            slot_spec.resize((size_t)slot + 1, nullptr);
+        }
+        slot_id[slot] = id;
+        if (spec) slot_spec[slot] = spec;
+        if (slot_spec[slot]) slot_spec[slot]->stream_id = id;
+    };
     const long long t0 = wall_ns();
     const long long min_gap = std::max<long long>(1, tick_us / 5);
     size_t i = 0;
@@ -886,8 +1011,35 @@ int esi_server_run(esi_server *s, const esi_packet *pk, size_t n, int64_t tick_u
             now = next_tick;
         }
         for (; i < n && pk[i].arrival_us <= now; ++i) {
-            int rc = esi_stream_push(s, pk[i].stream, pk[i].ev, (size_t)pk[i].n);
-            if (!rc) rc = esi_stream_watermark(s, pk[i].stream, pk[i].arrival_us);
+            const esi_packet &q = pk[i];
+            int rc = ESI_OK;
+            if (q.kind == ESI_PACKET_OPEN) {
+                // the spec is the caller's, writable: the packet carries it as ev
+                esi_stream_spec *sp = reinterpret_cast<esi_stream_spec *>(const_cast<esi_event *>(q.ev));
+                int id = -1;
+                rc = esi_stream_open(s, sp->width, sp->height, &sp->params, &id);
+                if (rc == ESI_EBUSY) {  // refused admission: its packets are dropped
+                    bind(q.stream, -1, sp);
+                    continue;
+                }
+                if (!rc && sp->tile_h) rc = esi_stream_set_tile_h(s, id, sp->tile_h);
+                if (!rc) bind(q.stream, id, sp);
+            } else {
+                const int id = sid_of(q.stream);
+                if (id < 0) {
+                    if (q.kind == ESI_PACKET_EVENTS) s->n_events_refused += q.n;
+                    continue;
+                }
+                if (q.kind == ESI_PACKET_CLOSE) {
+                    // the stream's frames up to its last packet come first
+                    rc = drain_frames(s, id, std::min<long long>(now, t_end_us));
+                    if (!rc) rc = esi_stream_close(s, id);
+                    bind(q.stream, -1, nullptr);
+                } else {
+                    rc = esi_stream_push(s, id, q.ev, (size_t)q.n);
+                    if (!rc) rc = esi_stream_watermark(s, id, q.arrival_us);
+                }
+            }
             if (rc) return rc;
         }
         // tick at the tick period, and early when a packet has made a frame due
@@ -906,6 +1058,8 @@ int esi_server_run(esi_server *s, const esi_packet *pk, size_t n, int64_t tick_u
             if (now >= t_end_us) break;
         }
     }
+    int rc = drain_frames(s, -1, t_end_us);
+    if (rc) return rc;
     return wait_all(s);
 }
 
@@ -916,6 +1070,9 @@ int esi_plain_run(int n_streams, const int *widths, const int *heights, const es
     if (n_streams < 1 || !widths || !heights || !params || (n && !pk) || tick_us < 1 ||
         frame_period_us < 1 || !out)
         return ESI_EINVAL;
+    for (size_t i = 0; i < n; ++i)
+        if (pk[i].kind != ESI_PACKET_EVENTS || pk[i].stream < 0 || pk[i].stream >= n_streams)
+            return ESI_EINVAL;
     struct PS {
         esi_handle *h = nullptr;
         std::vector<unsigned char> frame;

@@ -63,12 +63,22 @@ class esi_server_stats(ctypes.Structure):
                 ("packet_latency_p50_ms", ctypes.c_double), ("packet_latency_p99_ms", ctypes.c_double),
                 ("gpu_ms_per_tick", ctypes.c_double), ("state_bytes_used", ctypes.c_uint64),
                 ("state_budget_bytes", ctypes.c_uint64), ("streams_open", ctypes.c_int32),
-                ("kernel_launches_per_tick", ctypes.c_int32)]
+                ("kernel_launches_per_tick", ctypes.c_int32),
+                ("streams_admitted", ctypes.c_uint64), ("streams_refused", ctypes.c_uint64),
+                ("events_refused", ctypes.c_uint64)]
+
+
+ESI_PACKET_EVENTS, ESI_PACKET_OPEN, ESI_PACKET_CLOSE = 0, 1, 2
 
 
 class esi_packet(ctypes.Structure):
-    _fields_ = [("stream", ctypes.c_int32), ("_pad", ctypes.c_int32),
+    _fields_ = [("stream", ctypes.c_int32), ("kind", ctypes.c_int32),
                 ("arrival_us", ctypes.c_int64), ("ev", ctypes.c_void_p), ("n", ctypes.c_uint64)]
+
+
+class esi_stream_spec(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("tile_h", ctypes.c_int32), ("stream_id", ctypes.c_int32), ("params", esi_params)]
 
 
 _P = ctypes.c_void_p
@@ -86,6 +96,7 @@ SIGNATURES = {
     "esi_get_stats": (_i32, [_P, ctypes.POINTER(esi_stats)]),
     "esi_set_tuning": (_i32, [_P, ctypes.POINTER(esi_tuning)]),
     "esi_get_tuning": (_i32, [_P, ctypes.POINTER(esi_tuning)]),
+    "esi_autotune": (_i32, [_P, _P, _sz, _P, _sz, _i32, ctypes.POINTER(esi_tuning)]),
     "esi_profile_enable": (_i32, [_P, _i32]),
     "esi_profile_read": (_i32, [_P, ctypes.POINTER(esi_kernel_time), _i32]),
     "esi_profile_reset": (_i32, [_P]),
@@ -98,6 +109,8 @@ SIGNATURES = {
     "esi_stream_push": (_i32, [_P, _i32, _P, _sz]),
     "esi_server_tick": (_i32, [_P, _i64]),
     "esi_stream_watermark": (_i32, [_P, _i32, _i64]),
+    "esi_stream_set_tile_h": (_i32, [_P, _i32, _i32]),
+    "esi_stream_autotune": (_i32, [_P, _i32, _P, _sz, _i32, ctypes.POINTER(_i32)]),
     "esi_server_run": (_i32, [_P, _P, _sz, _i64, _i64, _i32]),
     "esi_plain_run": (_i32, [_i32, _P, _P, _P, _P, _sz, _i64, _i64, _i64, _i32,
                              ctypes.POINTER(esi_server_stats)]),
@@ -204,6 +217,18 @@ def esi_get_tuning(h):
     return rc, t
 
 
+ESI_AUTOTUNE_FORCE = 1
+ESI_AUTOTUNE_WIDE_ONLY = 2
+
+
+def esi_autotune(h, sample, n: int, t_frames, m: int, flags: int = 0):
+    """Returns (rc, chosen esi_tuning)."""
+    t = esi_tuning()
+    rc = _fn("esi_autotune")(h, _P(ptr(sample) or None), int(n), _P(ptr(t_frames) or None),
+                             int(m), int(flags), ctypes.byref(t))
+    return rc, t
+
+
 def esi_profile_enable(h, enable: int) -> int:
     return _fn("esi_profile_enable")(h, int(enable))
 
@@ -259,6 +284,18 @@ def esi_server_tick(srv, now_us: int) -> int:
 
 def esi_stream_watermark(srv, stream_id: int, t_us: int) -> int:
     return _fn("esi_stream_watermark")(srv, int(stream_id), int(t_us))
+
+
+def esi_stream_set_tile_h(srv, stream_id: int, tile_h: int) -> int:
+    return _fn("esi_stream_set_tile_h")(srv, int(stream_id), int(tile_h))
+
+
+def esi_stream_autotune(srv, stream_id: int, sample, n: int, flags: int = 0):
+    """Returns (rc, chosen tile height)."""
+    th = _i32(0)
+    rc = _fn("esi_stream_autotune")(srv, int(stream_id), _P(ptr(sample) or None), int(n),
+                                    int(flags), ctypes.byref(th))
+    return rc, int(th.value)
 
 
 def esi_server_run(srv, packets, n: int, tick_us: int, t_end_us: int, realtime: int) -> int:

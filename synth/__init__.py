@@ -68,6 +68,7 @@ class Scene(ctypes.Structure):
         ("hot_frac", ctypes.c_double), ("hot_rate_min", ctypes.c_double),
         ("hot_rate_max", ctypes.c_double), ("hot_pos_prob", ctypes.c_double),
         ("sin_phase_px", ctypes.c_double),
+        ("keep_prob", ctypes.c_double),
     ]
 
 
@@ -236,3 +237,52 @@ def lognormal_rates(n: int, seed: int, median: float = 1.0e6, sigma: float = 0.8
 
 
 CONFIGS = {0: config0, 1: config1, 2: config2}
+
+# Generated events/s of the config-1 and config-2 scenes at their default sizes
+# (over their first 0.25 s); thinning brings a stream of either form down to a
+# lower target rate.
+C1_NATURAL_RATE = 4.9e6
+C2_NATURAL_RATE = 46.0e6
+# the config-0 calibration above reaches 8 Mev/s at 346x260
+C0_MAX_RATE = 8.0e6
+
+
+def mixed_serving(duration_s: float = 0.25, seed: int = 1004, counts=(16, 48, 128),
+                  median: float = 1.0e6, sigma: float = 1.0, lo: float = 0.1e6,
+                  hi: float = 20.0e6, late_join: float = 0.25, leave: float = 0.2):
+    """Mixed-resolution serving workload: counts[0] 1280x720 config-2 form,
+    counts[1] 640x480 config-1 form and counts[2] 346x260 config-0 form
+    streams.  Rates are lognormal(median, sigma) clipped to [lo, hi] and to
+    what each scene generates.  A fraction late_join of the streams joins at a
+    seeded time in the first half (on a 1 ms grid), a fraction leave leaves at
+    a seeded time in the second half.  Each stream's scene starts at its join
+    time and ends at its leave time (or duration_s).
+
+    Returns a list of dicts: form, W, H, rate, t_join_us, t_leave_us (None if
+    it stays), scene.
+    """
+    rng = np.random.default_rng(seed)
+    forms = [2] * counts[0] + [1] * counts[1] + [0] * counts[2]
+    rates = np.clip(median * np.exp(sigma * rng.standard_normal(len(forms))), lo, hi)
+    D = int(round(duration_s * 1e6))
+    out = []
+    for i, form in enumerate(forms):
+        t_join = int(rng.integers(1, D // 2000)) * 1000 if rng.random() < late_join else 0
+        t_leave = int(rng.integers(D // 2000, D // 1000)) * 1000 if rng.random() < leave else None
+        dur = ((t_leave if t_leave is not None else D) - t_join) / 1e6
+        sd = seed * 1000 + i
+        if form == 0:
+            rate = float(min(rates[i], C0_MAX_RATE))
+            sc = config0(duration_s=dur, seed=sd, t0_us=t_join, rate_ev_s=rate,
+                         phase_px=(i * 7.3) % 20.0)
+        elif form == 1:
+            rate = float(min(rates[i], C1_NATURAL_RATE))
+            sc = config1(duration_s=dur, seed=sd, t0_us=t_join)
+            sc.keep_prob = rate / C1_NATURAL_RATE
+        else:
+            rate = float(min(rates[i], C2_NATURAL_RATE))
+            sc = config2(duration_s=dur, seed=sd, t0_us=t_join)
+            sc.keep_prob = rate / C2_NATURAL_RATE
+        out.append(dict(form=form, W=sc.W, H=sc.H, rate=rate, t_join_us=t_join,
+                        t_leave_us=t_leave, scene=sc))
+    return out

@@ -64,6 +64,9 @@ typedef struct {
     double burst_start_s[SYN_MAX_BURSTS], burst_len_s[SYN_MAX_BURSTS];
     double hot_frac, hot_rate_min, hot_rate_max, hot_pos_prob;
     double sin_phase_px;
+    /* thinning: keep each generated event with this probability (0 or >= 1:
+       keep all), from a per-pixel generator of its own */
+    double keep_prob;
 } syn_scene;
 
 /* ---------------------------------------------------------------- RNG */
@@ -482,8 +485,11 @@ syn_event *syn_generate(const syn_scene *sc, int64_t *n_out, int nthreads)
                     scene2_pixel(sc, x, y, &rs, &pb, &rscr, &rcap);
                 poisson(&pb, &rs, sc->noise_hz, T, 0.5);
                 if (pb.n > 1) qsort(pb.a, (size_t)pb.n, sizeof(pev), pev_cmp);
+                const int thin = sc->keep_prob > 0.0 && sc->keep_prob < 1.0;
+                uint64_t ks = key_state(sc->seed, 0x5151ull, pix);
                 int64_t last = 0;
                 for (int64_t i = 0; i < pb.n; ++i) {
+                    if (thin && u01(&ks) >= sc->keep_prob) continue;
                     int64_t tu = (int64_t)llround(pb.a[i].t * 1e6);
                     if (tu < last) tu = last;
                     if (tu < 0 || tu > Tus) continue;

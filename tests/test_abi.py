@@ -71,4 +71,5 @@ def test_null_handle_calls_are_rejected():
     assert esi.esi_push_events(None, None, 0, 0) == esi.ESI_EINVAL
     assert esi.esi_render_frame(None, 0, None, 0) == esi.ESI_EINVAL
     assert esi.esi_synchronize(None) == esi.ESI_EINVAL
+    assert esi.esi_autotune(None, None, 0, None, 0)[0] == esi.ESI_EINVAL
     esi.esi_destroy(None)  # no-op

@@ -4,6 +4,8 @@ Each stream of a server must give, frame for frame, what the oracle gives
 for that stream alone (parity tolerance of esi_harness), and exactly what it
 gives when served alone: streams never interact.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -49,7 +51,7 @@ def make_stream_events(i, W, H, p, kind, t_end):
                          hot=(W // 3, H // 2, 0.02))
 
 
-def drive(esi, srv, ids, events, dims, t_end, tick_us=1000, start=0):
+def drive(esi, srv, ids, events, dims, t_end, tick_us=1000, start=0, on_tick=None):
     """Push 1 ms packets, tick every ms, read every finished frame."""
     frames = {sid: {} for sid in ids}
     pos = {sid: 0 for sid in ids}
@@ -62,6 +64,8 @@ def drive(esi, srv, ids, events, dims, t_end, tick_us=1000, start=0):
                 pkt = np.ascontiguousarray(ev[pos[sid]:j])
                 assert esi.esi_stream_push(srv, sid, pkt, len(pkt)) == 0
                 pos[sid] = j
+        if on_tick is not None:
+            on_tick(now)
         assert esi.esi_server_tick(srv, now) == 0
         assert esi.esi_server_sync(srv) == 0
         for sid in ids:
@@ -73,7 +77,9 @@ def drive(esi, srv, ids, events, dims, t_end, tick_us=1000, start=0):
     return frames
 
 
-def serve(stream_specs, t_end, use_graph=1, budget=256 << 20):
+def serve(stream_specs, t_end, use_graph=1, budget=256 << 20, tile_hs=None, retile=None):
+    """tile_hs: {spec index: tile height} set at open; retile: (time, {index: tile height})
+    applied before that tick."""
     esi = _esi()
     opts = esi.esi_server_opts()
     opts.use_graph = use_graph
@@ -88,7 +94,17 @@ def serve(stream_specs, t_end, use_graph=1, budget=256 << 20):
             events[sid] = make_stream_events(i, W, H, p, kind, t_end)
             dims[sid] = (W, H)
             specs[sid] = (i, W, H, p)
-        frames = drive(esi, srv, ids, events, dims, t_end)
+            if tile_hs and i in tile_hs:
+                assert esi.esi_stream_set_tile_h(srv, sid, tile_hs[i]) == 0
+        on_tick = None
+        if retile is not None:
+            def on_tick(now):
+                if now == retile[0]:
+                    for sid in ids:
+                        th = retile[1].get(specs[sid][0])
+                        if th:
+                            assert esi.esi_stream_set_tile_h(srv, sid, th) == 0
+        frames = drive(esi, srv, ids, events, dims, t_end, on_tick=on_tick)
         states = {}
         for sid in ids:
             W, H = dims[sid]
@@ -233,5 +249,145 @@ def test_push_validation():
         assert esi.esi_stream_push(srv, 99, ev, len(ev)) == esi.ESI_EINVAL
         rc, _ = esi.esi_stream_open(srv, 5000, 5000, p)
         assert rc == esi.ESI_ERANGE
+    finally:
+        esi.esi_server_destroy(srv)
+
+
+def test_per_stream_tile_heights_are_bit_identical():
+    # tiles only organise the work: every pixel applies its events in the same
+    # order with the same arithmetic at any tile height, and the height may
+    # change between ticks
+    t_end = 60_000
+    specs = list(enumerate(STREAMS))
+    base, _ = serve(specs, t_end)
+    mixed, st = serve(specs, t_end, tile_hs={0: 4, 1: 16, 2: 4, 3: 16})
+    moved, _ = serve(specs, t_end, tile_hs={1: 4}, retile=(25_000, {0: 16, 1: 8, 2: 16, 3: 4}))
+    for other in (mixed, moved):
+        for i in range(len(STREAMS)):
+            fa, (Sa, Ta), _ = base[i]
+            fb, (Sb, Tb), _ = other[i]
+            assert sorted(fa) == sorted(fb)
+            for t in fa:
+                assert np.array_equal(fa[t], fb[t]), (i, t)
+            assert np.array_equal(Sa, Sb) and np.array_equal(Ta, Tb)
+    assert st.kernel_launches_per_tick >= 2
+
+
+def test_stream_tile_height_validation_and_autotune():
+    esi = _esi()
+    rc, srv = esi.esi_server_create(64 << 20, None, 0)
+    assert rc == 0
+    try:
+        W, H, p, kind = STREAMS[1]
+        rc, sid = esi.esi_stream_open(srv, W, H, esi.make_params(**{**dict(t_origin_us=0), **p}))
+        assert rc == 0
+        for bad in (0, 2, 12, 32):
+            assert esi.esi_stream_set_tile_h(srv, sid, bad) == esi.ESI_EINVAL
+        assert esi.esi_stream_set_tile_h(srv, sid + 1, 8) == esi.ESI_EINVAL
+        sample = make_stream_events(1, W, H, p, kind, 100_000)
+        rc, th = esi.esi_stream_autotune(srv, sid, sample, len(sample), esi.ESI_AUTOTUNE_FORCE)
+        assert rc == 0 and th in (4, 8, 16)
+        rc, th2 = esi.esi_stream_autotune(srv, sid, sample, len(sample), 0)   # cached
+        assert rc == 0 and th2 == th
+        # the stream's state is untouched (Alg. 2 initial state)
+        S = np.empty(W * H, dtype=np.float32)
+        T = np.empty(W * H, dtype=np.int64)
+        assert esi.esi_stream_state(srv, sid, S, T) == 0
+        assert np.all(S == 0) and np.all(T == 0)
+        # and the tuned stream still matches the oracle
+        ev = sample[sample["t"] <= 50_000]
+        frames = drive(esi, srv, [sid], {sid: ev}, {sid: (W, H)}, 50_000)
+        assert esi.esi_stream_state(srv, sid, S, T) == 0
+        tf = sorted(frames[sid])
+        assert tf == list(range(10_000, 50_001, 10_000))
+        pp = {**dict(t_origin_us=0), **p}
+        ref = oracle.OracleState(W, H, oracle_params(pp))
+        ref_frames, n_used = ref.replay(ev, tf)
+        ref.integrate(ev[n_used:])
+        compare({"S": S, "T": T, "frames": np.stack([frames[sid][t] for t in tf])},
+                {"S": ref.S, "T": ref.T, "frames": ref_frames}, pp["C"], "autotuned stream")
+    finally:
+        esi.esi_server_destroy(srv)
+
+
+def _state_bytes(W, H):
+    P = W * H
+    return ((P * 4 + 255) // 256 * 256 + P * 8 + 255) // 256 * 256
+
+
+def test_executor_join_leave_and_admission():
+    """Streams join and leave through the executor's OPEN / CLOSE packets; a
+    join that does not fit the state budget is refused and its events dropped;
+    a later join fits again once a stream has left."""
+    esi = _esi()
+    P = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1)
+    t_end = 60_000
+    # slot: (W, H, join, leave, rate)
+    plan = [(346, 260, 0, None, 1.5e6), (640, 480, 0, 30_000, 2.0e6),
+            (346, 260, 10_000, None, 0.8e6), (640, 480, 20_000, None, 1.0e6),
+            (640, 480, 40_000, None, 3.0e6)]
+    budget = 2 * _state_bytes(346, 260) + _state_bytes(640, 480) + 4096
+    evs, specs = [], []
+    for k, (W, H, tj, tl, rate) in enumerate(plan):
+        dur = ((tl or t_end) - tj) / 1e6
+        if W == 346:
+            sc = synth.serving_stream(k, rate, dur, t0_us=tj)
+        else:
+            sc = synth.config1(duration_s=dur, seed=5000 + k, t0_us=tj)
+            sc.keep_prob = rate / synth.C1_NATURAL_RATE
+        evs.append(synth.generate(sc))
+        sp = esi.esi_stream_spec()
+        sp.width, sp.height, sp.tile_h = W, H, (4, 8, 16, 8, 4)[k]
+        sp.params = esi.make_params(**P, t_origin_us=tj)
+        specs.append(sp)
+    items = []
+    for k, (W, H, tj, tl, rate) in enumerate(plan):
+        items.append((tj, 0, k, ctypes.addressof(specs[k]), 0, esi.ESI_PACKET_OPEN))
+        ev = evs[k]
+        lo = 0
+        for a in range(tj + 1000, (tl or t_end) + 1, 1000):
+            hi = int(np.searchsorted(ev["t"], a, side="right"))
+            items.append((a, 1, k, ev.ctypes.data + lo * 16, hi - lo, esi.ESI_PACKET_EVENTS))
+            lo = hi
+        if tl is not None:
+            items.append((tl, 2, k, 0, 0, esi.ESI_PACKET_CLOSE))
+    items.sort(key=lambda x: (x[0], x[1], x[2]))
+    pk = (esi.esi_packet * len(items))()
+    for j, (a, _, k, p_, n, kind) in enumerate(items):
+        pk[j].stream, pk[j].kind, pk[j].arrival_us, pk[j].ev, pk[j].n = k, kind, a, p_, n
+    rc, srv = esi.esi_server_create(budget, None, 0)
+    assert rc == 0
+    try:
+        assert esi.esi_server_run(srv, pk, len(items), 1000, t_end, 0) == 0
+        rc, st = esi.esi_server_get_stats(srv)
+        assert rc == 0
+        assert st.streams_admitted == 4 and st.streams_refused == 1
+        assert st.events_refused == len(evs[3])
+        assert st.streams_open == 3
+        assert [sp.stream_id >= 0 for sp in specs] == [True, False, True, False, True]
+        # frames every 10 ms from each stream's join up to the end or its leave
+        # (slot 1's 30 ms frame is rendered before it closes)
+        assert st.frames == 6 + 3 + 5 + 2
+        for k in (0, 2, 4):
+            W, H, tj, tl, rate = plan[k]
+            sid = specs[k].stream_id
+            S = np.empty(W * H, dtype=np.float32)
+            T = np.empty(W * H, dtype=np.int64)
+            assert esi.esi_stream_state(srv, sid, S, T) == 0
+            out = np.empty((H, W), dtype=np.uint8)
+            rc, tf, _ = esi.esi_stream_frame(srv, sid, out)
+            assert rc == 0 and tf == t_end
+            ev = evs[k]
+            ref = oracle.OracleState(W, H, oracle_params({**P, "t_origin_us": tj}))
+            ref_frames, n_used = ref.replay(ev, [t_end])
+            ref.integrate(ev[n_used:])
+            compare({"S": S, "T": T, "frames": out[None]},
+                    {"S": ref.S, "T": ref.T, "frames": ref_frames}, P["C"], f"slot {k}")
+        # the executor rejects malformed control packets
+        bad = (esi.esi_packet * 1)()
+        bad[0].stream, bad[0].kind, bad[0].arrival_us = 0, 7, 0
+        assert esi.esi_server_run(srv, bad, 1, 1000, 0, 0) == esi.ESI_EINVAL
+        bad[0].kind, bad[0].ev = esi.ESI_PACKET_OPEN, None
+        assert esi.esi_server_run(srv, bad, 1, 1000, 0, 0) == esi.ESI_EINVAL
     finally:
         esi.esi_server_destroy(srv)

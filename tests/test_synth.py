@@ -51,3 +51,40 @@ def test_serving_stream_rate():
     ev = synth.generate(sc)
     rate = len(ev) / 0.05
     assert 1.0e6 < rate < 3.0e6
+
+
+def _keys(ev):
+    return set(zip(ev["t"].tolist(), ev["x"].tolist(), ev["y"].tolist(), ev["p"].tolist()))
+
+
+def test_thinning_keeps_a_subset_at_the_asked_fraction():
+    sc = synth.config1(duration_s=0.05, W=160, H=120, n_blobs=10)
+    full = synth.generate(sc)
+    sc.keep_prob = 0.3
+    thin = synth.generate(sc)
+    assert np.all(np.diff(thin["t"]) >= 0)
+    # the thinning draws come from their own generator: the kept events are
+    # exactly events of the unthinned stream
+    assert _keys(thin) <= _keys(full)
+    frac = len(thin) / len(full)
+    assert abs(frac - 0.3) < 4 * np.sqrt(0.3 * 0.7 / len(full)) + 0.01, frac
+
+
+def test_mixed_serving_workload_shape():
+    ws = synth.mixed_serving(duration_s=0.1)
+    assert len(ws) == 192
+    dims = [(w["W"], w["H"]) for w in ws]
+    assert dims.count((1280, 720)) == 16 and dims.count((640, 480)) == 48
+    assert dims.count((346, 260)) == 128
+    assert sum(W * H for W, H in dims) == 41_006_080
+    for w in ws:
+        assert 0.1e6 <= w["rate"] <= 20e6
+        assert w["t_join_us"] % 1000 == 0 and 0 <= w["t_join_us"] < 50_000
+        if w["t_leave_us"] is not None:
+            assert w["t_leave_us"] % 1000 == 0 and 50_000 <= w["t_leave_us"] < 100_000
+        assert w["scene"].t0_us == w["t_join_us"]
+    assert any(w["t_join_us"] > 0 for w in ws) and any(w["t_leave_us"] for w in ws)
+    # deterministic
+    again = synth.mixed_serving(duration_s=0.1)
+    assert [(w["rate"], w["t_join_us"], w["t_leave_us"]) for w in again] == \
+        [(w["rate"], w["t_join_us"], w["t_leave_us"]) for w in ws]

@@ -130,6 +130,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, ws: int, device) -> float:
+    """The step time of the slowest rank (every rank gets it)."""
+    if ws == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: int, steps: int, ws: int, ms: float) -> float:
+    """Units all ranks processed per second over the slowest rank's time."""
+    return units_per_rank_step * steps * ws / (ms / 1e3)
+
+
 def make_stream():
     import synth
     sc = synth.config1()
@@ -255,19 +271,14 @@ def bench_esi(args):
     if ws > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
     esi.check(esi.esi_profile_enable(h, 0))
     rc, prof = esi.esi_profile_read(h)
     rc, st1 = esi.esi_get_stats(h)
     launches = int(st1.kernel_launches - st0.kernel_launches)
 
-    events_done = n_ev * args.steps * ws
-    value = events_done / (ms / 1e3)
-    frames_per_s = n_windows * args.steps * ws / (ms / 1e3)
+    value = whole_job_rate(n_ev, args.steps, ws, ms)
+    frames_per_s = whole_job_rate(n_windows, args.steps, ws, ms)
 
     # roofline of the dominant kernel (algorithmic bytes / measured duration)
     peak, peak_kind = load_peaks()

@@ -91,9 +91,9 @@ typedef struct {
 
 /*
  * Launch-shape knobs (all 0 = library default).  tile_w: pixels per tile
- * row, 128 (four per thread) or 32 (one per thread: four times as many
- * independent row walks).  tile_h: rows per tile, 4, 8 or 16 with tile_w =
- * 128, 16 or 32 with tile_w = 32.  chunk_events: events per binning block
+ * row, 128 (four per thread), 64 (two per thread) or 32 (one per thread):
+ * narrower rows give more independent row walks.  tile_h: rows per tile, 4,
+ * 8 or 16 with tile_w = 128 or 64, 16 or 32 with tile_w = 32.  chunk_events: events per binning block
  * (power of two, 512..8192).  batch_records: records a tile sorts in shared
  * memory at once (power of two, 1024..8192).  max_batch_events: events per
  * binning pass of a render (>= chunk_events).

@@ -75,7 +75,7 @@ void prepare_params(const esi_params &p, DecayParams *dp, MapParams *mp)
 int validate_tuning(const esi_tuning &t)
 {
     auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
-    if (t.tile_w == 128) {
+    if (t.tile_w == 128 || t.tile_w == 64) {
         if (t.tile_h != 4 && t.tile_h != 8 && t.tile_h != 16) return ESI_EINVAL;
     } else if (t.tile_w == 32) {
         if (t.tile_h != 16 && t.tile_h != 32) return ESI_EINVAL;
@@ -113,7 +113,7 @@ static int apply_tuning(esi_handle *h, const esi_tuning &t)
     int th_log2 = 0;
     while ((1 << th_log2) < t.tile_h) ++th_log2;
     h->th_log2 = th_log2;
-    h->tw_log2 = t.tile_w == 32 ? 5 : 7;
+    h->tw_log2 = t.tile_w == 32 ? 5 : t.tile_w == 64 ? 6 : 7;
     // the binning kernel keeps per-warp counters for every tile in shared memory
     if (bin_smem_bytes(t.chunk_events, h->n_tiles) + 1024 > (size_t)kMaxSmemPerBlock) return ESI_ERANGE;
     const int max_chunks = (t.max_batch_events + t.chunk_events - 1) / t.chunk_events;
@@ -176,12 +176,11 @@ static int ensure_ring(esi_handle *h, unsigned long long need)
     esi_event *nr = nullptr;
     cudaError_t e = cudaMalloc((void **)&nr, nc * sizeof(esi_event));
     if (e != cudaSuccess) return cuda_fail(h, e);
-    std::vector<long long> nm;
-    try {
-        nm.resize(nc);
-    } catch (...) {
+    long long *nm = nullptr;
+    e = cudaMallocHost((void **)&nm, nc * sizeof(long long));
+    if (e != cudaSuccess) {
         cudaFree(nr);
-        return ESI_ENOMEM;
+        return cuda_fail(h, e);
     }
     const unsigned long long om = h->cap ? h->cap - 1 : 0, nmk = nc - 1;
     for (unsigned long long a = h->head; a < h->tail;) {
@@ -191,6 +190,7 @@ static int ensure_ring(esi_handle *h, unsigned long long need)
                             cudaMemcpyDeviceToDevice, h->stream);
         if (e != cudaSuccess) {
             cudaFree(nr);
+            cudaFreeHost(nm);
             return cuda_fail(h, e);
         }
         std::memcpy(&nm[pn], &h->tmirror[po], len * sizeof(long long));
@@ -199,12 +199,14 @@ static int ensure_ring(esi_handle *h, unsigned long long need)
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         cudaFree(nr);
+        cudaFreeHost(nm);
         return cuda_fail(h, e);
     }
     if (h->ring) cudaFree(h->ring);
+    if (h->tmirror) cudaFreeHost(h->tmirror);
     h->ring = nr;
     h->cap = nc;
-    h->tmirror.swap(nm);
+    h->tmirror = nm;
     return ESI_OK;
 }
 
@@ -214,7 +216,7 @@ static int ensure_ring(esi_handle *h, unsigned long long need)
 static bool check_and_mirror(esi_handle *h, const esi_event *ev, size_t n, long long prev)
 {
     const unsigned long long mask = h->cap - 1, tail = h->tail;
-    long long *mir = h->tmirror.data();
+    long long *mir = h->tmirror;
     auto run = [&](size_t lo, size_t hi) -> bool {
         bool ok = true;
         long long last = lo ? ev[lo - 1].t_us : prev;
@@ -356,6 +358,11 @@ int esi_create(int width, int height, const esi_params *params, void *cuda_strea
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->hwin_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->bin_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking);
+    for (int c = 0; c < 4 && e == cudaSuccess; ++c)
+        e = cudaEventCreateWithFlags(&h->ev_chunk[c], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->dbad, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hbad, sizeof(int));
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
         e = cudaEventCreateWithFlags(&h->ev_bin[b], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_tile[b], cudaEventDisableTiming);
@@ -403,10 +410,25 @@ void esi_destroy(esi_handle *h)
     cudaFreeHost(h->hstatus);
     cudaFreeHost(h->hwin);
     if (h->hwin_ev) cudaEventDestroy(h->hwin_ev);
-    cudaFreeHost(h->hstage);
+    if (h->aux_stream) {
+        cudaStreamSynchronize(h->aux_stream);
+        cudaStreamDestroy(h->aux_stream);
+    }
+    for (int c = 0; c < 4; ++c)
+        if (h->ev_chunk[c]) cudaEventDestroy(h->ev_chunk[c]);
+    cudaFree(h->dtimes);
+    cudaFree(h->dbad);
+    cudaFreeHost(h->hbad);
+    cudaFreeHost(h->tmirror);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
 }
+
+// Pushes below this many host events are checked on the host (lowest
+// latency); larger ones and every device push are checked on the device.
+static constexpr size_t kHostCheckMax = 1u << 16;
+// events per chunk of a device-checked push
+static constexpr unsigned long long kPushChunk = 1ull << 21;
 
 int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_device)
 {
@@ -416,52 +438,79 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
     int rc = ensure_ring(h, pending + n);
     if (rc) return rc;
     const unsigned long long mask = h->cap - 1;
-    long long prev = std::max(h->push_floor, h->last_event_t);
+    const long long prev = std::max(h->push_floor, h->last_event_t);
+    const cudaMemcpyKind kind = ev_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     cudaError_t e = cudaSuccess;
-    if (!ev_on_device) {
+    // events [i0, i1) of the push into their ring slots (split at the wrap)
+    auto copy_in = [&](unsigned long long i0, unsigned long long i1) {
+        for (unsigned long long i = i0; e == cudaSuccess && i < i1;) {
+            const unsigned long long pos = (h->tail + i) & mask;
+            const unsigned long long len = std::min(i1 - i, h->cap - pos);
+            e = cudaMemcpyAsync(h->ring + pos, ev + i, len * sizeof(esi_event), kind, h->stream);
+            i += len;
+        }
+    };
+    if (!ev_on_device && n <= kHostCheckMax) {
         // the copy starts first; the time-order check and the host mirror of
         // the times run meanwhile (a rejected batch leaves ring slots past
         // tail that nothing reads)
-        for (unsigned long long a = h->tail, i = 0; i < n;) {
-            const unsigned long long pos = a & mask;
-            const unsigned long long len = std::min((unsigned long long)n - i, h->cap - pos);
-            e = cudaMemcpyAsync(h->ring + pos, ev + i, len * sizeof(esi_event),
-                                cudaMemcpyHostToDevice, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e);
-            a += len;
-            i += len;
-        }
+        copy_in(0, n);
+        if (e != cudaSuccess) return cuda_fail(h, e);
         const bool ordered = check_and_mirror(h, ev, n, prev);
         // the caller may reuse its buffer as soon as this returns
         e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e);
         if (!ordered) return ESI_ETIMEORDER;
-        prev = ev[n - 1].t_us;
     } else {
-        rc = ensure_pinned(h, &h->hstage, &h->hstage_cap, n);
+        // chunk by chunk: copy in, check on the device and compact the times
+        // (handle stream), then bring the times to the mirror (aux stream)
+        // while the next chunk is copied in
+        rc = ensure_device(h, &h->dtimes, &h->dtimes_cap, n);
         if (rc) return rc;
-        // times to the host (strided 8 of every 16 bytes) for validation and planning
-        e = cudaMemcpy2DAsync(h->hstage, sizeof(long long), ev, sizeof(esi_event),
-                              sizeof(long long), n, cudaMemcpyDeviceToHost, h->stream);
-        for (unsigned long long a = h->tail, i = 0; e == cudaSuccess && i < n;) {
-            const unsigned long long pos = a & mask;
-            const unsigned long long len = std::min((unsigned long long)n - i, h->cap - pos);
-            e = cudaMemcpyAsync(h->ring + pos, ev + i, len * sizeof(esi_event),
-                                cudaMemcpyDeviceToDevice, h->stream);
-            a += len;
-            i += len;
+        // a page-locked host buffer is read by the kernel itself over the
+        // host link (no copy-engine pass)
+        const esi_event *pull = nullptr;
+        if (!ev_on_device) {
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, ev) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+                at.devicePointer && ((uintptr_t)at.devicePointer & 15u) == 0)
+                pull = static_cast<const esi_event *>(at.devicePointer);
+            else
+                cudaGetLastError();
         }
+        e = cudaMemsetAsync(h->dbad, 0, sizeof(int), h->stream);
+        int j = 0;
+        for (unsigned long long c0 = 0; e == cudaSuccess && c0 < n; c0 += kPushChunk, ++j) {
+            const unsigned long long c1 = std::min<unsigned long long>(n, c0 + kPushChunk);
+            if (pull) {
+                e = launch_push_pull(pull, h->ring, mask, h->tail, c0, (long long)(c1 - c0), prev,
+                                     h->dtimes, h->dbad, h->stream);
+            } else {
+                copy_in(c0, c1);
+                if (e == cudaSuccess)
+                    e = launch_push_check(h->ring, mask, h->tail, c0, (long long)(c1 - c0), prev,
+                                          h->dtimes, h->dbad, h->stream);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev_chunk[j & 3], h->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux_stream, h->ev_chunk[j & 3], 0);
+            for (unsigned long long i = c0; e == cudaSuccess && i < c1;) {
+                const unsigned long long pos = (h->tail + i) & mask;
+                const unsigned long long len = std::min(c1 - i, h->cap - pos);
+                e = cudaMemcpyAsync(h->tmirror + pos, h->dtimes + i, len * sizeof(long long),
+                                    cudaMemcpyDeviceToHost, h->aux_stream);
+                i += len;
+            }
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->hbad, h->dbad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+        // the caller may reuse its buffer as soon as this returns
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->aux_stream);
         if (e != cudaSuccess) return cuda_fail(h, e);
-        for (size_t i = 0; i < n; ++i) {
-            const long long t = h->hstage[i];
-            if (t < prev) return ESI_ETIMEORDER;  // ring slots past tail are ignored
-            prev = t;
-        }
-        for (unsigned long long a = h->tail, i = 0; i < n; ++a, ++i) h->tmirror[a & mask] = h->hstage[i];
+        if (*h->hbad) return ESI_ETIMEORDER;  // ring slots past tail are ignored
     }
     h->tail += n;
-    h->last_event_t = prev;
+    h->last_event_t = h->tmirror[(h->tail - 1) & mask];
     h->pushed += n;
     return ESI_OK;
 }
@@ -704,11 +753,22 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
     if (e == cudaSuccess) e = cudaEventRecord(h->hwin_ev, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e);
     h->hwin_busy = true;
+    // host output: pinned (page-locked, mapped) buffers are written by the
+    // kernels directly; other host buffers through a device staging copy
     uint8_t *frames = out;
+    bool staged_out = false;
     if (!out_on_device) {
-        rc = ensure_device(h, &h->dframes, &h->dframes_cap, (size_t)m * (size_t)h->P);
-        if (rc) return rc;
-        frames = h->dframes;
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, out) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+            at.devicePointer) {
+            frames = static_cast<uint8_t *>(at.devicePointer);
+        } else {
+            cudaGetLastError();
+            rc = ensure_device(h, &h->dframes, &h->dframes_cap, (size_t)m * (size_t)h->P);
+            if (rc) return rc;
+            frames = h->dframes;
+            staged_out = true;
+        }
     }
     for (int b = 0; b < 2 && b < (int)plan.size(); ++b) {
         const size_t max_chunks = (size_t)((maxb + chunk - 1) / chunk);
@@ -721,8 +781,9 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->bin_stream, h->ev_start, 0);
     if (e != cudaSuccess) return cuda_fail(h, e);
     int sbi = 0;
-    // four-pixel words need 4-byte aligned rows and a 4-byte aligned output
-    const bool vec = (h->W % 4 == 0) && (((uintptr_t)frames & 3u) == 0);
+    // a lane's pixels go out as one frame word when rows and the buffer allow
+    const unsigned wb = h->tun.tile_w == 64 ? 2u : 4u;
+    const bool vec = (h->W % (int)wb == 0) && (((uintptr_t)frames & (wb - 1u)) == 0);
     for (const SubBatch &sb : plan) {
         const int nb = (int)(sb.i1 - sb.i0);
         const int n_chunks = (nb + chunk - 1) / chunk;
@@ -795,8 +856,10 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
     h->frame_floor = std::max(h->frame_floor, (long long)t_last);
     h->push_floor = std::max(h->push_floor, (long long)t_last);
     if (!out_on_device) {
-        e = cudaMemcpyAsync(out, frames, (size_t)m * (size_t)h->P, cudaMemcpyDeviceToHost, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e);
+        if (staged_out) {
+            e = cudaMemcpyAsync(out, frames, (size_t)m * (size_t)h->P, cudaMemcpyDeviceToHost, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e);
+        }
         return read_status(h);
     }
     return ESI_OK;

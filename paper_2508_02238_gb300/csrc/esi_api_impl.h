@@ -38,10 +38,19 @@ struct esi_handle {
     long long *T = nullptr;       // last decay time matrix (Alg. 2)
 
     // pending events: ring of `cap` events (power of two) on the device and a
-    // host mirror of their times; absolute indices head <= i < tail
+    // pinned host mirror of their times; absolute indices head <= i < tail
     esi_event *ring = nullptr;
     unsigned long long cap = 0, head = 0, tail = 0;
-    std::vector<long long> tmirror;
+    long long *tmirror = nullptr;
+
+    // large pushes: the device checks the time order and returns the times
+    // chunk by chunk on aux_stream while the next chunk is copied in
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t ev_chunk[4] = {nullptr, nullptr, nullptr, nullptr};
+    long long *dtimes = nullptr;         // times of the push being checked
+    size_t dtimes_cap = 0;
+    int *dbad = nullptr;                 // set when a push is out of order
+    int *hbad = nullptr;                 // pinned
 
     // binning of sub-batch i + 1 overlaps the tile kernel of sub-batch i:
     // it runs on bin_stream into the other half of the double-buffered
@@ -63,8 +72,6 @@ struct esi_handle {
     bool hwin_busy = false;
     unsigned char *dframes = nullptr;    // frames staged for host outputs
     size_t dframes_cap = 0;
-    long long *hstage = nullptr;         // pinned: times of a device push
-    size_t hstage_cap = 0;
 
     esi::DevStatus *dstatus = nullptr;
     esi::DevStatus *hstatus = nullptr;   // pinned
@@ -100,6 +107,17 @@ int init_state(esi_handle *h);
 int render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int out_on_device);
 int fill_i64(esi_handle *h, long long *dst, long long n, long long value);
 cudaError_t launch_fill_i64(long long *dst, long long n, long long value, cudaStream_t s);
+// Checks events a0 + first .. a0 + first + cnt of a push starting at ring
+// index a0: each time >= its predecessor's (prev for the push's first); sets
+// *bad otherwise; copies the times to times[first ..].
+// The same for events in a page-locked host buffer (src: its device view),
+// which the kernel also stores into their ring slots.
+cudaError_t launch_push_pull(const esi_event *src, esi_event *ring, unsigned long long mask,
+                             unsigned long long a0, unsigned long long first, long long cnt,
+                             long long prev, long long *times, int *bad, cudaStream_t s);
+cudaError_t launch_push_check(const esi_event *ring, unsigned long long mask, unsigned long long a0,
+                              unsigned long long first, long long cnt, long long prev,
+                              long long *times, int *bad, cudaStream_t s);
 
 // Launch-shape measurement shared by esi_autotune and esi_stream_autotune:
 // cache lookup, candidate timing on a scratch handle, cache update.

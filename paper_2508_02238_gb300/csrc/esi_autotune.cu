@@ -127,7 +127,7 @@ namespace {
 std::vector<esi_tuning> handle_candidates(int flags)
 {
     std::vector<esi_tuning> out;
-    const int shapes[][2] = {{128, 4}, {128, 8}, {128, 16}, {32, 16}, {32, 32}};
+    const int shapes[][2] = {{128, 4}, {128, 8}, {128, 16}, {64, 8}, {64, 16}, {32, 16}, {32, 32}};
     for (auto &sh : shapes) {
         if ((flags & ESI_AUTOTUNE_WIDE_ONLY) && sh[0] != 128) continue;
         for (int chunk : {2048, 4096})

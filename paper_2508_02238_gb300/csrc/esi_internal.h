@@ -52,7 +52,7 @@ struct BinArgs {
     long long t_base;             // record times are t - t_base (< 2^32)
     int W, H, tiles_x, n_tiles;
     int th_log2;                  // log2 of rows per tile
-    int tw_log2;                  // log2 of pixels per tile row (5 or 7)
+    int tw_log2;                  // log2 of pixels per tile row (5, 6 or 7)
     int tile_bits;                // bits of a tile index (n_tiles <= 2^tile_bits)
     unsigned long long *rec;      // out: records, block c at rec + c * chunk
     unsigned int *hrow;           // out: [chunk][tile] (start << 16 | count)
@@ -138,10 +138,12 @@ cudaError_t launch_bin(const BinArgs &a, int n_chunks, cudaStream_t s);
 cudaError_t launch_tile(const TileArgs &a, int tile_h, int tile_w, bool vec, cudaStream_t s);
 cudaError_t launch_tile_w128(const TileArgs &a, int tile_h, bool vec, cudaStream_t s);
 cudaError_t launch_tile_w32(const TileArgs &a, int tile_h, cudaStream_t s);
+cudaError_t launch_tile_w64(const TileArgs &a, int tile_h, bool vec, cudaStream_t s);
 cudaError_t launch_tile_tab_w128(const unsigned char *tab, int group, int grid, int tile_h, int rd,
                                  int dk, bool vec, int batch, int max_chunks, cudaStream_t s);
 cudaError_t set_tile_attributes_w128();
 cudaError_t set_tile_attributes_w32();
+cudaError_t set_tile_attributes_w64();
 cudaError_t launch_bin_batch_tab(const unsigned char *tab, int grid, int chunk, int max_tiles,
                                  cudaStream_t s);
 cudaError_t launch_tile_batch_tab(const unsigned char *tab, int group, int grid, int tile_h, int rd,

@@ -41,21 +41,22 @@ __device__ __forceinline__ int run_of(const unsigned *pre, int n, unsigned g)
 
 // One block per (32 PPL) x TH tile; warp w owns tile row w, lane l owns the
 // PPL pixels x = PPL l .. PPL l + PPL - 1 of that row for loads, stores and
-// frame codes (PPL = 4: 128-pixel rows; PPL = 1: 32-pixel rows, four times
-// as many independent row walks).
+// frame codes (PPL = 4: 128-pixel rows; PPL = 2: 64-pixel rows; PPL = 1:
+// 32-pixel rows: narrower rows give more independent row walks).
 // Events are applied event-parallel: a row's records are in time order, so at
 // each frame the due records go 32 at a time, one per lane; lanes holding the
 // same pixel (match_any) apply theirs in arrival order, rank by rank, to the
 // pixel state kept in shared memory.  RD: render_decay; DK: decay kind; VEC
-// (PPL = 4 only): rows start 4-byte aligned (W % 4 == 0), so a lane's four
-// pixels move as one float4 / two longlong2 / one 32-bit frame word.
+// (PPL = 4 or 2): rows start PPL-byte aligned (W % PPL == 0), so a lane's
+// pixels move as one float4 / two longlong2 / one 32-bit frame word (PPL = 4)
+// or one 16-bit frame word (PPL = 2).
 template <int TH, int PPL, int RD, int DK, bool VEC>
 __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
 {
     constexpr int NT = TH * 32;
     constexpr int TWP = 32 * PPL;              // pixels per tile row
-    constexpr int XB = (PPL == 4) ? 7 : 5;     // bits of x within the row
-    static_assert(PPL == 1 || PPL == 4, "1 or 4 pixels per lane");
+    constexpr int XB = (PPL == 4) ? 7 : (PPL == 2) ? 6 : 5;   // bits of x within the row
+    static_assert(PPL == 1 || PPL == 2 || PPL == 4, "1, 2 or 4 pixels per lane");
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned short rcnt[TH][TH];   // [warp][row] counts, then offsets
     constexpr int RB = (TH == 4) ? 2 : (TH == 8) ? 3 : (TH == 16) ? 4 : 5;  // bits of a row index
@@ -280,6 +281,22 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
                         if (q < nval) fr[q] = (unsigned char)code[q];
+                }
+            } else if constexpr (PPL == 2) {
+                const float2 s2 = *reinterpret_cast<const float2 *>(rS + 2 * lane);
+                float v0 = s2.x, v1 = s2.y;
+                if (RD) {
+                    const float2 f2 = *reinterpret_cast<const float2 *>(rF + 2 * lane);
+                    v0 *= decay_view_k<DK>(wv.tf_f - f2.x, dp);
+                    v1 *= decay_view_k<DK>(wv.tf_f - f2.y, dp);
+                }
+                const unsigned c0 = quantize_u8(fmaf(v0, mp.scale, mp.offs));
+                const unsigned c1 = quantize_u8(fmaf(v1, mp.scale, mp.offs));
+                if (VEC) {
+                    if (nval == 2) *reinterpret_cast<unsigned short *>(fr) = (unsigned short)(c0 | (c1 << 8));
+                } else {
+                    if (nval > 0) fr[0] = (unsigned char)c0;
+                    if (nval > 1) fr[1] = (unsigned char)c1;
                 }
             } else {
                 float v = rS[lane];

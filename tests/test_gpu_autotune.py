@@ -22,7 +22,8 @@ def _need_cuda():
 
 
 def _valid(t):
-    return ((t.tile_w, t.tile_h) in {(128, 4), (128, 8), (128, 16), (32, 16), (32, 32)}
+    return ((t.tile_w, t.tile_h) in {(128, 4), (128, 8), (128, 16), (64, 8), (64, 16), (32, 16),
+                                     (32, 32)}
             and t.chunk_events in (2048, 4096) and t.batch_records in (2048, 4096)
             and t.max_batch_events in (1 << 21, 1 << 23))
 

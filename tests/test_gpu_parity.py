@@ -66,6 +66,8 @@ def test_per_frame_equals_replay_bitwise():
 TUNINGS = [
     dict(tile_h=4), dict(tile_h=8), dict(tile_h=16),
     dict(tile_w=32, tile_h=16), dict(tile_w=32, tile_h=32),
+    dict(tile_w=64, tile_h=4), dict(tile_w=64, tile_h=8), dict(tile_w=64, tile_h=16),
+    dict(tile_w=64, tile_h=8, batch_records=2048, chunk_events=1024),
     dict(tile_w=32, tile_h=32, batch_records=1024, chunk_events=512),
     dict(chunk_events=512), dict(chunk_events=8192),
     dict(batch_records=1024), dict(batch_records=8192),
@@ -386,3 +388,62 @@ def test_clamp_free_alg1_matches_oracle():
     p = P(k_per_s=5.0, b=2.7, s_min=-1e30, s_max=1e30)
     tf = [500_000, 1_000_000]
     compare(run_gpu(ev, W, H, p, tf), run_oracle(ev, W, H, p, tf), p["C"])
+
+
+def test_launch_shapes_bit_identical_on_an_odd_width():
+    # odd width: no row starts aligned, every width takes the per-pixel path
+    rng = np.random.default_rng(41)
+    W, H = 201, 77
+    ev = random_events(rng, W, H, 40_000, 0, 400_000, hot=(200, 76, 0.05))
+    p = P(render_decay=1)
+    tf = np.arange(10_000, 400_001, 10_000)
+    ref = run_gpu(ev, W, H, p, tf)
+    compare(ref, run_oracle(ev, W, H, p, tf), p["C"])
+    for t in (dict(tile_w=64, tile_h=8), dict(tile_w=64, tile_h=4), dict(tile_w=32, tile_h=16),
+              dict(tile_w=128, tile_h=16)):
+        g = run_gpu(ev, W, H, p, tf, tuning=t)
+        assert np.array_equal(g["S"], ref["S"]), t
+        assert np.array_equal(g["T"], ref["T"]), t
+        assert np.array_equal(g["frames"], ref["frames"]), t
+
+
+def test_large_pushes_are_checked_on_the_device():
+    # pushes above 65536 events are checked chunk by chunk (2^21 events) on the
+    # device: violations inside a chunk, across a chunk boundary and against
+    # the previous push reject the whole push; a valid one goes through
+    rng = np.random.default_rng(14)
+    W, H = 64, 48
+    n = (1 << 21) + 300_000
+    ev = random_events(rng, W, H, n, 1_000, 60_000_000)
+    p = P(render_decay=1)
+    with GpuStream(W, H, p) as g:
+        import torch
+
+        def pinned(a):
+            # page-locked host copy: read by the kernel itself over the host link
+            t = torch.empty(a.nbytes, dtype=torch.uint8, pin_memory=True)
+            t.numpy()[:] = a.view(np.uint8)
+            return t
+
+        for where in (70_000, (1 << 21), (1 << 21) - 1, n - 1):
+            bad = ev.copy()
+            bad["t"][where] = bad["t"][where - 1] - 1
+            assert g.push(bad) == g.esi.ESI_ETIMEORDER, where
+            assert g.push(bad, on_device=True) == g.esi.ESI_ETIMEORDER, where
+            assert g.esi.esi_push_events(g.h, pinned(bad), n, 0) == g.esi.ESI_ETIMEORDER, where
+            assert g.stats().events_pushed == 0
+        half = n // 2
+        assert g.push(ev[:half]) == 0
+        back = ev[half:].copy()
+        back["t"][0] = ev["t"][half - 1] - 1          # earlier than the last pushed
+        assert g.push(back) == g.esi.ESI_ETIMEORDER
+        assert g.esi.esi_push_events(g.h, pinned(back), len(back), 0) == g.esi.ESI_ETIMEORDER
+        third = half + (n - half) // 2
+        assert g.esi.esi_push_events(g.h, pinned(ev[half:third]), third - half, 0) == 0
+        assert g.push(ev[third:], on_device=True) == 0
+        tf = np.arange(1_000_000, 60_000_001, 1_000_000)
+        rc, fr = g.render_frames(tf)
+        assert rc == 0
+        S, T = g.state()
+    ref = run_oracle(ev, W, H, p, tf)
+    compare({"S": S, "T": T, "frames": fr}, ref, p["C"], "large pushes")

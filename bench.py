@@ -44,7 +44,7 @@ WORKLOAD = "config1: 640x480, 2 s, ~10M events (40 Gaussian blobs), 200 x 10 ms 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the same launch shape (2 M events, 40 frames per launch);
 # profiles/esi_tile_kernel_config1_small.md, profiles/esi_bin_kernel_config1_small.md.
-NCU_TRAFFIC_PER_LAUNCH = {"esi_tile": 21141248, "esi_bin": 32484096}
+NCU_TRAFFIC_PER_LAUNCH = {"esi_tile": 21133568, "esi_bin": 32484352}
 
 
 def parse_args():

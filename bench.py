@@ -337,29 +337,48 @@ def bench_esi(args):
 
 
 def e2e_leg(esi, torch, h, stream, sc, ev, out, k0, steps, n_windows):
-    """Steps through the public API with pinned host input and output."""
+    """Steps through the public API with pinned host input and output.
+
+    Pipelined (the reported value): each step pushes its events from host
+    memory (the call returns once they are on the device) and queues its
+    render into a host buffer (out_on_device = 2), so the next step's push
+    overlaps this step's render; one esi_synchronize ends the timed region.
+    Synchronous (reported beside it): each render waits for its frames."""
     n_ev = len(ev)
+    steps = min(steps, 6)   # distinct pinned inputs: 2 x steps + 4 of 160 MB each
     host_in = []
-    for i in range(steps + 1):
+    for i in range(2 * steps + 4):
         buf = torch.empty(n_ev * 16, dtype=torch.uint8, pin_memory=True)
         buf.numpy().view(ev.dtype)[:] = shifted(ev, k0 + i)
         host_in.append(buf)
-    host_out = torch.empty((n_windows, sc.H, sc.W), dtype=torch.uint8, pin_memory=True)
+    host_out = [torch.empty((n_windows, sc.H, sc.W), dtype=torch.uint8, pin_memory=True)
+                for _ in range(2)]
 
-    def step(i):
+    def step(i, mode):
         esi.check(esi.esi_push_events(h, host_in[i], n_ev, 0), "push")
         esi.check(esi.esi_render_frames(h, frame_times(k0 + i, n_windows), n_windows,
-                                        host_out, 0), "render")
+                                        host_out[i % 2], mode), "render")
 
-    step(0)  # warm
+    def run(first, mode):
+        t0 = time.perf_counter()
+        for i in range(first, first + steps):
+            step(i, mode)
+        esi.check(esi.esi_synchronize(h), "sync")
+        return time.perf_counter() - t0
+
+    step(0, 0)  # warm, both modes
+    step(1, 2)
+    step(2, 2)
+    esi.check(esi.esi_synchronize(h), "sync")
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for i in range(1, steps + 1):
-        step(i)
-    dt = time.perf_counter() - t0
+    dt = run(3, 2)
+    dt_sync = run(3 + steps, 0)
     return {"value": n_ev * steps / dt, "unit": "events/s",
             "h2d_bytes_per_step": n_ev * 16, "d2h_bytes_per_step": n_windows * sc.W * sc.H,
-            "frames_per_s": n_windows * steps / dt}
+            "frames_per_s": n_windows * steps / dt,
+            "mode": "pipelined: push of step k+1 overlaps the render of step k (out_on_device=2)",
+            "synchronous": {"value": n_ev * steps / dt_sync, "unit": "events/s",
+                            "mode": "each render waits for its frames (out_on_device=0)"}}
 
 
 def latency_leg(esi, torch, sc, ev):

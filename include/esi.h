@@ -144,8 +144,12 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
  * loop; a frame at t shows the events t_n <= t, the condition under Eq. 5)
  * and write the Eq. 14 frame, W * H bytes row-major (y * W + x), to out.
  * Later events stay queued.  t_frame_us must not be earlier than the
- * previous frame or t_origin (ESI_ETIMEORDER).  out_on_device selects a
- * device or host buffer; with a host buffer the call waits for the frame.
+ * previous frame or t_origin (ESI_ETIMEORDER).  out_on_device: 1 = device
+ * buffer (the call returns once the work is queued); 0 = host buffer, the
+ * call waits for the frame; 2 = host buffer, the call returns once the work
+ * is queued and the frame is complete after esi_synchronize (or any call
+ * that waits).  A page-locked host buffer is written by the kernels
+ * directly; another one through a device copy.
  */
 int esi_render_frame(esi_handle *h, int64_t t_frame_us, uint8_t *out, int out_on_device);
 

@@ -7,7 +7,6 @@
 #include <cstring>
 #include <new>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "esi_api_impl.h"
@@ -176,10 +175,12 @@ static int ensure_ring(esi_handle *h, unsigned long long need)
     esi_event *nr = nullptr;
     cudaError_t e = cudaMalloc((void **)&nr, nc * sizeof(esi_event));
     if (e != cudaSuccess) return cuda_fail(h, e);
-    long long *nm = nullptr;
+    long long *nm = nullptr, *ns = nullptr;
     e = cudaMallocHost((void **)&nm, nc * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ns, nc / kSparse * sizeof(long long));
     if (e != cudaSuccess) {
         cudaFree(nr);
+        cudaFreeHost(nm);
         return cuda_fail(h, e);
     }
     const unsigned long long om = h->cap ? h->cap - 1 : 0, nmk = nc - 1;
@@ -191,71 +192,144 @@ static int ensure_ring(esi_handle *h, unsigned long long need)
         if (e != cudaSuccess) {
             cudaFree(nr);
             cudaFreeHost(nm);
+            cudaFreeHost(ns);
             return cuda_fail(h, e);
         }
         std::memcpy(&nm[pn], &h->tmirror[po], len * sizeof(long long));
         a += len;
     }
+    // the sparse times of the pending events (and of the block holding head)
+    const unsigned long long g_from = h->head / kSparse * kSparse;
+    if (h->cap)
+        for (unsigned long long g = std::max(g_from, h->sparse_from); g < h->tail; g += kSparse)
+            ns[(g / kSparse) & (nc / kSparse - 1)] = h->tsparse[(g / kSparse) & (h->cap / kSparse - 1)];
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         cudaFree(nr);
         cudaFreeHost(nm);
+        cudaFreeHost(ns);
         return cuda_fail(h, e);
     }
     if (h->ring) cudaFree(h->ring);
     if (h->tmirror) cudaFreeHost(h->tmirror);
+    if (h->tsparse) cudaFreeHost(h->tsparse);
     h->ring = nr;
     h->cap = nc;
     h->tmirror = nm;
+    h->tsparse = ns;
+    h->sparse_from = std::max(g_from, h->sparse_from);
     return ESI_OK;
 }
 
 // Checks that ev[0..n) is non-decreasing in time and not earlier than prev,
-// and writes the times into the host mirror at ring positions tail .. tail+n.
-// Large batches are split over threads.
+// and writes the times into the host mirrors at ring positions tail .. tail+n
+// (pushes of at most kHostCheckMax events).
 static bool check_and_mirror(esi_handle *h, const esi_event *ev, size_t n, long long prev)
 {
     const unsigned long long mask = h->cap - 1, tail = h->tail;
     long long *mir = h->tmirror;
-    auto run = [&](size_t lo, size_t hi) -> bool {
-        bool ok = true;
-        long long last = lo ? ev[lo - 1].t_us : prev;
-        for (size_t i = lo; i < hi; ++i) {
-            const long long t = ev[i].t_us;
-            ok &= t >= last;
-            last = t;
-            mir[(tail + i) & mask] = t;
-        }
-        return ok;
-    };
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const size_t nt = n < (1u << 20) ? 1 : std::min<size_t>({(size_t)hw, 16, n >> 18});
-    if (nt <= 1) return run(0, n);
-    std::vector<std::thread> th;
-    std::vector<char> ok(nt, 1);
-    const size_t per = (n + nt - 1) / nt;
-    for (size_t k = 0; k < nt; ++k)
-        th.emplace_back([&, k] { ok[k] = run(k * per, std::min(n, (k + 1) * per)) ? 1 : 0; });
-    for (auto &t : th) t.join();
-    for (char c : ok)
-        if (!c) return false;
-    return true;
-}
-
-static inline long long mirror_t(const esi_handle *h, unsigned long long a)
-{
-    return h->tmirror[a & (h->cap - 1)];
-}
-
-// First absolute index in [lo, hi) whose time is > v (times non-decreasing).
-static unsigned long long upper_bound_t(const esi_handle *h, unsigned long long lo,
-                                        unsigned long long hi, long long v)
-{
-    while (lo < hi) {
-        const unsigned long long mid = lo + (hi - lo) / 2;
-        if (mirror_t(h, mid) <= v) lo = mid + 1; else hi = mid;
+    bool ok = true;
+    long long last = prev;
+    for (size_t i = 0; i < n; ++i) {
+        const long long t = ev[i].t_us;
+        ok &= t >= last;
+        last = t;
+        mir[(tail + i) & mask] = t;
     }
-    return lo;
+    const unsigned long long smask = h->cap / kSparse - 1;
+    for (unsigned long long g = (tail + kSparse - 1) / kSparse * kSparse; g < tail + n; g += kSparse)
+        h->tsparse[(g / kSparse) & smask] = ev[g - tail].t_us;
+    return ok;
+}
+
+// ------------------------------------------------ times for planning
+// Is the sparse time of absolute index g (a multiple of kSparse) held?
+static bool sparse_ok(const esi_handle *h, unsigned long long g)
+{
+    return g >= h->sparse_from && g < h->tail && g + h->cap >= h->tail;
+}
+
+static long long sparse_t(const esi_handle *h, unsigned long long g)
+{
+    return h->tsparse[(g / kSparse) & (h->cap / kSparse - 1)];
+}
+
+// Exact times of pending indices [a0, a1) (at most 2 kSparse of them) into
+// out: from the mirror when host pushes checked all of them, otherwise read
+// back from the ring (a short copy on the auxiliary stream).
+static int block_times(esi_handle *h, unsigned long long a0, unsigned long long a1, long long *out)
+{
+    if (a1 <= a0) return ESI_OK;
+    bool exact = false;
+    for (const auto &sp : h->exact_spans)
+        if (sp.first <= a0 && a1 <= sp.second) exact = true;
+    const unsigned long long mask = h->cap - 1;
+    if (exact) {
+        for (unsigned long long a = a0; a < a1; ++a) out[a - a0] = h->tmirror[a & mask];
+        return ESI_OK;
+    }
+    cudaError_t e = cudaSuccess;
+    for (unsigned long long a = a0; e == cudaSuccess && a < a1;) {
+        const unsigned long long pos = a & mask;
+        const unsigned long long len = std::min(a1 - a, h->cap - pos);
+        e = cudaMemcpyAsync(h->hfetch + (a - a0), h->ring + pos, len * sizeof(esi_event),
+                            cudaMemcpyDeviceToHost, h->aux_stream);
+        a += len;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->aux_stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    for (unsigned long long a = a0; a < a1; ++a) out[a - a0] = h->hfetch[a - a0].t_us;
+    return ESI_OK;
+}
+
+static int exact_t(esi_handle *h, unsigned long long a, long long *t)
+{
+    return block_times(h, a, a + 1, t);
+}
+
+// A time <= that of pending index a, no earlier than it by 2^31 us or more
+// (the sparse time of its block, or the exact one).
+static int lower_t(esi_handle *h, unsigned long long a, long long *t)
+{
+    const unsigned long long g = a / kSparse * kSparse, g2 = g + kSparse;
+    if (g == a && sparse_ok(h, g)) {
+        *t = sparse_t(h, g);
+        return ESI_OK;
+    }
+    if (sparse_ok(h, g) && sparse_ok(h, g2) && sparse_t(h, g2) - sparse_t(h, g) < (1ll << 31)) {
+        *t = sparse_t(h, g);
+        return ESI_OK;
+    }
+    return exact_t(h, a, t);
+}
+
+// First absolute index in [lo, hi) (pending indices) whose time is > v
+// (times non-decreasing): a search over the sparse times, then one block of
+// at most kSparse - 1 exact times.
+static int upper_bound_t(esi_handle *h, unsigned long long lo, unsigned long long hi, long long v,
+                         unsigned long long *res)
+{
+    unsigned long long blo = lo, bhi = hi;
+    const unsigned long long G0 = (lo + kSparse - 1) / kSparse * kSparse;
+    if (G0 < hi) {
+        const unsigned long long nG = (hi - 1 - G0) / kSparse + 1;
+        unsigned long long L = 0, R = nG;
+        while (L < R) {
+            const unsigned long long mid = L + (R - L) / 2;
+            if (sparse_t(h, G0 + mid * kSparse) <= v) L = mid + 1; else R = mid;
+        }
+        // every index before G0 + L kSparse - ... : the answer lies in
+        // (G0 + (L - 1) kSparse, G0 + L kSparse]
+        blo = L == 0 ? lo : G0 + (L - 1) * kSparse + 1;
+        bhi = L < nG ? G0 + L * kSparse : hi;
+    }
+    long long t[kSparse];
+    int rc = block_times(h, blo, bhi, t);
+    if (rc) return rc;
+    unsigned long long a = blo;
+    while (a < bhi && t[a - blo] <= v) ++a;
+    *res = a;
+    return ESI_OK;
 }
 
 int esi::read_status(esi_handle *h)
@@ -359,10 +433,14 @@ int esi_create(int width, int height, const esi_params *params, void *cuda_strea
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->bin_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->in_stream, cudaStreamNonBlocking);
+    for (int r = 0; r < esi_handle::kSpans && e == cudaSuccess; ++r)
+        e = cudaEventCreateWithFlags(&h->span[r].ev, cudaEventDisableTiming);
     for (int c = 0; c < 4 && e == cudaSuccess; ++c)
         e = cudaEventCreateWithFlags(&h->ev_chunk[c], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&h->dbad, sizeof(int));
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hbad, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->dres, sizeof(PushResult));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hres, sizeof(PushResult));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hfetch, 2 * kSparse * sizeof(esi_event));
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
         e = cudaEventCreateWithFlags(&h->ev_bin[b], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_tile[b], cudaEventDisableTiming);
@@ -414,12 +492,20 @@ void esi_destroy(esi_handle *h)
         cudaStreamSynchronize(h->aux_stream);
         cudaStreamDestroy(h->aux_stream);
     }
+    if (h->in_stream) {
+        cudaStreamSynchronize(h->in_stream);
+        cudaStreamDestroy(h->in_stream);
+    }
+    for (int r = 0; r < esi_handle::kSpans; ++r)
+        if (h->span[r].ev) cudaEventDestroy(h->span[r].ev);
     for (int c = 0; c < 4; ++c)
         if (h->ev_chunk[c]) cudaEventDestroy(h->ev_chunk[c]);
-    cudaFree(h->dtimes);
-    cudaFree(h->dbad);
-    cudaFreeHost(h->hbad);
+    cudaFree(h->dsparse);
+    cudaFree(h->dres);
+    cudaFreeHost(h->hres);
+    cudaFreeHost(h->hfetch);
     cudaFreeHost(h->tmirror);
+    cudaFreeHost(h->tsparse);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -440,13 +526,41 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
     const unsigned long long mask = h->cap - 1;
     const long long prev = std::max(h->push_floor, h->last_event_t);
     const cudaMemcpyKind kind = ev_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // device events keep the order of the handle's stream (they may come from
+    // work queued on it); host events go on in_stream once the slots they
+    // overwrite have been binned
+    const cudaStream_t cs = ev_on_device ? h->stream : h->in_stream;
     cudaError_t e = cudaSuccess;
+    if (!ev_on_device && h->tail + n > h->cap) {
+        // the slots written held indices [o0, o1); wait for the newest render
+        // that consumed one of them (renders bin in order, so older ones are
+        // done by then).  Before the oldest tracked render: wait for that one.
+        const unsigned long long o0 = h->tail - h->cap, o1 = h->tail + n - h->cap;
+        int pick = -1;
+        unsigned long long best = 0, oldest_a0 = ~0ull;
+        int oldest = -1;
+        for (int r = 0; r < esi_handle::kSpans; ++r) {
+            const auto &sp = h->span[r];
+            if (!sp.live) continue;
+            if (sp.a0 < oldest_a0) {
+                oldest_a0 = sp.a0;
+                oldest = r;
+            }
+            if (sp.a0 < o1 && o0 < sp.a1 && sp.a1 > best) {
+                best = sp.a1;
+                pick = r;
+            }
+        }
+        if (pick < 0 && oldest >= 0 && o0 < oldest_a0) pick = oldest;
+        if (pick >= 0) e = cudaStreamWaitEvent(cs, h->span[pick].ev, 0);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e);
     // events [i0, i1) of the push into their ring slots (split at the wrap)
     auto copy_in = [&](unsigned long long i0, unsigned long long i1) {
         for (unsigned long long i = i0; e == cudaSuccess && i < i1;) {
             const unsigned long long pos = (h->tail + i) & mask;
             const unsigned long long len = std::min(i1 - i, h->cap - pos);
-            e = cudaMemcpyAsync(h->ring + pos, ev + i, len * sizeof(esi_event), kind, h->stream);
+            e = cudaMemcpyAsync(h->ring + pos, ev + i, len * sizeof(esi_event), kind, cs);
             i += len;
         }
     };
@@ -458,59 +572,54 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
         if (e != cudaSuccess) return cuda_fail(h, e);
         const bool ordered = check_and_mirror(h, ev, n, prev);
         // the caller may reuse its buffer as soon as this returns
-        e = cudaStreamSynchronize(h->stream);
+        e = cudaStreamSynchronize(cs);
         if (e != cudaSuccess) return cuda_fail(h, e);
         if (!ordered) return ESI_ETIMEORDER;
+        // every time of this push is in the mirror (adjacent spans merge)
+        if (!h->exact_spans.empty() && h->exact_spans.back().second == h->tail)
+            h->exact_spans.back().second = h->tail + n;
+        else
+            h->exact_spans.push_back({h->tail, h->tail + n});
+        h->last_event_t = ev[n - 1].t_us;
     } else {
-        // chunk by chunk: copy in, check on the device and compact the times
-        // (handle stream), then bring the times to the mirror (aux stream)
-        // while the next chunk is copied in
-        rc = ensure_device(h, &h->dtimes, &h->dtimes_cap, n);
+        // chunk by chunk: copy in, check on the device and keep every
+        // kSparse-th time (push stream), then bring those to the sparse
+        // mirror (aux stream) while the next chunk is copied in
+        const unsigned long long g0 = (h->tail + kSparse - 1) / kSparse * kSparse;
+        rc = ensure_device(h, &h->dsparse, &h->dsparse_cap, (size_t)(n / kSparse + 2));
         if (rc) return rc;
-        // a page-locked host buffer is read by the kernel itself over the
-        // host link (no copy-engine pass)
-        const esi_event *pull = nullptr;
-        if (!ev_on_device) {
-            cudaPointerAttributes at{};
-            if (cudaPointerGetAttributes(&at, ev) == cudaSuccess && at.type == cudaMemoryTypeHost &&
-                at.devicePointer && ((uintptr_t)at.devicePointer & 15u) == 0)
-                pull = static_cast<const esi_event *>(at.devicePointer);
-            else
-                cudaGetLastError();
-        }
-        e = cudaMemsetAsync(h->dbad, 0, sizeof(int), h->stream);
+        const unsigned long long smask = h->cap / kSparse - 1;
+        e = cudaMemsetAsync(h->dres, 0, sizeof(PushResult), cs);
         int j = 0;
         for (unsigned long long c0 = 0; e == cudaSuccess && c0 < n; c0 += kPushChunk, ++j) {
             const unsigned long long c1 = std::min<unsigned long long>(n, c0 + kPushChunk);
-            if (pull) {
-                e = launch_push_pull(pull, h->ring, mask, h->tail, c0, (long long)(c1 - c0), prev,
-                                     h->dtimes, h->dbad, h->stream);
-            } else {
-                copy_in(c0, c1);
-                if (e == cudaSuccess)
-                    e = launch_push_check(h->ring, mask, h->tail, c0, (long long)(c1 - c0), prev,
-                                          h->dtimes, h->dbad, h->stream);
-            }
-            if (e == cudaSuccess) e = cudaEventRecord(h->ev_chunk[j & 3], h->stream);
+            copy_in(c0, c1);
+            if (e == cudaSuccess)
+                e = launch_push_check(h->ring, mask, h->tail, c0, (long long)(c1 - c0), n, prev, g0,
+                                      h->dsparse, h->dres, cs);
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev_chunk[j & 3], cs);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux_stream, h->ev_chunk[j & 3], 0);
-            for (unsigned long long i = c0; e == cudaSuccess && i < c1;) {
-                const unsigned long long pos = (h->tail + i) & mask;
-                const unsigned long long len = std::min(c1 - i, h->cap - pos);
-                e = cudaMemcpyAsync(h->tmirror + pos, h->dtimes + i, len * sizeof(long long),
+            // sparse entries j of this chunk: indices g0 + j kSparse in [tail + c0, tail + c1)
+            const unsigned long long ja = (std::max(g0, (h->tail + c0 + kSparse - 1) / kSparse * kSparse) - g0) / kSparse;
+            const unsigned long long jb = (std::max(g0, (h->tail + c1 + kSparse - 1) / kSparse * kSparse) - g0) / kSparse;
+            for (unsigned long long j = ja; e == cudaSuccess && j < jb;) {
+                const unsigned long long pos = (g0 / kSparse + j) & smask;
+                const unsigned long long len = std::min(jb - j, smask + 1 - pos);
+                e = cudaMemcpyAsync(h->tsparse + pos, h->dsparse + j, len * sizeof(long long),
                                     cudaMemcpyDeviceToHost, h->aux_stream);
-                i += len;
+                j += len;
             }
         }
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(h->hbad, h->dbad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+            e = cudaMemcpyAsync(h->hres, h->dres, sizeof(PushResult), cudaMemcpyDeviceToHost, cs);
         // the caller may reuse its buffer as soon as this returns
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->aux_stream);
         if (e != cudaSuccess) return cuda_fail(h, e);
-        if (*h->hbad) return ESI_ETIMEORDER;  // ring slots past tail are ignored
+        if (h->hres->bad) return ESI_ETIMEORDER;  // ring slots past tail are ignored
+        h->last_event_t = h->hres->last;
     }
     h->tail += n;
-    h->last_event_t = h->tmirror[(h->tail - 1) & mask];
     h->pushed += n;
     return ESI_OK;
 }
@@ -518,7 +627,7 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
 int esi_render_frames(esi_handle *h, const int64_t *t_frames, size_t m, uint8_t *out,
                       int out_on_device)
 {
-    if (!h || !t_frames || m == 0 || !out || (out_on_device != 0 && out_on_device != 1))
+    if (!h || !t_frames || m == 0 || !out || out_on_device < 0 || out_on_device > 2)
         return ESI_EINVAL;
     if (m > (size_t)INT_MAX) return ESI_EINVAL;
     if ((long long)t_frames[0] < h->frame_floor) return ESI_ETIMEORDER;
@@ -562,7 +671,12 @@ int esi_set_state(esi_handle *h, const float *S, const int64_t *T, int on_device
     }
     long long tmax = LLONG_MIN;
     for (long long i = 0; i < h->P; ++i) tmax = std::max(tmax, (long long)Th[i]);
-    if (h->tail > h->head && mirror_t(h, h->head) < tmax) return ESI_ETIMEORDER;
+    if (h->tail > h->head) {
+        long long t0 = 0;
+        int rc2 = exact_t(h, h->head, &t0);
+        if (rc2) return rc2;
+        if (t0 < tmax) return ESI_ETIMEORDER;
+    }
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     cudaError_t e = cudaMemcpyAsync(h->S, S, (size_t)h->P * sizeof(float), k, h->stream);
     if (e == cudaSuccess)
@@ -696,7 +810,10 @@ struct SubBatch {
 int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int out_on_device)
 {
     const long long t_last = tf[m - 1];
-    const unsigned long long n_split = upper_bound_t(h, h->head, h->tail, t_last) - h->head;
+    unsigned long long n_end = 0;
+    int rc = upper_bound_t(h, h->head, h->tail, t_last, &n_end);
+    if (rc) return rc;
+    const unsigned long long n_split = n_end - h->head;
     const esi_tuning &tu = h->tun;
     const int chunk = tu.chunk_events;
     const unsigned long long maxb = (unsigned long long)tu.max_batch_events;
@@ -710,20 +827,41 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
         for (;;) {
             SubBatch sb;
             sb.i0 = i;
+            // a split at an index the sparse mirror holds keeps its time exact
+            // without reading it back
+            auto aligned = [&](unsigned long long j) {
+                const unsigned long long g = (h->head + j) / kSparse * kSparse;
+                return g > h->head + i ? g - h->head : j;
+            };
             sb.i1 = std::min(n_split, i + maxb);
+            if (sb.i1 < n_split) sb.i1 = aligned(sb.i1);
             sb.t_base = 0;
             if (sb.i1 > i) {
-                sb.t_base = mirror_t(h, h->head + i);
+                // a base no later than the first event (record times are
+                // 32-bit offsets from it)
+                rc = lower_t(h, h->head + i, &sb.t_base);
+                if (rc) return rc;
                 const long long lim = sb.t_base + 0xffffffffll;
-                const unsigned long long cut = upper_bound_t(h, h->head + i, h->head + sb.i1, lim) - h->head;
-                sb.i1 = std::max(cut, i + 1);
+                unsigned long long cut = 0;
+                rc = upper_bound_t(h, h->head + i, h->head + sb.i1, lim, &cut);
+                if (rc) return rc;
+                if (cut - h->head < sb.i1) sb.i1 = std::max(aligned(cut - h->head), i + 1);
             } else if (w < m) {
                 sb.t_base = tf[w];
             }
             sb.w0 = w;
             sb.w1 = m;
             if (sb.i1 < n_split) {
-                const long long tn = mirror_t(h, h->head + sb.i1);
+                // frames before the next sub-batch's first time complete
+                // here (exact: the launch emits them among its records)
+                const unsigned long long a1 = h->head + sb.i1;
+                long long tn = 0;
+                if (a1 % kSparse == 0 && sparse_ok(h, a1)) {
+                    tn = sparse_t(h, a1);
+                } else {
+                    rc = exact_t(h, a1, &tn);
+                    if (rc) return rc;
+                }
                 sb.w1 = (int)(std::lower_bound(tf + w, tf + m, (int64_t)tn) - tf);
             }
             plan.push_back(sb);
@@ -738,7 +876,7 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
         if (e0 != cudaSuccess) return cuda_fail(h, e0);
         h->hwin_busy = false;
     }
-    int rc = ensure_pinned(h, &h->hwin, &h->hwin_cap, (size_t)m);
+    rc = ensure_pinned(h, &h->hwin, &h->hwin_cap, (size_t)m);
     if (!rc) rc = ensure_device(h, &h->dwin, &h->dwin_cap, (size_t)m);
     if (rc) return rc;
     for (const SubBatch &sb : plan)
@@ -757,7 +895,8 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
     // kernels directly; other host buffers through a device staging copy
     uint8_t *frames = out;
     bool staged_out = false;
-    if (!out_on_device) {
+    const bool host_out = out_on_device != 1;   // 0: host, waits; 2: host, returns at once
+    if (host_out) {
         cudaPointerAttributes at{};
         if (cudaPointerGetAttributes(&at, out) == cudaSuccess && at.type == cudaMemoryTypeHost &&
             at.devicePointer) {
@@ -816,6 +955,7 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
             if (!rc) rc = cuda_fail(h, launch_bin(ba, n_chunks, h->bin_stream));
             if (!rc) rc = prof_end(h, kKindBin, ev, h->bin_stream);
             if (!rc) rc = cuda_fail(h, cudaEventRecord(h->ev_bin[buf], h->bin_stream));
+
             if (!rc) rc = cuda_fail(h, cudaStreamWaitEvent(h->stream, h->ev_bin[buf], 0));
             if (rc) return rc;
         }
@@ -849,18 +989,30 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
         if (rc) return rc;
         h->tile_pending[buf] = true;
     }
+    if (n_split > 0) {
+        // the binning launches of this render read ring indices [head, head + n_split)
+        auto &sp = h->span[h->span_next];
+        e = cudaEventRecord(sp.ev, h->bin_stream);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+        sp.a0 = h->head;
+        sp.a1 = h->head + n_split;
+        sp.live = true;
+        h->span_next = (h->span_next + 1) % esi_handle::kSpans;
+    }
     h->head += n_split;
     h->consumed += n_split;
+    while (!h->exact_spans.empty() && h->exact_spans.front().second <= h->head)
+        h->exact_spans.erase(h->exact_spans.begin());
     h->frames += (unsigned long long)m;
     h->last_frame_t = t_last;
     h->frame_floor = std::max(h->frame_floor, (long long)t_last);
     h->push_floor = std::max(h->push_floor, (long long)t_last);
-    if (!out_on_device) {
+    if (host_out) {
         if (staged_out) {
             e = cudaMemcpyAsync(out, frames, (size_t)m * (size_t)h->P, cudaMemcpyDeviceToHost, h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e);
         }
-        return read_status(h);
+        if (out_on_device == 0) return read_status(h);
     }
     return ESI_OK;
 }

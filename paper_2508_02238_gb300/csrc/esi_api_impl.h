@@ -37,20 +37,41 @@ struct esi_handle {
     float *S = nullptr;           // accumulation matrix (Alg. 2), row-major
     long long *T = nullptr;       // last decay time matrix (Alg. 2)
 
-    // pending events: ring of `cap` events (power of two) on the device and a
-    // pinned host mirror of their times; absolute indices head <= i < tail
+    // pending events: ring of `cap` events (power of two) on the device;
+    // absolute indices head <= i < tail.  Times for planning, pinned:
+    // tsparse holds the time of every kSparse-th absolute index (slot
+    // (i / kSparse) & (cap / kSparse - 1)), valid for i >= sparse_from until
+    // the slot is reused; tmirror holds every time of host-checked pushes,
+    // whose index ranges exact_spans lists.  Other times are read back from
+    // the ring when planning needs them.
     esi_event *ring = nullptr;
     unsigned long long cap = 0, head = 0, tail = 0;
     long long *tmirror = nullptr;
+    long long *tsparse = nullptr;
+    unsigned long long sparse_from = 0;
+    std::vector<std::pair<unsigned long long, unsigned long long>> exact_spans;
+    esi_event *hfetch = nullptr;         // pinned: events read back for planning
 
+    // host pushes run on in_stream, which waits only for renders whose
+    // binning still reads ring slots the push overwrites: the last renders'
+    // consumed index ranges, each with an event after its last binning launch
+    cudaStream_t in_stream = nullptr;
+    struct RenderSpan {
+        unsigned long long a0 = 0, a1 = 0;   // absolute ring indices consumed
+        cudaEvent_t ev = nullptr;             // after the render's last binning launch
+        bool live = false;
+    };
+    static constexpr int kSpans = 4;
+    RenderSpan span[kSpans];
+    int span_next = 0;                        // oldest entry, reused next
     // large pushes: the device checks the time order and returns the times
     // chunk by chunk on aux_stream while the next chunk is copied in
     cudaStream_t aux_stream = nullptr;
     cudaEvent_t ev_chunk[4] = {nullptr, nullptr, nullptr, nullptr};
-    long long *dtimes = nullptr;         // times of the push being checked
-    size_t dtimes_cap = 0;
-    int *dbad = nullptr;                 // set when a push is out of order
-    int *hbad = nullptr;                 // pinned
+    long long *dsparse = nullptr;        // every kSparse-th time of the push being checked
+    size_t dsparse_cap = 0;
+    esi::PushResult *dres = nullptr;
+    esi::PushResult *hres = nullptr;     // pinned
 
     // binning of sub-batch i + 1 overlaps the tile kernel of sub-batch i:
     // it runs on bin_stream into the other half of the double-buffered
@@ -107,17 +128,15 @@ int init_state(esi_handle *h);
 int render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int out_on_device);
 int fill_i64(esi_handle *h, long long *dst, long long n, long long value);
 cudaError_t launch_fill_i64(long long *dst, long long n, long long value, cudaStream_t s);
-// Checks events a0 + first .. a0 + first + cnt of a push starting at ring
-// index a0: each time >= its predecessor's (prev for the push's first); sets
-// *bad otherwise; copies the times to times[first ..].
-// The same for events in a page-locked host buffer (src: its device view),
-// which the kernel also stores into their ring slots.
-cudaError_t launch_push_pull(const esi_event *src, esi_event *ring, unsigned long long mask,
-                             unsigned long long a0, unsigned long long first, long long cnt,
-                             long long prev, long long *times, int *bad, cudaStream_t s);
+// Checks events a0 + first .. a0 + first + cnt of an n-event push starting at
+// ring index a0: each time >= its predecessor's (prev for the push's first),
+// res->bad set otherwise; the time of absolute index g (g % kSparse == 0)
+// goes to sparse[(g - g0) / kSparse] (g0: the push's first such index); the
+// push's last time to res->last.
 cudaError_t launch_push_check(const esi_event *ring, unsigned long long mask, unsigned long long a0,
-                              unsigned long long first, long long cnt, long long prev,
-                              long long *times, int *bad, cudaStream_t s);
+                              unsigned long long first, long long cnt, unsigned long long n,
+                              long long prev, unsigned long long g0, long long *sparse,
+                              PushResult *res, cudaStream_t s);
 
 // Launch-shape measurement shared by esi_autotune and esi_stream_autotune:
 // cache lookup, candidate timing on a scratch handle, cache update.

@@ -42,6 +42,18 @@ struct DevStatus {
     int err_where;                // which kernel / wait gave up
 };
 
+// Result of a device-checked push: an order violation anywhere, and the time
+// of the push's last event.
+struct PushResult {
+    int bad;
+    int pad;
+    long long last;
+};
+
+// Host pushes keep the time of every kSparse-th absolute ring index for
+// planning (device-checked ones keep only those).
+constexpr unsigned kSparse = 32;
+
 // Arguments of the binning kernel (one block per chunk of events).
 struct BinArgs {
     const esi_event *ring;        // pending-event ring

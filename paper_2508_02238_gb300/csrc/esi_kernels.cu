@@ -288,60 +288,30 @@ __global__ void esi_fill_i64_kernel(long long *dst, long long n, long long value
 
 __global__ void esi_push_check_kernel(const esi_event *ring, unsigned long long mask,
                                       unsigned long long a0, unsigned long long first, long long cnt,
-                                      long long prev, long long *times, int *bad)
+                                      unsigned long long n, long long prev, unsigned long long g0,
+                                      long long *sparse, PushResult *res)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt;
          i += (long long)gridDim.x * blockDim.x) {
         const unsigned long long k = first + (unsigned long long)i;
-        const long long t = ring[(a0 + k) & mask].t_us;
-        const long long tp = k ? ring[(a0 + k - 1) & mask].t_us : prev;
-        if (t < tp) *bad = 1;
-        times[k] = t;
+        const unsigned long long g = a0 + k;
+        const long long t = ring[g & mask].t_us;
+        const long long tp = k ? ring[(g - 1) & mask].t_us : prev;
+        if (t < tp) res->bad = 1;
+        if (g % kSparse == 0) sparse[(g - g0) / kSparse] = t;
+        if (k == n - 1) res->last = t;
     }
-}
-
-// Zero-copy variant: events are read from the caller's page-locked host
-// buffer (src, a device view of it) and stored into their ring slots here,
-// one event per thread; the predecessor's time comes from the next lower lane.
-__global__ void esi_push_pull_kernel(const esi_event *src, esi_event *ring, unsigned long long mask,
-                                     unsigned long long a0, unsigned long long first, long long cnt,
-                                     long long prev, long long *times, int *bad)
-{
-    const int lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < cnt; i0 += stride) {
-        const long long i = i0 + lane;
-        const unsigned long long k = first + (unsigned long long)i;
-        esi_event e{};
-        if (i < cnt) {
-            const longlong2 v = *reinterpret_cast<const longlong2 *>(src + k);
-            e = *reinterpret_cast<const esi_event *>(&v);
-            *reinterpret_cast<longlong2 *>(ring + ((a0 + k) & mask)) = v;
-            times[k] = e.t_us;
-        }
-        long long tp = __shfl_up_sync(0xffffffffu, e.t_us, 1);
-        if (lane == 0) tp = k ? src[k - 1].t_us : prev;
-        if (i < cnt && e.t_us < tp) *bad = 1;
-    }
-}
-
-cudaError_t launch_push_pull(const esi_event *src, esi_event *ring, unsigned long long mask,
-                             unsigned long long a0, unsigned long long first, long long cnt,
-                             long long prev, long long *times, int *bad, cudaStream_t s)
-{
-    if (cnt <= 0) return cudaSuccess;
-    const long long blocks = std::min<long long>((cnt + 255) / 256, 152LL * 16);
-    esi_push_pull_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, ring, mask, a0, first, cnt, prev, times, bad);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_push_check(const esi_event *ring, unsigned long long mask, unsigned long long a0,
-                              unsigned long long first, long long cnt, long long prev,
-                              long long *times, int *bad, cudaStream_t s)
+                              unsigned long long first, long long cnt, unsigned long long n,
+                              long long prev, unsigned long long g0, long long *sparse,
+                              PushResult *res, cudaStream_t s)
 {
     if (cnt <= 0) return cudaSuccess;
     const long long blocks = std::min<long long>((cnt + 255) / 256, 152LL * 8);
-    esi_push_check_kernel<<<(unsigned)blocks, 256, 0, s>>>(ring, mask, a0, first, cnt, prev, times, bad);
+    esi_push_check_kernel<<<(unsigned)blocks, 256, 0, s>>>(ring, mask, a0, first, cnt, n, prev, g0,
+                                                           sparse, res);
     return cudaGetLastError();
 }
 

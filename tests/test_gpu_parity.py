@@ -420,7 +420,7 @@ def test_large_pushes_are_checked_on_the_device():
         import torch
 
         def pinned(a):
-            # page-locked host copy: read by the kernel itself over the host link
+            # page-locked host copy
             t = torch.empty(a.nbytes, dtype=torch.uint8, pin_memory=True)
             t.numpy()[:] = a.view(np.uint8)
             return t
@@ -447,3 +447,38 @@ def test_large_pushes_are_checked_on_the_device():
         S, T = g.state()
     ref = run_oracle(ev, W, H, p, tf)
     compare({"S": S, "T": T, "frames": fr}, ref, p["C"], "large pushes")
+
+
+def test_async_host_output_with_overlapping_pushes():
+    # out_on_device = 2 returns once the render is queued; the next host push
+    # runs on its own stream and may only overwrite ring slots the previous
+    # render has binned.  Each push here fills the whole initial ring (2^20
+    # events) and each render consumes all of it, so every push overwrites
+    # exactly the slots the previous render reads.
+    import torch
+    rng = np.random.default_rng(15)
+    W, H = 160, 120
+    n = 1 << 20
+    K = 4
+    ev = random_events(rng, W, H, n * K, 0, 40_000_000, hot=(7, 9, 0.02))
+    p = P(render_decay=1)
+    per = 10
+    tfs = [np.linspace(ev["t"][k * n] + 1, ev["t"][(k + 1) * n - 1], per).astype(np.int64)
+           for k in range(K)]
+    for k in range(K - 1):   # a frame at the push's last event time takes all of it
+        assert ev["t"][(k + 1) * n] > tfs[k][-1]
+    with GpuStream(W, H, p) as g:
+        outs = []
+        for k in range(K):
+            assert g.push(ev[k * n:(k + 1) * n]) == 0
+            if k % 2 == 0:
+                o = torch.empty((per, H, W), dtype=torch.uint8, pin_memory=True)
+            else:
+                o = np.empty((per, H, W), dtype=np.uint8)     # staged through the device
+            assert g.esi.esi_render_frames(g.h, tfs[k], per, o, 2) == 0
+            outs.append(o)
+        assert g.esi.esi_synchronize(g.h) == 0
+        frames = np.concatenate([o.numpy() if hasattr(o, "numpy") else o for o in outs])
+        S, T = g.state()
+    ref = run_oracle(ev, W, H, p, np.concatenate(tfs))
+    compare({"S": S, "T": T, "frames": frames}, ref, p["C"], "async host output")

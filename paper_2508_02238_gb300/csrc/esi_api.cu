@@ -619,6 +619,7 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
         if (h->hres->bad) return ESI_ETIMEORDER;  // ring slots past tail are ignored
         h->last_event_t = h->hres->last;
     }
+    if (ev_on_device) h->dev_push_pending = true;
     h->tail += n;
     h->pushed += n;
     return ESI_OK;
@@ -909,24 +910,31 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
             staged_out = true;
         }
     }
-    for (int b = 0; b < 2 && b < (int)plan.size(); ++b) {
+    // both scratch halves fit the current shape: the halves alternate across
+    // renders, so a one-sub-batch render may use either
+    for (int b = 0; b < 2; ++b) {
         const size_t max_chunks = (size_t)((maxb + chunk - 1) / chunk);
         rc = ensure_device(h, &h->rec[b], &h->rec_cap[b], max_chunks * (size_t)chunk);
         if (!rc) rc = ensure_device(h, &h->hrow[b], &h->hrow_cap[b], max_chunks * (size_t)h->n_tiles);
         if (rc) return rc;
     }
-    // binning may start once everything queued before this render (pushes) is done
-    e = cudaEventRecord(h->ev_start, h->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->bin_stream, h->ev_start, 0);
-    if (e != cudaSuccess) return cuda_fail(h, e);
-    int sbi = 0;
+    // binning reads only the ring and its own scratch half: it may start
+    // during the previous render's last tile kernel (the halves alternate
+    // across renders), after device pushes queued on the handle's stream
+    if (h->dev_push_pending) {
+        e = cudaEventRecord(h->ev_start, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->bin_stream, h->ev_start, 0);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+        h->dev_push_pending = false;
+    }
     // a lane's pixels go out as one frame word when rows and the buffer allow
     const unsigned wb = h->tun.tile_w == 64 ? 2u : 4u;
     const bool vec = (h->W % (int)wb == 0) && (((uintptr_t)frames & (wb - 1u)) == 0);
     for (const SubBatch &sb : plan) {
         const int nb = (int)(sb.i1 - sb.i0);
         const int n_chunks = (nb + chunk - 1) / chunk;
-        const int buf = sbi++ & 1;
+        const int buf = h->next_buf;
+        h->next_buf ^= 1;
         if (nb > 0) {
             // the buffer's previous tile kernel must be done reading it
             if (h->tile_pending[buf]) {

@@ -81,6 +81,8 @@ struct esi_handle {
     cudaEvent_t ev_bin[2] = {nullptr, nullptr};
     cudaEvent_t ev_tile[2] = {nullptr, nullptr};
     bool tile_pending[2] = {false, false};
+    int next_buf = 0;                    // scratch half of the next sub-batch
+    bool dev_push_pending = false;       // a device push queued since the last render
     unsigned long long *rec[2] = {nullptr, nullptr};   // binned records of a sub-batch
     size_t rec_cap[2] = {0, 0};
     unsigned int *hrow[2] = {nullptr, nullptr};        // [chunk][tile] run table

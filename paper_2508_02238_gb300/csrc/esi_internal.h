@@ -67,7 +67,7 @@ struct BinArgs {
     int tw_log2;                  // log2 of pixels per tile row (5, 6 or 7)
     int tile_bits;                // bits of a tile index (n_tiles <= 2^tile_bits)
     unsigned long long *rec;      // out: records, block c at rec + c * chunk
-    unsigned int *hrow;           // out: [chunk][tile] (start << 16 | count)
+    unsigned int *hrow;           // out: [tile][chunk] (start << 16 | count)
     DevStatus *status;
 };
 

@@ -162,9 +162,10 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
     const unsigned total = block_exclusive_scan<NT>(tstart, n_tiles, scan_tmp);
     if (tid == 0) tstart[n_tiles] = total;
     __syncthreads();
-    unsigned *hrow = a.hrow + (size_t)cidx * n_tiles;
+    // tile-major run table: a tile reads its runs of every chunk contiguously
+    const size_t n_chunks_all = ((size_t)a.n + a.chunk - 1) / a.chunk;
     for (int j = tid; j < n_tiles; j += NT)
-        hrow[j] = (tstart[j] << 16) | (tstart[j + 1] - tstart[j]);
+        a.hrow[(size_t)j * n_chunks_all + cidx] = (tstart[j] << 16) | (tstart[j + 1] - tstart[j]);
 
     // phase 3: scatter every event to its stable place in tile order
     const int th_mask = (1 << thl) - 1;

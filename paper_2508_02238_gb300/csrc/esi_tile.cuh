@@ -91,7 +91,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
 
     // this tile's run in every chunk, in chunk (= arrival) order
     for (int c = tid; c < n_chunks; c += NT) {
-        const unsigned h = a.hrow[(size_t)c * a.n_tiles + tile];
+        const unsigned h = a.hrow[(size_t)tile * n_chunks + c];
         runpre[c] = h & 0xffffu;
         runoff[c] = h >> 16;
     }

@@ -324,6 +324,7 @@ def bench_esi(args):
         line["latency"] = latency_leg(esi, torch, sc, ev)
         line["serving"] = serving_leg(esi)
         line["serving_mixed"] = mixed_serving_leg(esi)
+        line["other_configs"] = other_configs_leg(esi, torch)
     elif not args.no_extras:
         line["e2e"] = None
     esi.esi_destroy(h)
@@ -483,6 +484,64 @@ def serving_leg(esi):
                     "frame_latency_p99_ms": st.frame_latency_p99_ms,
                     "packet_to_frame_p50_ms": st.packet_latency_p50_ms,
                     "packet_to_frame_p99_ms": st.packet_latency_p99_ms}
+    return out
+
+
+def other_configs_leg(esi, torch):
+    """Device-resident throughput of the other single-stream workloads, measured
+    as the main step: K replays of the stream shifted in time, pushed before
+    timing, rendered to device memory, CUDA events on the handle's stream."""
+    import synth
+    peak, _ = load_peaks()
+    out = {}
+    cases = [("config0: 346x260, 1 s, ~1 M events, 100 x 10 ms frames", 0, 10_000, 12),
+             ("config2: 1280x720, 1 s, ~50 M events, 100 x 10 ms frames", 2, 10_000, 3),
+             ("config2: 1280x720, 1 s, ~50 M events, 1000 x 1 ms frames", 2, 1_000, 3)]
+    streams = {}
+    for label, cfg, win, K in cases:
+        if cfg not in streams:
+            sc = synth.CONFIGS[cfg]()
+            streams[cfg] = (sc, synth.generate(sc))
+        sc, ev = streams[cfg]
+        n_ev = len(ev)
+        span = int(round(sc.duration_s * 1e6))
+        n_w = span // win
+        prm = dict(PARAMS, C=0.2)
+        P = sc.W * sc.H
+        step_bytes = 16 * n_ev + 24 * P + n_w * P
+        fr = torch.empty((n_w, sc.H, sc.W), dtype=torch.uint8, device="cuda")
+        tfs = [np.arange(1, n_w + 1, dtype=np.int64) * win + k * span for k in range(1 + K)]
+        res = {"events_per_step": n_ev, "frames_per_step": n_w, "steps": K}
+        for mode in ("default", "autotuned"):
+            st = torch.cuda.Stream()
+            rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**prm), st.cuda_stream)
+            esi.check(rc, "esi_create")
+            if mode == "autotuned":
+                # a quarter of the stream as the sample, with its own frame times
+                samp = ev[ev["t"] < span // 4]
+                stf = np.arange(1, span // 4 // win + 1, dtype=np.int64) * win
+                rc, t = esi.esi_autotune(h, samp, len(samp), stf, len(stf), 0)
+                esi.check(rc, "autotune")
+                res["autotuned_shape"] = {f: getattr(t, f) for f in (
+                    "tile_w", "tile_h", "chunk_events", "batch_records", "max_batch_events")}
+            for k in range(1 + K):
+                e = ev.copy()
+                e["t"] += k * span
+                esi.check(esi.esi_push_events(h, e, n_ev, 0), "push")
+            esi.check(esi.esi_render_frames(h, tfs[0], n_w, fr, 1), "render")
+            esi.check(esi.esi_synchronize(h), "sync")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for k in range(1, 1 + K):
+                esi.check(esi.esi_render_frames(h, tfs[k], n_w, fr, 1), "render")
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / K
+            esi.esi_destroy(h)
+            res[mode] = {"ms_per_step": ms, "events_per_s": n_ev / (ms / 1e3),
+                         "frames_per_s": n_w / (ms / 1e3),
+                         "step_hbm_frac": step_bytes / (ms / 1e3) / 1e9 / peak}
+        out[label] = res
     return out
 
 

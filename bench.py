@@ -42,9 +42,9 @@ PARAMS = dict(C=0.15, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, t_origin_us=0,
 WORKLOAD = "config1: 640x480, 2 s, ~10M events (40 Gaussian blobs), 200 x 10 ms frames, decay view"
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of the same launch shape (2 M events, 40 frames per launch);
+# ncu capture of the same launch shape (4 M events, 80 frames per launch);
 # profiles/esi_tile_kernel_config1_small.md, profiles/esi_bin_kernel_config1_small.md.
-NCU_TRAFFIC_PER_LAUNCH = {"esi_tile": 21133568, "esi_bin": 32484352}
+NCU_TRAFFIC_PER_LAUNCH = {"esi_tile": 38493440, "esi_bin": 68670976}
 
 
 def parse_args():
@@ -645,23 +645,23 @@ def mixed_serving_leg(esi, seconds=MIXED_SECONDS, seed=1004):
 
 
 def ncu_case():
-    """A small case of the same workload for kernel captures: 0.4 s of the
-    config-1 stream (about 2 M events, 32 MB, larger than L2 per render of
-    three), 40 frames per render, three renders."""
+    """A small case of the same launch shape for kernel captures: 0.8 s of the
+    config-1 stream (about 4 M events, 64 MB, one sub-batch per render as in
+    the bench), 80 frames per render, three renders."""
     import torch  # noqa: F401  (CUDA context as in the bench)
     import synth
     from paper_2508_02238_gb300 import esi
-    sc = synth.config1(duration_s=0.4)
+    sc = synth.config1(duration_s=0.8)
     ev = synth.generate(sc)
-    span = 400_000
+    span = 800_000
     rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**PARAMS), 0)
     esi.check(rc, "create")
-    out = torch.empty((40, sc.H, sc.W), dtype=torch.uint8, device="cuda")
+    out = torch.empty((80, sc.H, sc.W), dtype=torch.uint8, device="cuda")
     for k in range(3):
         esi.check(esi.esi_push_events(h, _shift(ev, k * span), len(ev), 0))
     for k in range(3):
-        tf = np.arange(1, 41, dtype=np.int64) * WINDOW_US + k * span
-        esi.check(esi.esi_render_frames(h, tf, 40, out, 1), "render")
+        tf = np.arange(1, 81, dtype=np.int64) * WINDOW_US + k * span
+        esi.check(esi.esi_render_frames(h, tf, 80, out, 1), "render")
     esi.check(esi.esi_synchronize(h))
     esi.esi_destroy(h)
     print(f"ncu case done: {len(ev)} events x 3 renders")

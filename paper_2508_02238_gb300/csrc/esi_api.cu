@@ -96,7 +96,7 @@ esi_tuning default_tuning(int W, int H)
     t.tile_h = 8;
     t.chunk_events = 2048;
     t.batch_records = 4096;
-    t.max_batch_events = 1 << 21;
+    t.max_batch_events = 1 << 22;
     return t;
 }
 

@@ -132,7 +132,7 @@ std::vector<esi_tuning> handle_candidates(int flags)
         if ((flags & ESI_AUTOTUNE_WIDE_ONLY) && sh[0] != 128) continue;
         for (int chunk : {2048, 4096})
             for (int batch : {2048, 4096})
-                for (int mb : {1 << 21, 1 << 23}) {
+                for (int mb : {1 << 21, 1 << 22, 1 << 23}) {
                     esi_tuning t;
                     t.tile_w = sh[0];
                     t.tile_h = sh[1];

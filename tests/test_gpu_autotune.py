@@ -25,7 +25,7 @@ def _valid(t):
     return ((t.tile_w, t.tile_h) in {(128, 4), (128, 8), (128, 16), (64, 8), (64, 16), (32, 16),
                                      (32, 32)}
             and t.chunk_events in (2048, 4096) and t.batch_records in (2048, 4096)
-            and t.max_batch_events in (1 << 21, 1 << 23))
+            and t.max_batch_events in (1 << 21, 1 << 22, 1 << 23))
 
 
 def test_autotune_keeps_state_and_matches_oracle():

@@ -13,14 +13,17 @@
  *   - Return 0 (ESI_OK) or a negative ESI_E* code; esi_strerror() names it.
  *   - Pointers are plain host or device pointers as the *_on_device flag
  *     says; the caller owns every buffer it passes.  No call keeps a pointer
- *     the caller passed after it returns.
+ *     the caller passed after it returns, with one exception: a render with
+ *     out_on_device = 2 writes its host buffer until the next call that
+ *     waits (esi_synchronize).
  *   - Time is int64 microseconds.  k is given per second.
  *   - A handle (and a server) is not thread-safe: drive it from one thread.
  *   - Device work runs on the CUDA stream given at creation (NULL = a stream
  *     the library creates).  Calls that write host memory wait for their
- *     own work; calls that only write device memory return once the work is
- *     queued, and errors found by the device are reported by the next call
- *     that waits (esi_synchronize, esi_get_state, a host-output render).
+ *     own work (a render with out_on_device = 2 excepted); calls that only
+ *     write device memory return once the work is queued, and errors found
+ *     by the device are reported by the next call that waits
+ *     (esi_synchronize, esi_get_state, a render with out_on_device = 0).
  */
 #ifndef ESI_H
 #define ESI_H
@@ -134,8 +137,12 @@ int esi_create(int width, int height, const esi_params *params,
  * whole batch is rejected with ESI_ETIMEORDER and nothing is queued.
  * Events with x >= W or y >= H are accepted but dropped (counted, never
  * applied).  ev_on_device = 0: host buffer, copied before the call
- * returns.  ev_on_device = 1: device buffer, copied on the handle's stream;
- * the call waits for that copy.  n = 0 is a no-op.
+ * returns; the copy may run while earlier renders are still on the device
+ * (it waits only for renders that read the ring slots it overwrites).
+ * ev_on_device = 1: device buffer, copied on the handle's stream after the
+ * work queued on it; the call waits for that copy.  Pushes of more than
+ * 65,536 events and all device pushes are checked for time order on the
+ * device, smaller host pushes on the host.  n = 0 is a no-op.
  */
 int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_device);
 

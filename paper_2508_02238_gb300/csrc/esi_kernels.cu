@@ -3,17 +3,18 @@
 //   esi_bin_kernel   one block per chunk of consecutive events: bulk-copies
 //                    the chunk into shared memory (TMA), validates x < W,
 //                    y < H, and writes the chunk's events as 8-byte records
-//                    stably sorted by pixel tile, plus the chunk's per-tile
-//                    (start, count) row.  Events of one tile stay in arrival
-//                    (= time) order: ranks come from warp match_any over warp
-//                    slices that are themselves in order.
-//   esi_tile_kernel  one block per 128 x TH pixel tile (one warp per row, four
-//                    pixels per lane): gathers the tile's runs from every
-//                    chunk in chunk order (so arrival order is kept),
-//                    stable-sorts each batch by row and then by lane in shared
-//                    memory, and lets every lane walk its own pixels' events
-//                    through Alg. 2, emitting the Eq. 14 codes of its four
-//                    pixels (one 32-bit store) at every frame time.
+//                    stably sorted by pixel tile, plus the chunk's column of
+//                    the tile-major (start, count) run table.  Events of one
+//                    tile stay in arrival (= time) order: ranks come from
+//                    same-tile peer masks (one ballot per tile-index bit)
+//                    over warp slices that are themselves in order.
+//   esi_tile_kernel  one block per tile, one warp per tile row (esi_tile.cuh):
+//                    gathers the tile's runs from every chunk in chunk order
+//                    (so arrival order is kept), stable-sorts each batch by
+//                    row in shared memory, and walks each row frame by frame:
+//                    the due records 32 at a time through Alg. 2, then the
+//                    Eq. 14 codes of the row's pixels at the frame.
+//   esi_push_check_kernel  time-order check of a large push on the device.
 //
 // Per-pixel independence (each pixel's state depends only on its own
 // time-ordered events, Eq. 5 and Alg. 2) is what makes the reorder legal.

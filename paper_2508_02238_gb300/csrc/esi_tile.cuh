@@ -45,8 +45,8 @@ __device__ __forceinline__ int run_of(const unsigned *pre, int n, unsigned g)
 // 32-pixel rows: narrower rows give more independent row walks).
 // Events are applied event-parallel: a row's records are in time order, so at
 // each frame the due records go 32 at a time, one per lane; lanes holding the
-// same pixel (match_any) apply theirs in arrival order, rank by rank, to the
-// pixel state kept in shared memory.  RD: render_decay; DK: decay kind; VEC
+// same pixel (peer masks from one ballot per x bit) apply theirs in arrival
+// order, rank by rank, to the pixel state kept in shared memory.  RD: render_decay; DK: decay kind; VEC
 // (PPL = 4 or 2): rows start PPL-byte aligned (W % PPL == 0), so a lane's
 // pixels move as one float4 / two longlong2 / one 32-bit frame word (PPL = 4)
 // or one 16-bit frame word (PPL = 2).

@@ -183,28 +183,32 @@ def cpu_baseline(sc, ev, budget_s: float = 10.0):
 def _oracle_band(job):
     """Worker: the oracle over the events of one band of rows (pixels of
     different bands never interact, Eq. 5), timed inside the worker."""
-    band, n_bands = job
+    band, n_bands, path, W, H = job
     import oracle
-    import synth
-    sc = synth.config1()
-    ev = synth.generate(sc, threads=1)   # one generator thread per worker
-    y0, y1 = band * sc.H // n_bands, (band + 1) * sc.H // n_bands
-    sel = ev[(ev["y"] >= y0) & (ev["y"] < y1)].copy()
+    ev = np.load(path, mmap_mode="r")
+    y0, y1 = band * H // n_bands, (band + 1) * H // n_bands
+    sel = np.array(ev[(ev["y"] >= y0) & (ev["y"] < y1)])
     sel["y"] -= y0     # the band as a sensor of its own: only its pixels render
-    st = oracle.OracleState(sc.W, y1 - y0, oracle.OracleParams(**PARAMS))
+    st = oracle.OracleState(W, y1 - y0, oracle.OracleParams(**PARAMS))
     t0 = time.perf_counter()
     _, used = st.replay(sel, frame_times(0, DURATION_US // WINDOW_US))
     return used, time.perf_counter() - t0
 
 
-def cpu_baseline_parallel():
+def cpu_baseline_parallel(sc, ev):
     """The same oracle on every host core: one process per band of rows
     (spawned, so no CUDA state is inherited); throughput = all events / the
     slowest band's compute time."""
     import multiprocessing as mp
     cores = os.cpu_count() or 1
-    with mp.get_context("spawn").Pool(cores) as pool:
-        res = pool.map(_oracle_band, [(b, cores) for b in range(cores)])
+    fd, path = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    try:
+        np.save(path, ev)
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_band, [(b, cores, path, sc.W, sc.H) for b in range(cores)])
+    finally:
+        os.unlink(path)
     used = sum(r[0] for r in res)
     slowest = max(r[1] for r in res)
     return {"value": used / slowest, "unit": "events/s", "cores": cores, "kind": "oracle",
@@ -362,7 +366,7 @@ def bench_esi(args):
     esi.esi_destroy(h)
     if rank == 0 and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline(sc, ev)
-        line["cpu_baseline_all_cores"] = cpu_baseline_parallel()
+        line["cpu_baseline_all_cores"] = cpu_baseline_parallel(sc, ev)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()

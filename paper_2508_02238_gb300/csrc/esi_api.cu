@@ -126,6 +126,7 @@ int esi::sync_all(esi_handle *h)
 {
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e == cudaSuccess && h->bin_stream) e = cudaStreamSynchronize(h->bin_stream);
+    if (e == cudaSuccess && h->tile_stream) e = cudaStreamSynchronize(h->tile_stream);
     return cuda_fail(h, e);
 }
 
@@ -431,6 +432,14 @@ int esi_create(int width, int height, const esi_params *params, void *cuda_strea
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hstatus, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->hwin_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->bin_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        int least = 0, greatest = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithPriority(&h->tile_stream, cudaStreamNonBlocking, greatest);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_tstart, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_tdone, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->in_stream, cudaStreamNonBlocking);
@@ -482,6 +491,12 @@ void esi_destroy(esi_handle *h)
     }
     if (h->ev_start) cudaEventDestroy(h->ev_start);
     if (h->bin_stream) cudaStreamDestroy(h->bin_stream);
+    if (h->tile_stream) {
+        cudaStreamSynchronize(h->tile_stream);
+        cudaStreamDestroy(h->tile_stream);
+    }
+    if (h->ev_tstart) cudaEventDestroy(h->ev_tstart);
+    if (h->ev_tdone) cudaEventDestroy(h->ev_tdone);
     cudaFree(h->dwin);
     cudaFree(h->dframes);
     cudaFree(h->dstatus);
@@ -930,6 +945,11 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
     // a lane's pixels go out as one frame word when rows and the buffer allow
     const unsigned wb = h->tun.tile_w == 64 ? 2u : 4u;
     const bool vec = (h->W % (int)wb == 0) && (((uintptr_t)frames & (wb - 1u)) == 0);
+    // the tile stream starts after everything queued on the handle's stream
+    // (pushes of device events, the frame table, state writes)
+    e = cudaEventRecord(h->ev_tstart, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->tile_stream, h->ev_tstart, 0);
+    if (e != cudaSuccess) return cuda_fail(h, e);
     for (const SubBatch &sb : plan) {
         const int nb = (int)(sb.i1 - sb.i0);
         const int n_chunks = (nb + chunk - 1) / chunk;
@@ -964,7 +984,7 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
             if (!rc) rc = prof_end(h, kKindBin, ev, h->bin_stream);
             if (!rc) rc = cuda_fail(h, cudaEventRecord(h->ev_bin[buf], h->bin_stream));
 
-            if (!rc) rc = cuda_fail(h, cudaStreamWaitEvent(h->stream, h->ev_bin[buf], 0));
+            if (!rc) rc = cuda_fail(h, cudaStreamWaitEvent(h->tile_stream, h->ev_bin[buf], 0));
             if (rc) return rc;
         }
         TileArgs ta;
@@ -990,10 +1010,10 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
         ta.batch = tu.batch_records;
         ta.status = h->dstatus;
         cudaEvent_t ev;
-        rc = prof_begin(h, &ev, h->stream);
-        if (!rc) rc = cuda_fail(h, launch_tile(ta, tu.tile_h, tu.tile_w, vec, h->stream));
-        if (!rc) rc = prof_end(h, kKindTile, ev, h->stream);
-        if (!rc) rc = cuda_fail(h, cudaEventRecord(h->ev_tile[buf], h->stream));
+        rc = prof_begin(h, &ev, h->tile_stream);
+        if (!rc) rc = cuda_fail(h, launch_tile(ta, tu.tile_h, tu.tile_w, vec, h->tile_stream));
+        if (!rc) rc = prof_end(h, kKindTile, ev, h->tile_stream);
+        if (!rc) rc = cuda_fail(h, cudaEventRecord(h->ev_tile[buf], h->tile_stream));
         if (rc) return rc;
         h->tile_pending[buf] = true;
     }
@@ -1015,6 +1035,10 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
     h->last_frame_t = t_last;
     h->frame_floor = std::max(h->frame_floor, (long long)t_last);
     h->push_floor = std::max(h->push_floor, (long long)t_last);
+    // the handle's stream continues after the render's tile kernels
+    e = cudaEventRecord(h->ev_tdone, h->tile_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_tdone, 0);
+    if (e != cudaSuccess) return cuda_fail(h, e);
     if (host_out) {
         if (staged_out) {
             e = cudaMemcpyAsync(out, frames, (size_t)m * (size_t)h->P, cudaMemcpyDeviceToHost, h->stream);

@@ -77,6 +77,11 @@ struct esi_handle {
     // it runs on bin_stream into the other half of the double-buffered
     // scratch; events order it against the handle's stream
     cudaStream_t bin_stream = nullptr;
+    // tile kernels run on a high-priority stream joined to the handle's
+    // stream by events, so their blocks are dispatched before those of a
+    // binning launch queued at the same time
+    cudaStream_t tile_stream = nullptr;
+    cudaEvent_t ev_tstart = nullptr, ev_tdone = nullptr;
     cudaEvent_t ev_start = nullptr;      // render's work may begin (handle stream)
     cudaEvent_t ev_bin[2] = {nullptr, nullptr};
     cudaEvent_t ev_tile[2] = {nullptr, nullptr};

@@ -382,7 +382,8 @@ typedef struct {
  * after its last frame are discarded.  After the last tick the executor ticks
  * again at t_end_us until every due frame is issued, then waits.
  * A slot that no OPEN packet of this call has bound names a server stream id
- * directly (streams opened before the call).  Other errors end the call.
+ * directly (streams opened before the call).  Slots are in [0, 2^20).  Other
+ * errors end the call.
  */
 int esi_server_run(esi_server *srv, const esi_packet *packets, size_t n_packets,
                    int64_t tick_us, int64_t t_end_us, int realtime);

@@ -92,6 +92,7 @@ constexpr int kChunk = 2048;
 constexpr int kBatch = 2048;
 constexpr int kMaxChunksPerStream = 64;
 constexpr int kTickSlots = 64;  // completion stamps kept for ticks in flight
+constexpr int kMaxSlots = 1 << 20;  // caller stream slots of one esi_server_run
 
 struct Stream {
     bool open = false;
@@ -977,8 +978,8 @@ int esi_server_run(esi_server *s, const esi_packet *pk, size_t n, int64_t tick_u
     for (size_t i = 1; i < n; ++i)
         if (pk[i].arrival_us < pk[i - 1].arrival_us) return ESI_EINVAL;
     for (size_t i = 0; i < n; ++i)
-        if (pk[i].stream < 0 || pk[i].kind < ESI_PACKET_EVENTS || pk[i].kind > ESI_PACKET_CLOSE ||
-            (pk[i].kind == ESI_PACKET_OPEN && !pk[i].ev))
+        if (pk[i].stream < 0 || pk[i].stream >= kMaxSlots || pk[i].kind < ESI_PACKET_EVENTS ||
+            pk[i].kind > ESI_PACKET_CLOSE || (pk[i].kind == ESI_PACKET_OPEN && !pk[i].ev))
             return ESI_EINVAL;
     // slot -> server stream id; a slot no OPEN packet has bound names a server id
     constexpr int kUnbound = INT_MIN;

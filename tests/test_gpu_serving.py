@@ -389,5 +389,7 @@ def test_executor_join_leave_and_admission():
         assert esi.esi_server_run(srv, bad, 1, 1000, 0, 0) == esi.ESI_EINVAL
         bad[0].kind, bad[0].ev = esi.ESI_PACKET_OPEN, None
         assert esi.esi_server_run(srv, bad, 1, 1000, 0, 0) == esi.ESI_EINVAL
+        bad[0].kind, bad[0].stream = esi.ESI_PACKET_EVENTS, 1 << 20
+        assert esi.esi_server_run(srv, bad, 1, 1000, 0, 0) == esi.ESI_EINVAL
     finally:
         esi.esi_server_destroy(srv)

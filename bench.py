@@ -10,9 +10,16 @@ by k * 2 s, so the state carries on as one continuous stream.
 value: events/s with every step's events already resident in device memory
 (pushed before the timed region), frames written to device memory; inputs
 per step (160 MB) exceed the 129 MB L2.  e2e: the same metric through the C
-ABI with pinned host buffers (events pushed from host, frames read back to
-host) inside the timed region.  With --gpus N (torchrun) every rank runs its
-own replica on its own GPU (no collective on the data path; weak scaling).
+ABI with pinned host buffers inside the timed region: each step pushes its
+events from host memory and renders its frames into a host buffer, the next
+step's push overlapping this step's render (the synchronous variant is
+reported beside it).  With --gpus N (torchrun) every rank runs its own replica
+on its own GPU (no collective on the data path; weak scaling).
+
+Further legs on rank 0 (skipped with --no-extras): single-frame latency;
+serving of config 3 (64 streams) and config 4 (192 mixed streams with joins
+and leaves), batched and plain; configs 0 and 2 with the default and the
+autotuned launch shape; the oracle on one host core and on all of them.
 
 --impl reference times the FP64 CPU oracle (the test reference) on the host
 cores instead, on a bounded sample of the same workload.

@@ -8,6 +8,10 @@
 namespace esi {
 
 constexpr int kStageFrames = 256;   // per-frame constants a tile block keeps in shared memory
+#ifndef ESI_GATHER_LANES
+#define ESI_GATHER_LANES 4
+#endif
+constexpr int kGatherLanes = ESI_GATHER_LANES;   // lanes copying one run of a batch
 
 static __host__ __device__ inline int tile_round_up(int v, int m) { return (v + m - 1) / m * m; }
 
@@ -179,18 +183,21 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
         const bool last = b0 + (unsigned)R >= total;
 
         // gather the batch (records b0 .. b0 + nb of this tile, arrival
-        // order, plus the next batch's first record): one thread per run,
-        // asynchronous copies, so every record of the batch is in flight
+        // order, plus the next batch's first record) with asynchronous
+        // copies, so every record of the batch is in flight
         const unsigned next = last ? 0u : 1u;
         if (nb > 0) {
             const unsigned bend = b0 + (unsigned)nb + next;
             const int cfirst = run_of(runpre, n_chunks, b0);
             const int clast = run_of(runpre, n_chunks, bend - 1u);
-            for (int c = cfirst + tid; c <= clast; c += NT) {
+            // kGatherLanes lanes per run: a warp instruction copies several
+            // runs, each from contiguous addresses
+            const int grp = tid / kGatherLanes, sub = tid % kGatherLanes;
+            for (int c = cfirst + grp; c <= clast; c += NT / kGatherLanes) {
                 const unsigned rs = max(runpre[c], b0), re = min(runpre[c + 1], bend);
                 const unsigned long long *src =
                     a.rec + (size_t)c * a.chunk + runoff[c] + (rs - runpre[c]);
-                for (unsigned i = 0; i + rs < re; ++i) cp_async8(&A[rs - b0 + i], src + i);
+                for (unsigned i = sub; i + rs < re; i += kGatherLanes) cp_async8(&A[rs - b0 + i], src + i);
             }
         }
         cp_async_wait_all();

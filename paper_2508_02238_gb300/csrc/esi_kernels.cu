@@ -168,9 +168,11 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
     for (int j = tid; j < n_tiles; j += NT)
         a.hrow[(size_t)j * n_chunks_all + cidx] = (tstart[j] << 16) | (tstart[j + 1] - tstart[j]);
 
-    // phase 3: scatter every event to its stable place in tile order
+    // phase 3: scatter every event to its stable place in tile order; each
+    // warp scatters the slice it ranked
     const int th_mask = (1 << thl) - 1;
-    for (int k = tid; k < nc; k += NT) {
+    const int w = warp;
+    for (int k = warp * per + lane; k < min(nc, (warp + 1) * per); k += 32) {
         const unsigned tile = ltile[k];
         if (tile == 0xffffu) continue;
         const int4 e = sev[k];
@@ -178,7 +180,6 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
         const long long t = ((long long)(unsigned)e.y << 32) | (unsigned)e.x;
         const unsigned pit = ((unsigned)(y & th_mask) << twl) | (unsigned)(x & ((1 << twl) - 1));
         const bool pos = (signed char)(e.w & 0xff) > 0;
-        const int w = k / per;
         ssort[tstart[tile] + cnt[w * ntp + tile] + loff[k]] =
             make_record((unsigned)(t - a.t_base), pit, pos ? 1u : 0u);
     }

@@ -235,10 +235,11 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
             if (tid == 0) rowstart[TH] = (unsigned)nb;
         }
         __syncthreads();
-        for (int k = tid; k < nb; k += NT) {
+        // each warp scatters the slice it ranked
+        for (int k = s0 + lane; k < s1; k += 32) {
             const unsigned long long r = A[k];
             const int row = (int)(r >> (33 + XB));
-            B[rcnt[k / max(sl, 1)][row] + lpos[k]] = r;
+            B[rcnt[warp][row] + lpos[k]] = r;
         }
         __syncthreads();
 

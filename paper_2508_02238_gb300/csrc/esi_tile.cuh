@@ -147,17 +147,18 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
     auto apply_group = [&](unsigned long long r, bool valid) {
         const int x = (int)((r >> 33) & (unsigned)(TWP - 1));
         const unsigned toff = (unsigned)r;
+        // the pixel's state as the group starts (no lane writes it before the
+        // write-back below): loaded by every lane while the peers are found
+        const float s_mem = rS[x];
+        const long long o_mem = rO[x];
         const unsigned peers = warp_peers_n<XB>((unsigned)x, valid);
         const unsigned below = peers & lanemask_lt();
         const unsigned rank = __popc(below);
         const int prev = below ? 31 - __clz(below) : lane;
         const unsigned t_prev_rec = __shfl_sync(kFull, toff, prev);
-        float s_in = 0.0f;
-        long long t_prev = (long long)t_prev_rec;
-        if (valid && rank == 0) {
-            s_in = rS[x];
-            t_prev = rO[x];
-        }
+        const bool first = valid && rank == 0;
+        float s_in = first ? s_mem : 0.0f;
+        const long long t_prev = first ? o_mem : (long long)t_prev_rec;
         const float d = valid ? decay_state_k<DK>((long long)toff - t_prev, dp) : 0.0f;
         const float c = ((r >> 32) & 1u) ? mp.C : -mp.C;
         const unsigned maxr = __reduce_max_sync(kFull, valid ? rank : 0u);

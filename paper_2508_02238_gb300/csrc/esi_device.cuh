@@ -56,6 +56,20 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
         : "memory");
 }
 
+// The same with an L2 evict-first hint: for data read exactly once (the
+// events), so that it leaves L2 before data a later kernel reads again.
+__device__ __forceinline__ void bulk_g2s_stream(void *dst, const void *src, unsigned bytes,
+                                                uint64_t *bar)
+{
+    uint64_t policy;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
 {
     unsigned ok;

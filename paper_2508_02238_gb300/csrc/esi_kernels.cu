@@ -93,8 +93,8 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
         const unsigned long long r0 = (a.first + (unsigned long long)c0) & a.ring_mask;
         const int n1 = (int)min((unsigned long long)nc, cap - r0);
         mbar_expect_tx(&bar, (unsigned)nc * 16u);
-        bulk_g2s(sev, a.ring + r0, (unsigned)n1 * 16u, &bar);
-        if (n1 < nc) bulk_g2s(sev + n1, a.ring, (unsigned)(nc - n1) * 16u, &bar);
+        bulk_g2s_stream(sev, a.ring + r0, (unsigned)n1 * 16u, &bar);
+        if (n1 < nc) bulk_g2s_stream(sev + n1, a.ring, (unsigned)(nc - n1) * 16u, &bar);
     }
     __shared__ int s_copy_ok;
     for (int i = tid; i < NW * ntp; i += NT) cnt[i] = 0;

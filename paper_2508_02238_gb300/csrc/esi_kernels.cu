@@ -228,8 +228,9 @@ size_t tile_smem_bytes(int tile_h, int batch, int n_chunks)
 
 size_t tile_static_smem_bytes(int tile_h, int tile_w)
 {
-    // pixel state (S, F, O per pixel), staged frames and the sort scratch
-    return (size_t)tile_h * tile_w * 16 + (size_t)kStageFrames * sizeof(WinInfo) +
+    // pixel state (S, F, O and a peer mask per pixel), staged frames and the
+    // sort scratch
+    return (size_t)tile_h * tile_w * 20 + (size_t)kStageFrames * sizeof(WinInfo) +
            (size_t)tile_h * tile_h * 2 + 1024;
 }
 

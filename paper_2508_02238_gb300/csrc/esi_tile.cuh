@@ -49,8 +49,9 @@ __device__ __forceinline__ int run_of(const unsigned *pre, int n, unsigned g)
 // 32-pixel rows: narrower rows give more independent row walks).
 // Events are applied event-parallel: a row's records are in time order, so at
 // each frame the due records go 32 at a time, one per lane; lanes holding the
-// same pixel (peer masks from one ballot per x bit) apply theirs in arrival
-// order, rank by rank, to the pixel state kept in shared memory.  RD: render_decay; DK: decay kind; VEC
+// same pixel (their lane masks gathered in a shared-memory word per pixel)
+// apply theirs in arrival order, rank by rank, to the pixel state kept in
+// shared memory.  RD: render_decay; DK: decay kind; VEC
 // (PPL = 4 or 2): rows start PPL-byte aligned (W % PPL == 0), so a lane's
 // pixels move as one float4 / two longlong2 / one 32-bit frame word (PPL = 4)
 // or one 16-bit frame word (PPL = 2).
@@ -71,6 +72,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
     __shared__ __align__(16) float sS[TH][TWP];      // S of the tile's pixels
     __shared__ __align__(16) float sF[TH][TWP];      // (float)(T - t_base)
     __shared__ __align__(16) long long sO[TH][TWP];  // T - t_base
+    __shared__ unsigned sPeer[TH][TWP];              // per-pixel lane masks of a group (kept zero)
 
     const int R = a.batch, n_chunks = a.n_chunks;
     size_t off_b, off_runpre, off_runoff, off_lpos;
@@ -89,6 +91,8 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
     const long long tb = a.t_base;
     const DecayParams dp = a.dp;
     const MapParams mp = a.mp;
+    unsigned *rP = sPeer[warp];
+    for (int i = lane; i < TWP; i += 32) rP[i] = 0u;
     float *rS = sS[warp];
     float *rF = sF[warp];
     long long *rO = sO[warp];
@@ -151,7 +155,13 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
         // write-back below): loaded by every lane while the peers are found
         const float s_mem = rS[x];
         const long long o_mem = rO[x];
-        const unsigned peers = warp_peers_n<XB>((unsigned)x, valid);
+        // lanes holding the same pixel: each sets its bit in the pixel's
+        // mask word, reads the word, and clears it for the next group
+        if (valid) atomicOr(&rP[x], 1u << lane);
+        __syncwarp();
+        const unsigned peers = valid ? rP[x] : 0u;
+        __syncwarp();
+        if (valid) rP[x] = 0u;
         const unsigned below = peers & lanemask_lt();
         const unsigned rank = __popc(below);
         const int prev = below ? 31 - __clz(below) : lane;

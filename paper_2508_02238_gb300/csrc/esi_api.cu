@@ -114,7 +114,7 @@ static int apply_tuning(esi_handle *h, const esi_tuning &t)
     h->th_log2 = th_log2;
     h->tw_log2 = t.tile_w == 32 ? 5 : t.tile_w == 64 ? 6 : 7;
     // the binning kernel keeps per-warp counters for every tile in shared memory
-    if (bin_smem_bytes(t.chunk_events, h->n_tiles) + 1024 > (size_t)kMaxSmemPerBlock) return ESI_ERANGE;
+    if (bin_smem_bytes(t.chunk_events, h->n_tiles, false) + 1024 > (size_t)kMaxSmemPerBlock) return ESI_ERANGE;
     const int max_chunks = (t.max_batch_events + t.chunk_events - 1) / t.chunk_events;
     if (tile_smem_bytes(t.tile_h, t.batch_records, max_chunks) + tile_static_smem_bytes(t.tile_h, t.tile_w) >
         (size_t)kMaxSmemPerBlock)
@@ -977,6 +977,7 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
             ba.tile_bits = index_bits(h->n_tiles);
             ba.rec = h->rec[buf];
             ba.hrow = h->hrow[buf];
+            ba.use_mask = (h->n_tiles <= kBinMaskTiles && bin_mask_fits(chunk, h->n_tiles)) ? 1 : 0;
             ba.status = h->dstatus;
             cudaEvent_t ev;
             rc = prof_begin(h, &ev, h->bin_stream);

@@ -42,6 +42,11 @@ struct DevStatus {
     int err_where;                // which kernel / wait gave up
 };
 
+// Up to this many tiles the binning finds same-tile lanes through a mask word
+// per tile and warp in shared memory (when it fits); above, through one
+// ballot per tile-index bit.
+constexpr int kBinMaskTiles = 1024;
+
 // Result of a device-checked push: an order violation anywhere, and the time
 // of the push's last event.
 struct PushResult {
@@ -68,6 +73,7 @@ struct BinArgs {
     int tile_bits;                // bits of a tile index (n_tiles <= 2^tile_bits)
     unsigned long long *rec;      // out: records, block c at rec + c * chunk
     unsigned int *hrow;           // out: [tile][chunk] (start << 16 | count)
+    int use_mask;                 // same-tile lanes by shared mask words (up to 1024 tiles)
     DevStatus *status;
 };
 
@@ -143,7 +149,8 @@ inline int index_bits(int n)
 }
 
 // Launchers (esi_kernels.cu).
-size_t bin_smem_bytes(int chunk, int n_tiles);
+size_t bin_smem_bytes(int chunk, int n_tiles, bool mask);
+bool bin_mask_fits(int chunk, int n_tiles);
 size_t tile_smem_bytes(int tile_h, int batch, int n_chunks);
 size_t tile_static_smem_bytes(int tile_h, int tile_w);
 cudaError_t launch_bin(const BinArgs &a, int n_chunks, cudaStream_t s);
@@ -157,7 +164,7 @@ cudaError_t set_tile_attributes_w128();
 cudaError_t set_tile_attributes_w32();
 cudaError_t set_tile_attributes_w64();
 cudaError_t launch_bin_batch_tab(const unsigned char *tab, int grid, int chunk, int max_tiles,
-                                 cudaStream_t s);
+                                 bool mask, cudaStream_t s);
 cudaError_t launch_tile_batch_tab(const unsigned char *tab, int group, int grid, int tile_h, int rd,
                                   int dk, bool vec, int batch, int max_chunks, cudaStream_t s);
 int decay_kind_of(const DecayParams &dp);

@@ -34,8 +34,9 @@ constexpr int kWhereBinCopy = 1;
 static __host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 // Shared-memory layout of the binning kernel.
-static __host__ __device__ inline size_t bin_layout(int chunk, int n_tiles, size_t *off_sort,
-                                                    size_t *off_tstart, size_t *off_cnt)
+static __host__ __device__ inline size_t bin_layout(int chunk, int n_tiles, bool mask,
+                                                    size_t *off_sort, size_t *off_tstart,
+                                                    size_t *off_cnt)
 {
     constexpr int NW = kBinThreads / 32;
     size_t o = 0;
@@ -48,13 +49,26 @@ static __host__ __device__ inline size_t bin_layout(int chunk, int n_tiles, size
     o += (size_t)NW * round_up(n_tiles, 8) * 2;    // per-warp tile counters
     o += (size_t)chunk * 2;                        // event: offset within its warp's tile run
     o += (size_t)chunk * 2;                        // event: tile (0xffff = dropped)
+    if (mask)
+        o += (size_t)NW * round_up(n_tiles, 8) * 4; // per-warp lane masks per tile (kept zero)
     return o;
 }
 
-size_t bin_smem_bytes(int chunk, int n_tiles)
+// Shared memory for chunks of `chunk` events over at most n_tiles tiles;
+// with `mask`, jobs of at most kBinMaskTiles tiles use the mask words, so the
+// larger of the two layouts.
+size_t bin_smem_bytes(int chunk, int n_tiles, bool mask)
 {
     size_t a, b, c;
-    return bin_layout(chunk, n_tiles, &a, &b, &c);
+    const size_t plain = bin_layout(chunk, n_tiles, false, &a, &b, &c);
+    if (!mask) return plain;
+    return std::max(plain, bin_layout(chunk, std::min(n_tiles, kBinMaskTiles), true, &a, &b, &c));
+}
+
+// Whether chunks over up to n_tiles tiles can take the mask-word layout.
+bool bin_mask_fits(int chunk, int n_tiles)
+{
+    return bin_smem_bytes(chunk, n_tiles, true) + 1024 <= (size_t)kMaxSmemPerBlock;
 }
 
 // One chunk of events: block-level body shared by the single-sensor and the
@@ -69,14 +83,16 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
 
     const int chunk = a.chunk, n_tiles = a.n_tiles;
     const int ntp = round_up(n_tiles, 8);
+    const bool use_mask = a.use_mask && n_tiles <= kBinMaskTiles;
     size_t off_sort, off_tstart, off_cnt;
-    bin_layout(chunk, n_tiles, &off_sort, &off_tstart, &off_cnt);
+    bin_layout(chunk, n_tiles, use_mask, &off_sort, &off_tstart, &off_cnt);
     int4 *sev = reinterpret_cast<int4 *>(smem);
     unsigned long long *ssort = reinterpret_cast<unsigned long long *>(smem + off_sort);
     unsigned *tstart = reinterpret_cast<unsigned *>(smem + off_tstart);
     unsigned short *cnt = reinterpret_cast<unsigned short *>(smem + off_cnt);
     unsigned short *loff = cnt + NW * ntp;
     unsigned short *ltile = loff + chunk;
+    unsigned *tmask = reinterpret_cast<unsigned *>(ltile + chunk);   // [NW][ntp], if use_mask
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long c0 = (long long)cidx * chunk;
@@ -98,6 +114,8 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
     }
     __shared__ int s_copy_ok;
     for (int i = tid; i < NW * ntp; i += NT) cnt[i] = 0;
+    if (use_mask)
+        for (int i = tid; i < NW * ntp; i += NT) tmask[i] = 0u;
     if (tid == 0) {
         // one thread waits for the copy; the others sleep at the barrier
         int ok = mbar_wait_bounded(&bar, 0, kWaitLimitNs) ? 1 : 0;
@@ -133,7 +151,19 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
                 ++drop;
         }
         const bool valid = tile >= 0;
-        const unsigned peers = warp_peers((unsigned)tile, tbits, valid);
+        unsigned peers;
+        if (use_mask) {
+            // each lane sets its bit in its tile's mask word, reads the word
+            // and clears it once every lane has read
+            unsigned *mw = tmask + warp * ntp + (valid ? tile : 0);
+            if (valid) atomicOr(mw, 1u << lane);
+            __syncwarp();
+            peers = valid ? *mw : 0u;
+            __syncwarp();
+            if (valid) *mw = 0u;
+        } else {
+            peers = warp_peers((unsigned)tile, tbits, valid);
+        }
         const unsigned rank = __popc(peers & lanemask_lt());
         const unsigned pre = valid ? cnt[warp * ntp + tile] : 0u;
         __syncwarp();
@@ -253,15 +283,15 @@ cudaError_t set_kernel_attributes()
 
 cudaError_t launch_bin(const BinArgs &a, int n_chunks, cudaStream_t s)
 {
-    const size_t smem = bin_smem_bytes(a.chunk, a.n_tiles);
+    const size_t smem = bin_smem_bytes(a.chunk, a.n_tiles, a.use_mask != 0);
     esi_bin_kernel<<<n_chunks, kBinThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bin_batch_tab(const unsigned char *tab, int grid, int chunk, int max_tiles,
-                                 cudaStream_t s)
+                                 bool mask, cudaStream_t s)
 {
-    const size_t smem = bin_smem_bytes(chunk, max_tiles);
+    const size_t smem = bin_smem_bytes(chunk, max_tiles, mask);
     esi_bin_tab_kernel<<<grid, kBinThreads, smem, s>>>(tab);
     return cudaGetLastError();
 }

@@ -185,6 +185,7 @@ extern "C" int esi_render_frames_noalloc(int width, int height, const esi_params
         ba.tile_bits = index_bits(n_tiles);
         ba.rec = rec;
         ba.hrow = hrow;
+        ba.use_mask = 0;
         ba.status = st;
         rc = cuda_rc(launch_bin(ba, n_chunks, s));
         if (rc) return rc;

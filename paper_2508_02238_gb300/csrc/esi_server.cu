@@ -178,6 +178,7 @@ struct esi_server {
     // capacities of one tick
     int cap_jobs = 0, cap_chunks = 0, cap_items = 0, cap_frames = 0, max_tiles = 0;
     int tile_grid = 0;  // persistent grid of the batched tile kernel
+    bool bin_mask = false;  // binning jobs of up to 1024 tiles use mask words
     long long cap_events = 0;
     size_t off_binjob = 0, off_chunkjob = 0, off_tilejob = 0, off_items = 0, off_win = 0,
            off_fout = 0, off_events = 0, tab_bytes = 0;
@@ -291,7 +292,7 @@ int build_graph(esi_server *s, unsigned long long groups)
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess)
-        e = launch_bin_batch_tab(s->dtab, s->cap_chunks, kChunk, s->max_tiles, cs);
+        e = launch_bin_batch_tab(s->dtab, s->cap_chunks, kChunk, s->max_tiles, s->bin_mask, cs);
     for (int gi = 0; gi < kGroups && e == cudaSuccess; ++gi)
         if (groups & (1ull << gi)) e = launch_group(s, gi, cs);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(cs, on_tick_done, s->comp);
@@ -398,6 +399,7 @@ int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts, vo
     off = align_up(off + sizeof(esi_event) * (size_t)s->cap_events, 256);
     s->tab_bytes = off;
     s->hrow_cap = (size_t)s->cap_chunks * (size_t)s->max_tiles;
+    s->bin_mask = bin_mask_fits(kChunk, s->max_tiles);
 
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = set_kernel_attributes();
@@ -714,6 +716,7 @@ int esi_server_tick(esi_server *s, int64_t now_us)
         B.args.tile_bits = index_bits(st.n_tiles);
         B.args.rec = s->rec + (size_t)n_chunks * kChunk;
         B.args.hrow = s->hrow + hrow_off;
+        B.args.use_mask = s->bin_mask ? 1 : 0;
         B.args.status = s->dstatus;
         B.first_chunk = n_chunks;
         for (int c = 0; c < chunks; ++c) cj[n_chunks + c] = j;
@@ -824,7 +827,7 @@ int esi_server_tick(esi_server *s, int64_t now_us)
             for (int g = 0; g < kGroups; ++g) ng += (int)((s->graph_groups >> g) & 1ull);
             s->launches_per_tick = 1 + ng;
         } else {
-            e = launch_bin_batch_tab(s->dtab, s->cap_chunks, kChunk, s->max_tiles, s->stream);
+            e = launch_bin_batch_tab(s->dtab, s->cap_chunks, kChunk, s->max_tiles, s->bin_mask, s->stream);
             for (int g = 0; g < kGroups && e == cudaSuccess; ++g)
                 if (groups & (1ull << g)) e = launch_group(s, g, s->stream);
             if (e == cudaSuccess) e = cudaLaunchHostFunc(s->stream, on_tick_done, s->comp);

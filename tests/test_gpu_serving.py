@@ -393,3 +393,25 @@ def test_executor_join_leave_and_admission():
         assert esi.esi_server_run(srv, bad, 1, 1000, 0, 0) == esi.ESI_EINVAL
     finally:
         esi.esi_server_destroy(srv)
+
+
+def test_large_and_small_streams_in_one_tick():
+    # a 1280x720 stream at tile height 4 has 1800 tiles: its binning job
+    # finds same-tile lanes by ballots, while the small stream's job in the
+    # same launch uses the shared-memory mask words
+    big = (1280, 720, dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1),
+           "random")
+    small = STREAMS[0]
+    t_end = 40_000
+    res, _ = serve([(0, big), (1, small)], t_end, tile_hs={0: 4})
+    for i, (W, H, p, kind) in ((0, big), (1, small)):
+        frames, (S, T), ev = res[i]
+        expect_tf = list(range(10_000, t_end + 1, 10_000))
+        assert sorted(frames) == expect_tf
+        pp = {**dict(t_origin_us=0), **p}
+        used = ev[ev["t"] <= t_end]
+        st_ref = oracle.OracleState(W, H, oracle_params(pp))
+        ref_frames, n_used = st_ref.replay(used, expect_tf)
+        st_ref.integrate(used[n_used:])
+        got = {"S": S, "T": T, "frames": np.stack([frames[t] for t in expect_tf])}
+        compare(got, {"S": st_ref.S, "T": st_ref.T, "frames": ref_frames}, pp["C"], f"stream {i}")

@@ -45,19 +45,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
                  : "memory");
 }
 
-// 1-D bulk copy global -> shared through the TMA unit; completes `bytes` of
-// transaction count on `bar`.  dst, src 16-byte aligned, bytes % 16 == 0.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// The same with an L2 evict-first hint: for data read exactly once (the
-// events), so that it leaves L2 before data a later kernel reads again.
+// 1-D bulk copy global -> shared through the TMA unit, completing `bytes` of
+// transaction count on `bar` (dst, src 16-byte aligned, bytes % 16 == 0),
+// with an L2 evict-first hint: for data read exactly once (the events), so
+// that it leaves L2 before data a later kernel reads again.
 __device__ __forceinline__ void bulk_g2s_stream(void *dst, const void *src, unsigned bytes,
                                                 uint64_t *bar)
 {
@@ -224,21 +215,6 @@ __device__ __forceinline__ float decay_state(long long dt, const DecayParams &dp
     }
 }
 
-// Eq. 4 for the render-time view; only feeds an 8-bit code, so the general-b
-// case uses the fast hardware power.
-__device__ __forceinline__ float decay_view(long long dt, const DecayParams &dp)
-{
-    if (dt >= dp.cutoff) return 0.0f;
-    if (dp.b_mode == 4) return 1.0f;
-    float u = one_minus_kdt(dt, dp);
-    switch (dp.b_mode) {
-    case 1: return u;
-    case 2: return u * u;
-    case 3: return u * u * u;
-    default: return __powf(u, dp.b);
-    }
-}
-
 // Decay kinds the kernels are specialised on.
 enum DecayKind { kDecayGeneral = 0, kDecaySquare = 1, kDecayNone = 2 };
 
@@ -277,34 +253,6 @@ __device__ __forceinline__ unsigned quantize_u8(float x)
     unsigned short r;
     asm("cvt.rni.sat.u8.f32 %0, %1;" : "=h"(r) : "f"(x));
     return r;
-}
-
-// Alg. 2 loop body for one event of this pixel, in the paper's order:
-// S <- S + p C;  dt <- t - T;  S <- S d(dt);  T <- t;  S <- clamp (Eq. 13).
-__device__ __forceinline__ void esi_apply(float &S, long long &T, long long t, bool pos,
-                                          const DecayParams &dp, const MapParams &mp)
-{
-    float s = S + (pos ? mp.C : -mp.C);
-    long long dt = t - T;
-    s = s * decay_state(dt, dp);
-    T = t;
-    S = fminf(fmaxf(s, mp.s_min), mp.s_max);
-}
-
-// Eq. 14 with round-half-to-even and saturation to [0, 255].
-__device__ __forceinline__ unsigned char esi_quantize(float v, const MapParams &mp)
-{
-    int r = __float2int_rn(fmaf(v, mp.scale, mp.offs));
-    r = max(0, min(255, r));
-    return static_cast<unsigned char>(r);
-}
-
-__device__ __forceinline__ unsigned char esi_pixel_code(float S, long long T, long long t_frame,
-                                                        const DecayParams &dp, const MapParams &mp)
-{
-    float v = S;
-    if (mp.render_decay && S != 0.0f) v = S * decay_view(t_frame - T, dp);
-    return esi_quantize(v, mp);
 }
 
 __device__ __forceinline__ void set_error(DevStatus *st, int code, int where)

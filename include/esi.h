@@ -125,7 +125,9 @@ typedef struct esi_handle esi_handle;
  * S = 0, T = t_origin for every pixel) on the current CUDA device.
  * width, height in [1, 65535].  cuda_stream: a cudaStream_t or NULL.
  * Errors: ESI_EINVAL for bad sizes or parameters (checked before any CUDA
- * call), ESI_ENOMEM, ESI_ECUDA.
+ * call), ESI_ERANGE for sensors with more tiles than the binning can count
+ * in shared memory (above about 10,000 tiles of 128 x 16 pixels, some
+ * 20 M pixels), ESI_ENOMEM, ESI_ECUDA.
  */
 int esi_create(int width, int height, const esi_params *params,
                void *cuda_stream, esi_handle **out);

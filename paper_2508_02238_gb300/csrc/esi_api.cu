@@ -414,7 +414,18 @@ int esi_create(int width, int height, const esi_params *params, void *cuda_strea
     h->frame_floor = params->t_origin_us;
     h->last_event_t = params->t_origin_us;
     h->last_frame_t = params->t_origin_us;
+    // the default shape, or for large sensors (too many tiles for the
+    // binning's per-tile counters) taller tiles and smaller chunks
     rc = apply_tuning(h, default_tuning(width, height));
+    for (int chunk : {2048, 1024, 512}) {
+        if (rc != ESI_ERANGE) break;
+        esi_tuning t = default_tuning(width, height);
+        t.tile_w = 128;
+        t.tile_h = 16;
+        t.chunk_events = chunk;
+        t.batch_records = 2048;
+        rc = apply_tuning(h, t);
+    }
     if (rc) {
         delete h;
         return rc;

@@ -482,3 +482,15 @@ def test_async_host_output_with_overlapping_pushes():
         S, T = g.state()
     ref = run_oracle(ev, W, H, p, np.concatenate(tfs))
     compare({"S": S, "T": T, "frames": frames}, ref, p["C"], "async host output")
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (1, 300), (300, 1), (65535, 2), (3, 65535), (4000, 3000)])
+def test_extreme_sensor_shapes(W, H):
+    # single pixels, single rows and columns, the widest and tallest sizes,
+    # and a 12 M-pixel sensor (taller tiles and smaller chunks by default)
+    rng = np.random.default_rng(W * 7 + H)
+    n = min(200_000, max(50, W * H * 2))
+    ev = random_events(rng, W, H, n, 0, 300_000, hot=(W - 1, H - 1, 0.05))
+    p = P(render_decay=1)
+    tf = np.array([100_000, 200_000, 300_000], dtype=np.int64)
+    compare(run_gpu(ev, W, H, p, tf), run_oracle(ev, W, H, p, tf), p["C"], f"{W}x{H}")

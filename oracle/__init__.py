@@ -11,6 +11,9 @@ multiply-add); this module only marshals numpy arrays.  It follows:
 * Eq. 4  -- d(t) = max(1 - k t, 0)^b (reading of max{(1-kt)^b, 0}).
 * Eq. 14 -- B = 255 (S - S_min) / (S_max - S_min), round half to even,
   saturate; ``render_decay`` maps the view S d(t_frame - T) instead of S.
+* ``method`` 1 -- Alg. 1: the same loop without the clamp (Eq. 2 when k = 0).
+* ``method`` 2 -- Eq. 3 with d(t) = exp(-k t), no clamp, kept as the exact
+  regrouping S <- S exp(-k (t - T)) + p C; T <- t of its sum.
 
 Pinned by ``tests/test_oracle_pins.py`` against closed forms the paper fixes
 (Eq. 2, the corrected Eq. 5, Eq. 6), hand-worked cases, invariants and a
@@ -59,14 +62,16 @@ def _load():
         i64, d, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_int
         lib.oracle_decay.argtypes = [i64, d, d]
         lib.oracle_decay.restype = d
+        lib.oracle_decay_exp.argtypes = [i64, d]
+        lib.oracle_decay_exp.restype = d
         lib.oracle_init.argtypes = [P, P, i64, i64]
         lib.oracle_init.restype = None
-        lib.oracle_integrate.argtypes = [P, i64, i32, i32, d, d, d, d, d, P, P, P]
+        lib.oracle_integrate.argtypes = [P, i64, i32, i32, d, d, d, d, d, i32, P, P, P]
         lib.oracle_integrate.restype = i64
-        lib.oracle_render.argtypes = [P, P, i64, d, d, d, d, i32, i64, P]
+        lib.oracle_render.argtypes = [P, P, i64, d, d, d, d, i32, i32, i64, P]
         lib.oracle_render.restype = None
-        lib.oracle_replay.argtypes = [P, i64, i32, i32, d, d, d, d, d, i32, P,
-                                      i64, P, P, P, P]
+        lib.oracle_replay.argtypes = [P, i64, i32, i32, d, d, d, d, d, i32, i32,
+                                      P, i64, P, P, P, P]
         lib.oracle_replay.restype = i64
         _lib = lib
         return lib
@@ -74,7 +79,10 @@ def _load():
 
 @dataclass(frozen=True)
 class OracleParams:
-    """ESI parameters: C (Alg. 2), k in 1/s and b (Eq. 4), clamp bounds (Eq. 13)."""
+    """ESI parameters: C (Alg. 2), k in 1/s and b (Eq. 4), clamp bounds (Eq. 13).
+
+    method: 0 Alg. 2, 1 Alg. 1 (no clamp), 2 Eq. 3 with d(t) = exp(-k t).
+    """
     C: float
     k_per_s: float
     b: float
@@ -82,6 +90,7 @@ class OracleParams:
     s_max: float
     t_origin_us: int = 0
     render_decay: int = 0
+    method: int = 0
 
 
 def _ptr(a: np.ndarray) -> int:
@@ -91,6 +100,11 @@ def _ptr(a: np.ndarray) -> int:
 def decay(dt_us: int, k_per_s: float, b: float) -> float:
     """Eq. 4 (reading max(1 - k dt, 0)^b), dt in microseconds."""
     return float(_load().oracle_decay(int(dt_us), float(k_per_s), float(b)))
+
+
+def decay_exp(dt_us: int, k_per_s: float) -> float:
+    """The exponential decay exp(-k dt) used with Eq. 3, dt in microseconds."""
+    return float(_load().oracle_decay_exp(int(dt_us), float(k_per_s)))
 
 
 class OracleState:
@@ -110,7 +124,7 @@ class OracleState:
         p = self.params
         return int(_load().oracle_integrate(
             _ptr(ev), len(ev), self.W, self.H, p.C, p.k_per_s, p.b, p.s_min,
-            p.s_max, _ptr(self.S), _ptr(self.T), _ptr(self.dropped)))
+            p.s_max, int(p.method), _ptr(self.S), _ptr(self.T), _ptr(self.dropped)))
 
     def render(self, t_frame_us: int, render_decay: int | None = None) -> np.ndarray:
         """Eq. 14 frame (uint8, H x W) at t_frame."""
@@ -119,7 +133,7 @@ class OracleState:
         B = np.empty(self.W * self.H, dtype=np.uint8)
         _load().oracle_render(_ptr(self.S), _ptr(self.T), self.W * self.H,
                               p.k_per_s, p.b, p.s_min, p.s_max, int(rd),
-                              int(t_frame_us), _ptr(B))
+                              int(p.method), int(t_frame_us), _ptr(B))
         return B.reshape(self.H, self.W)
 
     def replay(self, events: np.ndarray, t_frames) -> tuple[np.ndarray, int]:
@@ -134,6 +148,6 @@ class OracleState:
         p = self.params
         used = _load().oracle_replay(
             _ptr(ev), len(ev), self.W, self.H, p.C, p.k_per_s, p.b, p.s_min,
-            p.s_max, int(p.render_decay), _ptr(tf), M, _ptr(self.S),
+            p.s_max, int(p.render_decay), int(p.method), _ptr(tf), M, _ptr(self.S),
             _ptr(self.T), _ptr(B), _ptr(self.dropped))
         return B, int(used)

@@ -20,6 +20,19 @@
  *     S * d(t_frame - T), which is not written back; with render_decay = 0 it
  *     is S as stored, as Alg. 2 renders it.
  *
+ * Three methods share the event loop (argument `method`):
+ *   0  Alg. 2 as above (the default).
+ *   1  Alg. 1 (Sec. III-B): the same loop without the clamp of Eq. 13.  With
+ *      k = 0 it is the plain integration of Eq. 2.
+ *   2  Eq. 3 (Sec. III-B) with the exponential decay d(t) = exp(-k t):
+ *      L(t) = C sum_{t_i <= t} p_i exp(-k (t - t_i)), no clamp.  Since
+ *      exp(-k a) exp(-k b) = exp(-k (a + b)), the sum regroups exactly (up to
+ *      rounding) into a per-pixel recurrence on (S, T) = (L(T), the last
+ *      event time):  S <- S exp(-k (t_i - T)) + p_i C;  T <- t_i.  The event's
+ *      own term enters undecayed, unlike Alg. 1 and 2.  b is not used.
+ * For every method the render maps with Eq. 14 and saturates to [0, 255];
+ * the decay view uses the method's own d.
+ *
  * Other readings: polarity p > 0 counts +1, anything else -1 (Sec. III-A gives
  * p in {+1, -1}); events with x >= W or y >= H are dropped and counted, never
  * applied; time is int64 microseconds and k is given per second, so the
@@ -50,19 +63,43 @@ double oracle_decay(int64_t dt_us, double k_per_s, double b)
     return 0.0;
 }
 
-/* One pass of the Alg. 2 loop body for one accepted event at pixel index pix. */
+/* The decay of Eq. 3 read with d(t) = exp(-k t); dt in microseconds, k in 1/s. */
+double oracle_decay_exp(int64_t dt_us, double k_per_s)
+{
+    return exp(-(k_per_s * 1e-6) * (double)dt_us);
+}
+
+/* The decay function of a method (Eq. 4 for Alg. 1 and 2, exp for Eq. 3). */
+static double method_decay(int method, int64_t dt, double k_per_s, double b)
+{
+    if (method == 2)
+        return oracle_decay_exp(dt, k_per_s);
+    return oracle_decay(dt, k_per_s, b);
+}
+
+/* One pass of the event loop for one accepted event at pixel index pix. */
 static void oracle_step(double *S, int64_t *T, int64_t pix, int8_t p, int64_t t,
                         double C, double k_per_s, double b, double s_min,
-                        double s_max)
+                        double s_max, int method)
 {
     double pol = (p > 0) ? 1.0 : -1.0;
     double s = S[pix];
+    if (method == 2) {
+        /* Eq. 3 regrouped: L(t_i) = L(T) exp(-k (t_i - T)) + p_i C */
+        s = s * oracle_decay_exp(t - T[pix], k_per_s);
+        s = s + pol * C;
+        T[pix] = t;
+        S[pix] = s;
+        return;
+    }
     s = s + pol * C;                              /* S <- S + p C          */
     int64_t dt = t - T[pix];                      /* dt <- t - T           */
     s = s * oracle_decay(dt, k_per_s, b);         /* S <- S max{(1-k dt)^b,0} */
     T[pix] = t;                                   /* T <- t                */
-    if (s < s_min) s = s_min;                     /* S <- min(max(S,Smin),Smax) */
-    if (s > s_max) s = s_max;
+    if (method == 0) {                            /* S <- min(max(S,Smin),Smax) */
+        if (s < s_min) s = s_min;
+        if (s > s_max) s = s_max;
+    }
     S[pix] = s;
 }
 
@@ -80,13 +117,15 @@ void oracle_init(double *S, int64_t *T, int64_t P, int64_t t_origin)
 }
 
 /*
- * Alg. 2 event loop over n events in push order.  S and T (row-major, pixel
+ * The event loop (Alg. 2, Alg. 1 or Eq. 3 by `method`) over n events in push
+ * order.  S and T (row-major, pixel
  * y*W + x) are updated in place.  Returns the number of events applied;
  * *dropped is increased by the number of out-of-range events.
  */
 int64_t oracle_integrate(const oracle_event *ev, int64_t n, int W, int H,
                          double C, double k_per_s, double b, double s_min,
-                         double s_max, double *S, int64_t *T, int64_t *dropped)
+                         double s_max, int method, double *S, int64_t *T,
+                         int64_t *dropped)
 {
     int64_t applied = 0;
     for (int64_t i = 0; i < n; ++i) {
@@ -96,7 +135,8 @@ int64_t oracle_integrate(const oracle_event *ev, int64_t n, int W, int H,
             continue;
         }
         int64_t pix = (int64_t)e->y * W + e->x;
-        oracle_step(S, T, pix, e->p, e->t, C, k_per_s, b, s_min, s_max);
+        oracle_step(S, T, pix, e->p, e->t, C, k_per_s, b, s_min, s_max,
+                    method);
         applied += 1;
     }
     return applied;
@@ -105,12 +145,12 @@ int64_t oracle_integrate(const oracle_event *ev, int64_t n, int W, int H,
 /* Eq. 14 for every pixel; render_decay selects the decay view (see header). */
 void oracle_render(const double *S, const int64_t *T, int64_t P, double k_per_s,
                    double b, double s_min, double s_max, int render_decay,
-                   int64_t t_frame, uint8_t *B)
+                   int method, int64_t t_frame, uint8_t *B)
 {
     for (int64_t i = 0; i < P; ++i) {
         double v = S[i];
         if (render_decay)
-            v = v * oracle_decay(t_frame - T[i], k_per_s, b);
+            v = v * method_decay(method, t_frame - T[i], k_per_s, b);
         double q = 255.0 * (v - s_min) / (s_max - s_min);
         double r = rint(q);
         if (r < 0.0) r = 0.0;
@@ -129,9 +169,9 @@ void oracle_render(const double *S, const int64_t *T, int64_t P, double k_per_s,
  */
 int64_t oracle_replay(const oracle_event *ev, int64_t n, int W, int H,
                       double C, double k_per_s, double b, double s_min,
-                      double s_max, int render_decay, const int64_t *t_frames,
-                      int64_t M, double *S, int64_t *T, uint8_t *B,
-                      int64_t *dropped)
+                      double s_max, int render_decay, int method,
+                      const int64_t *t_frames, int64_t M, double *S, int64_t *T,
+                      uint8_t *B, int64_t *dropped)
 {
     int64_t P = (int64_t)W * H;
     int64_t i = 0;
@@ -139,10 +179,10 @@ int64_t oracle_replay(const oracle_event *ev, int64_t n, int W, int H,
         int64_t j = i;
         while (j < n && ev[j].t <= t_frames[w])
             ++j;
-        oracle_integrate(ev + i, j - i, W, H, C, k_per_s, b, s_min, s_max, S,
-                         T, dropped);
+        oracle_integrate(ev + i, j - i, W, H, C, k_per_s, b, s_min, s_max,
+                         method, S, T, dropped);
         i = j;
-        oracle_render(S, T, P, k_per_s, b, s_min, s_max, render_decay,
+        oracle_render(S, T, P, k_per_s, b, s_min, s_max, render_decay, method,
                       t_frames[w], B + w * P);
     }
     return i;

@@ -24,7 +24,8 @@ def oracle_params(p) -> oracle.OracleParams:
     return oracle.OracleParams(C=p["C"], k_per_s=p["k_per_s"], b=p["b"],
                                s_min=p["s_min"], s_max=p["s_max"],
                                t_origin_us=p.get("t_origin_us", 0),
-                               render_decay=p.get("render_decay", 0))
+                               render_decay=p.get("render_decay", 0),
+                               method=p.get("method", 0))
 
 
 def state_error(S_gpu, S_ref, C):

@@ -379,3 +379,119 @@ def test_bruteforce_clamped_affine_fold(b, bounds):
             assert np.allclose(val, got, rtol=1e-12, atol=1e-12)
             checked += 1
     assert checked == 9  # 1 + 1 + 2 + 5 bracketings for pixel sequences of 1..4 events
+
+
+# ------------------------------------------- Alg. 1 and Eq. 3 as methods
+def eq3_direct(ev_pix, t, k, C):
+    """Eq. 3 with d(t) = exp(-k t), summed term by term at time t (events t_i <= t)."""
+    sel = ev_pix[ev_pix["t"] <= t]
+    s = np.where(sel["p"] > 0, 1.0, -1.0)
+    return C * float(np.sum(s * np.exp(-(k * 1e-6) * (t - sel["t"]).astype(np.float64))))
+
+
+@pytest.mark.parametrize("b", [0.5, 2.0])
+def test_alg1_is_the_clamp_free_loop(b):
+    # Alg. 1 has no clamp: with bounds that bind for Alg. 2 the Alg. 1 state
+    # still follows the corrected Eq. 5 product form, and Alg. 2 differs
+    rng = np.random.default_rng(31)
+    W, H, k, C = 5, 4, 5.0, 0.3
+    ev = random_stream(rng, W, H, 4000, 300_000, pol_bias=0.8)
+    p1 = OracleParams(C=C, k_per_s=k, b=b, s_min=-0.3, s_max=0.3, method=1)
+    p2 = OracleParams(C=C, k_per_s=k, b=b, s_min=-0.3, s_max=0.3, method=0)
+    a1, a2 = OracleState(W, H, p1), OracleState(W, H, p2)
+    a1.integrate(ev)
+    a2.integrate(ev)
+    pix = ev["y"].astype(np.int64) * W + ev["x"]
+    for q in range(W * H):
+        sel = ev[pix == q]
+        t = np.concatenate([[0], sel["t"]])
+        suffix = np.cumprod(d_np(np.diff(t), k, b)[::-1])[::-1]
+        expect = C * np.sum(np.where(sel["p"] > 0, 1.0, -1.0) * suffix)
+        assert a1.S[q] == pytest.approx(expect, rel=1e-11, abs=1e-15)
+    assert np.max(np.abs(a1.S)) > 0.6          # the bounds would have bound
+    assert np.all((a2.S >= -0.3) & (a2.S <= 0.3))
+    assert np.array_equal(a1.T, a2.T)
+
+
+@pytest.mark.parametrize("method", [1, 2])
+def test_k_zero_is_eq2_for_unclamped_methods(method):
+    # Alg. 1 and Eq. 3 with k = 0 are Eq. 2: S = C (n_plus - n_minus), even
+    # with narrow bounds (neither method clamps)
+    rng = np.random.default_rng(32 + method)
+    W, H = 7, 6
+    ev = random_stream(rng, W, H, 5000, 10**6, pol_bias=0.7)
+    p = OracleParams(C=0.25, k_per_s=0.0, b=2.0, s_min=-0.5, s_max=0.5, method=method)
+    st = OracleState(W, H, p)
+    st.integrate(ev)
+    pix = ev["y"].astype(np.int64) * W + ev["x"]
+    net = np.bincount(pix, weights=np.where(ev["p"] > 0, 1, -1), minlength=W * H)
+    assert np.array_equal(st.S, 0.25 * net)
+    assert np.max(np.abs(st.S)) > 0.5
+
+
+@pytest.mark.parametrize("k", [1.0, 10.0, 300.0])
+def test_eq3_exp_matches_the_direct_sum(k):
+    # the regrouped recurrence equals Eq. 3's sum over every past event, at
+    # the last event (the state) and at each frame time (the decay view)
+    rng = np.random.default_rng(int(k) + 40)
+    W, H, C = 6, 5, 0.2
+    ev = random_stream(rng, W, H, 3000, 500_000)
+    tf = np.array([120_000, 250_001, 400_000, 500_000], dtype=np.int64)
+    lo, hi = -1.5, 2.0
+    p = OracleParams(C=C, k_per_s=k, b=7.0, s_min=lo, s_max=hi, render_decay=1, method=2)
+    st = OracleState(W, H, p)
+    frames, used = st.replay(ev, tf)
+    assert used == len(ev)
+    pix = ev["y"].astype(np.int64) * W + ev["x"]
+    for q in range(W * H):
+        ev_q = ev[pix == q]
+        if len(ev_q):
+            assert st.S[q] == pytest.approx(eq3_direct(ev_q, ev_q["t"][-1], k, C),
+                                             rel=1e-11, abs=1e-15)
+        for w, t in enumerate(tf):
+            x = 255.0 * (eq3_direct(ev_q, t, k, C) - lo) / (hi - lo)
+            if abs(x - np.floor(x) - 0.5) > 1e-6:     # away from a rounding tie
+                assert frames[w].ravel()[q] == int(np.clip(np.rint(x), 0, 255))
+
+
+def test_eq3_exp_decay_is_exp():
+    for dt, k in ((0, 10.0), (1, 10.0), (100_000, 10.0), (7, 1e4), (10**9, 1e-3)):
+        assert oracle.decay_exp(dt, k) == pytest.approx(np.exp(-k * 1e-6 * dt), rel=1e-15)
+    assert oracle.decay_exp(0, 123.0) == 1.0
+
+
+def first_event_residual(method, gaps_us, k, b):
+    """What is left at the last event of the first event's contribution.
+
+    One pixel with events at t_0 = 0 and at the cumulative gaps after it;
+    the state is linear in the polarities when nothing clamps, so half the
+    difference between the runs with p_0 = +1 and p_0 = -1, over C, is the
+    first event's residual."""
+    t = np.concatenate([[0], np.cumsum(gaps_us)])
+    out = []
+    for p0 in (1, -1):
+        ev = make_events([(int(ti), 0, 0, p0 if i == 0 else (1 if i % 2 else -1))
+                          for i, ti in enumerate(t)])
+        st = OracleState(1, 1, OracleParams(C=0.5, k_per_s=k, b=b, s_min=-BIG,
+                                            s_max=BIG, method=method))
+        st.integrate(ev)
+        out.append(st.S[0])
+    return (out[0] - out[1]) / (2 * 0.5)
+
+
+@pytest.mark.parametrize("n", [2, 3, 8, 40])
+@pytest.mark.parametrize("b", [0.7, 2.0])
+def test_eq6_adaptivity_ab(n, b):
+    # Eq. 6: n events spaced t apart leave d(t)^n of the first event's term
+    # under ESI's decay (Alg. 1), more than the d(n t) a single gap leaves.
+    # Eq. 3 with exp decay has no such rate dependence: exp(-k n t) either way.
+    k, span = 10.0, 60_000                     # n t = 0.06 s < 1 / k
+    dense = first_event_residual(1, [span // n] * n, k, b)
+    sparse = first_event_residual(1, [span], k, b)
+    assert dense == pytest.approx(d_np(span // n, k, b) ** n, rel=1e-12)
+    assert sparse == pytest.approx(d_np(span, k, b), rel=1e-12)
+    assert dense > sparse
+    e_dense = first_event_residual(2, [span // n] * n, k, b)
+    e_sparse = first_event_residual(2, [span], k, b)
+    assert e_dense == pytest.approx(np.exp(-k * 1e-6 * span), rel=1e-12)
+    assert e_sparse == pytest.approx(np.exp(-k * 1e-6 * span), rel=1e-12)

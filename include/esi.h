@@ -63,12 +63,24 @@ typedef struct {
 
 /*
  * Method parameters.  C: contrast step per event (Alg. 2), > 0.  k_per_s,
- * b: decay of Eq. 4, k >= 0 (k = 0 gives the plain integration of Eq. 2),
- * b > 0.  s_min < s_max: clamp bounds of Eq. 13, also the ends of the
- * linear map of Eq. 14; both finite.  t_origin_us: initial T of every pixel
- * (Alg. 2 uses 0).  render_decay: 0 maps S as stored (Alg. 2); 1 maps the
- * decay view S d(t_frame - T), which is not written back.
+ * b: decay of Eq. 4, 0 <= k <= 1e12 (k = 0 gives the plain integration of
+ * Eq. 2), b > 0.  s_min < s_max: clamp bounds of Eq. 13, also the ends of
+ * the linear map of Eq. 14; both finite.  t_origin_us: initial T of every
+ * pixel (Alg. 2 uses 0).  render_decay: 0 maps S as stored (Alg. 2); 1 maps
+ * the decay view S d(t_frame - T), which is not written back.
+ * method: which per-event update runs (Sec. III-B, III-C):
+ *   ESI_METHOD_ALG2     Alg. 2: S += p C; S *= d(t - T); T = t; clamp to
+ *                       [s_min, s_max] (Eq. 13).  The default (0).
+ *   ESI_METHOD_ALG1     Alg. 1: the same without the clamp.
+ *   ESI_METHOD_EQ3_EXP  Eq. 3 with d(t) = exp(-k t): S = S d(t - T) + p C;
+ *                       T = t, no clamp.  S is Eq. 3's sum
+ *                       C sum_{t_i <= T} p_i exp(-k (T - t_i)); b is unused.
+ * Without a clamp the state is unbounded; the map of Eq. 14 saturates every
+ * method's frame to [0, 255].
  */
+#define ESI_METHOD_ALG2 0
+#define ESI_METHOD_ALG1 1
+#define ESI_METHOD_EQ3_EXP 2
 typedef struct {
     double C;
     double k_per_s;
@@ -77,7 +89,7 @@ typedef struct {
     double s_max;
     int64_t t_origin_us;
     int32_t render_decay;
-    int32_t _reserved;
+    int32_t method;       /* ESI_METHOD_* */
 } esi_params;
 
 /* Counters of one handle (or one server stream). */

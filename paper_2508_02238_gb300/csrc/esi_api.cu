@@ -36,13 +36,23 @@ long long decay_cutoff(double k_per_s)
     return c;
 }
 
+// Smallest dt with k dt >= 110 (exp(-110) is below FP32's smallest
+// subnormal): Eq. 3's exponential decay is 0 from there on.
+long long exp_cutoff(double k_per_s)
+{
+    if (!(k_per_s > 0.0)) return LLONG_MAX;
+    const double x = std::ceil(110.0 / (k_per_s * 1e-6));
+    return x < 9.0e18 ? (long long)x : LLONG_MAX;
+}
+
 int validate_params(int W, int H, const esi_params *p)
 {
     if (!p) return ESI_EINVAL;
     if (W < 1 || H < 1 || W > 65535 || H > 65535) return ESI_EINVAL;
     if (!std::isfinite(p->C) || !(p->C > 0.0)) return ESI_EINVAL;
-    if (!std::isfinite(p->k_per_s) || p->k_per_s < 0.0) return ESI_EINVAL;
-    if (!std::isfinite(p->b) || !(p->b > 0.0)) return ESI_EINVAL;
+    if (!std::isfinite(p->k_per_s) || p->k_per_s < 0.0 || p->k_per_s > 1e12) return ESI_EINVAL;
+    if (p->method < ESI_METHOD_ALG2 || p->method > ESI_METHOD_EQ3_EXP) return ESI_EINVAL;
+    if (p->method != ESI_METHOD_EQ3_EXP && (!std::isfinite(p->b) || !(p->b > 0.0))) return ESI_EINVAL;
     if (!std::isfinite(p->s_min) || !std::isfinite(p->s_max)) return ESI_EINVAL;
     if (!((float)p->s_min < (float)p->s_max)) return ESI_EINVAL;
     if (!std::isfinite(p->s_max - p->s_min)) return ESI_EINVAL;
@@ -58,13 +68,19 @@ void prepare_params(const esi_params &p, DecayParams *dp, MapParams *mp)
     dp->b = (float)p.b;
     dp->cutoff = decay_cutoff(p.k_per_s);
     if (p.k_per_s == 0.0) dp->b_mode = 4;
+    else if (p.method == ESI_METHOD_EQ3_EXP) {
+        dp->b_mode = kBModeExp;
+        dp->b = 1.0f;
+        dp->cutoff = exp_cutoff(p.k_per_s);
+    }
     else if (p.b == 1.0) dp->b_mode = 1;
     else if (p.b == 2.0) dp->b_mode = 2;
     else if (p.b == 3.0) dp->b_mode = 3;
     else dp->b_mode = 0;
     mp->C = (float)p.C;
-    mp->s_min = (float)p.s_min;
-    mp->s_max = (float)p.s_max;
+    // only Alg. 2 clamps the state; the map of Eq. 14 saturates for all
+    mp->s_min = p.method == ESI_METHOD_ALG2 ? (float)p.s_min : -INFINITY;
+    mp->s_max = p.method == ESI_METHOD_ALG2 ? (float)p.s_max : INFINITY;
     const double sc = 255.0 / (p.s_max - p.s_min);
     mp->scale = (float)sc;
     mp->offs = (float)(-p.s_min * sc);

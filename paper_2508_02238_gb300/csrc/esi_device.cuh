@@ -201,11 +201,32 @@ __device__ __forceinline__ float one_minus_kdt(long long dt, const DecayParams &
     return fmaxf(u - corr, 0.0f);
 }
 
-// Eq. 4 for the state update (accurate powf for non-integer b).
+// exp(-k dt) for Eq. 3 (dt < cutoff, so k dt stays below about 110): with
+// dt = dh + dl and k_hi dh = p + e split exactly as above, the small rest
+// corr = k dt - p enters as the factor 1 - corr, so d keeps the relative
+// accuracy of expf at its FP32 argument.
+__device__ __forceinline__ float exp_kdt(long long dt, const DecayParams &dp)
+{
+    float dh, dl = 0.0f;
+    if (dt < (1ll << 24)) {
+        dh = __int2float_rn((int)dt);
+    } else {
+        dh = __ll2float_rn(dt);
+        dl = __ll2float_rn(dt - __float2ll_rn(dh));
+    }
+    const float p = dp.k_hi * dh;
+    const float e = fmaf(dp.k_hi, dh, -p);
+    const float corr = e + fmaf(dp.k_hi, dl, dp.k_lo * dh);
+    return expf(-p) * (1.0f - corr);
+}
+
+// Eq. 4 for the state update (accurate powf for non-integer b), or the
+// exponential decay of Eq. 3.
 __device__ __forceinline__ float decay_state(long long dt, const DecayParams &dp)
 {
     if (dt >= dp.cutoff) return 0.0f;
     if (dp.b_mode == 4) return 1.0f;
+    if (dp.b_mode == kBModeExp) return exp_kdt(dt, dp);
     float u = one_minus_kdt(dt, dp);
     switch (dp.b_mode) {
     case 1: return u;
@@ -234,10 +255,12 @@ __device__ __forceinline__ float decay_state_k(long long dt, const DecayParams &
 // Eq. 4 for the render-time view from an FP32 time difference (exact below
 // 2^24 us).  1 - k dt <= 0 gives d = 0; the decision may differ from the FP64
 // one only where d is within rounding of 0, and only the 8-bit code uses it.
+// Eq. 3's exponential view is exp(-k dt).
 template <int DK>
 __device__ __forceinline__ float decay_view_k(float dt, const DecayParams &dp)
 {
     if (DK == kDecayNone) return 1.0f;
+    if (DK == kDecayGeneral && dp.b_mode == kBModeExp) return expf(-dp.k_hi * dt);
     const float u = fmaxf(fmaf(-dp.k_hi, dt, 1.0f), 0.0f);
     if (DK == kDecaySquare) return u * u;
     switch (dp.b_mode) {

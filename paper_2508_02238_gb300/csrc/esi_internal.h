@@ -17,19 +17,23 @@ constexpr int kMaxSmemPerBlock = 227 * 1024;
 //   cutoff is the smallest integer dt with 1 - k dt <= 0 evaluated in double
 //   (so the device takes the d = 0 decision in the same precision as the
 //   definition); INT64_MAX when k = 0.
+// b_mode of Eq. 3 read with d(t) = exp(-k t): S <- S d(dt) + p C.
+constexpr int kBModeExp = 5;
+
 struct DecayParams {
     float k_hi;
     float k_lo;
     float b;
-    int b_mode;         // 0: powf; 1, 2, 3: integer b; 4: k == 0 (d = 1)
-    long long cutoff;
+    int b_mode;         // 0: powf; 1, 2, 3: integer b; 4: k == 0 (d = 1);
+                        // 5: exp(-k t) with Eq. 3's order (kBModeExp)
+    long long cutoff;   // d = 0 for dt >= cutoff
 };
 
 // Clamp of Eq. 13 and linear map of Eq. 14: B = rint(v * scale + offs).
 struct MapParams {
     float C;
-    float s_min;
-    float s_max;
+    float s_min;        // per-event clamp of Eq. 13 (-inf / +inf for the
+    float s_max;        // methods without one: Alg. 1, Eq. 3)
     float scale;        // 255 / (s_max - s_min)
     float offs;         // -s_min * scale
     int render_decay;

@@ -142,7 +142,9 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
 
 
     // Alg. 2 for a group of due records (one per valid lane, time order):
-    // S += p C; dt = t - T; S *= d(dt); T = t; clamp (Eq. 13).  A record's dt
+    // S += p C; dt = t - T; S *= d(dt); T = t; clamp (Eq. 13).  Alg. 1 and
+    // Eq. 3 run the same loop with infinite clamp bounds, Eq. 3 adding p C
+    // after the decay.  A record's dt
     // needs only times (the previous record of its pixel in the group, or T),
     // so every decay of the group is evaluated at once; only
     // S = clamp((S + p C) d) runs in rank order per pixel, S passing from
@@ -171,10 +173,17 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
         const long long t_prev = first ? o_mem : (long long)t_prev_rec;
         const float d = valid ? decay_state_k<DK>((long long)toff - t_prev, dp) : 0.0f;
         const float c = ((r >> 32) & 1u) ? mp.C : -mp.C;
+        // Alg. 1 and 2 add p C before the decay; Eq. 3 (general kind only)
+        // after it: S d + p C
+        const bool add_after = DK == kDecayGeneral && dp.b_mode == kBModeExp;
+        const float c_pre = add_after ? 0.0f : c, c_post = add_after ? c : 0.0f;
         const unsigned maxr = __reduce_max_sync(kFull, valid ? rank : 0u);
         float s_out = 0.0f;
         for (unsigned k = 0;; ++k) {
-            if (valid && rank == k) s_out = fminf(fmaxf((s_in + c) * d, mp.s_min), mp.s_max);
+            if (valid && rank == k) {
+                const float v = DK == kDecayGeneral ? fmaf(s_in + c_pre, d, c_post) : (s_in + c) * d;
+                s_out = fminf(fmaxf(v, mp.s_min), mp.s_max);
+            }
             if (k == maxr) break;
             const float got = __shfl_sync(kFull, s_out, prev);
             if (valid && rank == k + 1) s_in = got;

@@ -23,12 +23,15 @@ ESI_ECUDA = -6
 ESI_ETIMEOUT = -7
 ESI_ESTATE = -8
 
+# esi_params.method
+ESI_METHOD_ALG2, ESI_METHOD_ALG1, ESI_METHOD_EQ3_EXP = 0, 1, 2
+
 
 class esi_params(ctypes.Structure):
     _fields_ = [("C", ctypes.c_double), ("k_per_s", ctypes.c_double),
                 ("b", ctypes.c_double), ("s_min", ctypes.c_double),
                 ("s_max", ctypes.c_double), ("t_origin_us", ctypes.c_int64),
-                ("render_decay", ctypes.c_int32), ("_reserved", ctypes.c_int32)]
+                ("render_decay", ctypes.c_int32), ("method", ctypes.c_int32)]
 
 
 class esi_stats(ctypes.Structure):
@@ -365,8 +368,9 @@ def check(rc: int, what: str = "esi call") -> None:
 
 
 def make_params(C: float, k_per_s: float, b: float, s_min: float, s_max: float,
-                t_origin_us: int = 0, render_decay: int = 0) -> esi_params:
+                t_origin_us: int = 0, render_decay: int = 0,
+                method: int = 0) -> esi_params:
     p = esi_params()
     p.C, p.k_per_s, p.b, p.s_min, p.s_max = C, k_per_s, b, s_min, s_max
-    p.t_origin_us, p.render_decay = int(t_origin_us), int(render_decay)
+    p.t_origin_us, p.render_decay, p.method = int(t_origin_us), int(render_decay), int(method)
     return p

@@ -65,7 +65,8 @@ class GpuStream:
         self.esi, self.torch = esi, torch
         self.W, self.H = W, H
         params = esi.make_params(p["C"], p["k_per_s"], p["b"], p["s_min"], p["s_max"],
-                                 p.get("t_origin_us", 0), p.get("render_decay", 0))
+                                 p.get("t_origin_us", 0), p.get("render_decay", 0),
+                                 p.get("method", 0))
         rc, self.h = esi.esi_create(W, H, params, stream or 0)
         esi.check(rc, "esi_create")
         if tuning:

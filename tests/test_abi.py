@@ -52,6 +52,8 @@ GOOD = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0)
     (10, 10, {"k_per_s": -1.0}), (10, 10, {"k_per_s": float("inf")}),
     (10, 10, {"b": 0.0}), (10, 10, {"s_min": 1.0, "s_max": 1.0}),
     (10, 10, {"s_min": 2.0, "s_max": 1.0}), (10, 10, {"s_max": float("inf")}),
+    (10, 10, {"k_per_s": 2e12}), (10, 10, {"method": 3}), (10, 10, {"method": -1}),
+    (10, 10, {"b": 0.0, "method": 1}), (10, 10, {"s_min": 1.0, "s_max": 1.0, "method": 2}),
 ])
 def test_create_rejects_bad_arguments_before_touching_cuda(W, H, over):
     kw = dict(GOOD)

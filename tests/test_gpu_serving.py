@@ -38,6 +38,11 @@ STREAMS = [
                     t_origin_us=3000), "random"),
     (130, 70, dict(C=0.3, k_per_s=0.0, b=2.0, s_min=-2.0, s_max=2.0, render_decay=1,
                    t_origin_us=7000), "random"),
+    # Alg. 1 (no clamp) and Eq. 3 with exponential decay
+    (96, 64, dict(C=0.2, k_per_s=30.0, b=2.0, s_min=-0.4, s_max=0.4, render_decay=1,
+                  method=1), "random"),
+    (120, 80, dict(C=0.2, k_per_s=50.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1,
+                   method=2, t_origin_us=2000), "random"),
 ]
 
 

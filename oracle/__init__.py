@@ -14,6 +14,7 @@ multiply-add); this module only marshals numpy arrays.  It follows:
 * ``method`` 1 -- Alg. 1: the same loop without the clamp (Eq. 2 when k = 0).
 * ``method`` 2 -- Eq. 3 with d(t) = exp(-k t), no clamp, kept as the exact
   regrouping S <- S exp(-k (t - T)) + p C; T <- t of its sum.
+* Fig. 4 -- the noise-accumulation map ln(1 + |S|); per-pixel event counts.
 
 Pinned by ``tests/test_oracle_pins.py`` against closed forms the paper fixes
 (Eq. 2, the corrected Eq. 5, Eq. 6), hand-worked cases, invariants and a
@@ -73,6 +74,10 @@ def _load():
         lib.oracle_replay.argtypes = [P, i64, i32, i32, d, d, d, d, d, i32, i32,
                                       P, i64, P, P, P, P]
         lib.oracle_replay.restype = i64
+        lib.oracle_noise_map.argtypes = [P, i64, P]
+        lib.oracle_noise_map.restype = None
+        lib.oracle_count_events.argtypes = [P, i64, i32, i32, P]
+        lib.oracle_count_events.restype = None
         _lib = lib
         return lib
 
@@ -151,3 +156,19 @@ class OracleState:
             p.s_max, int(p.render_decay), int(p.method), _ptr(tf), M, _ptr(self.S),
             _ptr(self.T), _ptr(B), _ptr(self.dropped))
         return B, int(used)
+
+
+def noise_map(S: np.ndarray) -> np.ndarray:
+    """Fig. 4's map ln(1 + |S|) of a state (float64, same shape)."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    N = np.empty_like(S)
+    _load().oracle_noise_map(_ptr(S), S.size, _ptr(N))
+    return N
+
+
+def count_events(events: np.ndarray, W: int, H: int) -> np.ndarray:
+    """Events per pixel (uint32, W * H row-major); out-of-range events skipped."""
+    ev = np.ascontiguousarray(events, dtype=EVENT_DTYPE)
+    counts = np.empty(int(W) * int(H), dtype=np.uint32)
+    _load().oracle_count_events(_ptr(ev), len(ev), int(W), int(H), _ptr(counts))
+    return counts

@@ -33,6 +33,9 @@
  * For every method the render maps with Eq. 14 and saturates to [0, 255];
  * the decay view uses the method's own d.
  *
+ * Diagnostics (Sec. III-B, Fig. 4): the noise-accumulation map ln(1 + |S|)
+ * and per-pixel event counts.
+ *
  * Other readings: polarity p > 0 counts +1, anything else -1 (Sec. III-A gives
  * p in {+1, -1}); events with x >= W or y >= H are dropped and counted, never
  * applied; time is int64 microseconds and k is given per second, so the
@@ -186,4 +189,33 @@ int64_t oracle_replay(const oracle_event *ev, int64_t n, int W, int H,
                       t_frames[w], B + w * P);
     }
     return i;
+}
+
+/*
+ * The noise-accumulation map of Fig. 4 (Sec. III-B): for every pixel the
+ * absolute value of S, plus one, through the natural logarithm:
+ * N = ln(1 + |S|).  Sec. III-B draws it for the plain integration of Eq. 2
+ * over 2 s; any state may be passed.
+ */
+void oracle_noise_map(const double *S, int64_t P, double *N)
+{
+    for (int64_t i = 0; i < P; ++i)
+        N[i] = log(1.0 + fabs(S[i]));
+}
+
+/*
+ * Per-pixel event counts (the event-trigger rate of Sec. III-B times the
+ * window): counts[y * W + x] = number of the n events at (x, y); events with
+ * x >= W or y >= H are not counted.  counts is overwritten.
+ */
+void oracle_count_events(const oracle_event *ev, int64_t n, int W, int H,
+                         uint32_t *counts)
+{
+    for (int64_t i = 0; i < (int64_t)W * H; ++i)
+        counts[i] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if ((int)ev[i].x >= W || (int)ev[i].y >= H)
+            continue;
+        counts[(int64_t)ev[i].y * W + ev[i].x] += 1;
+    }
 }

@@ -495,3 +495,61 @@ def test_eq6_adaptivity_ab(n, b):
     e_sparse = first_event_residual(2, [span], k, b)
     assert e_dense == pytest.approx(np.exp(-k * 1e-6 * span), rel=1e-12)
     assert e_sparse == pytest.approx(np.exp(-k * 1e-6 * span), rel=1e-12)
+
+
+# -------------------------------------------------- Fig. 4 diagnostics
+def fig4_levels():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "fig4_noise_levels.txt")
+    rows = []
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            thr, ratio, value = line.split()
+            rows.append((float(thr), float(ratio), float(value)))
+    return rows
+
+
+@pytest.mark.parametrize("thr,ratio,value", fig4_levels())
+def test_fig4_printed_noise_levels(thr, ratio, value):
+    # the events that change the intensity by `ratio` at this threshold,
+    # accumulated by Eq. 2 in event units (C = 1), map to the printed value
+    n = int(round(np.log(ratio) / np.log(1.0 + thr)))
+    for sign in (1, -1):
+        st = OracleState(3, 2, OracleParams(C=1.0, k_per_s=0.0, b=1.0, s_min=-1.0,
+                                            s_max=1.0, method=1))
+        st.integrate(make_events([(10 * i, 2, 1, sign) for i in range(n)]))
+        N = oracle.noise_map(st.S)
+        assert round(float(N[1 * 3 + 2]), 1) == value
+        assert np.all(N[np.arange(6) != 5] == 0.0)
+
+
+def test_noise_map_of_eq2_accumulation():
+    # ln(1 + C |n_plus - n_minus|) per pixel; zero where no net events, the
+    # same for negated polarities
+    rng = np.random.default_rng(50)
+    W, H, C = 11, 9, 0.15
+    ev = random_stream(rng, W, H, 6000, 2_000_000, pol_bias=0.6)
+    p = OracleParams(C=C, k_per_s=0.0, b=1.0, s_min=-1.0, s_max=1.0, method=1)
+    st = OracleState(W, H, p)
+    st.integrate(ev)
+    pix = ev["y"].astype(np.int64) * W + ev["x"]
+    net = np.bincount(pix, weights=np.where(ev["p"] > 0, 1, -1), minlength=W * H)
+    np.testing.assert_allclose(oracle.noise_map(st.S), np.log1p(C * np.abs(net)),
+                               rtol=1e-13, atol=1e-15)
+    neg = ev.copy()
+    neg["p"] = -neg["p"]
+    st2 = OracleState(W, H, p)
+    st2.integrate(neg)
+    assert np.array_equal(oracle.noise_map(st2.S), oracle.noise_map(st.S))
+
+
+def test_count_events_is_a_histogram():
+    rng = np.random.default_rng(51)
+    W, H = 13, 7
+    ev = random_stream(rng, W + 3, H + 2, 9000, 10**6)     # some out of range
+    inside = (ev["x"] < W) & (ev["y"] < H)
+    pix = ev["y"][inside].astype(np.int64) * W + ev["x"][inside]
+    expect = np.bincount(pix, minlength=W * H)
+    assert np.array_equal(oracle.count_events(ev, W, H), expect)
+    assert np.array_equal(oracle.count_events(ev[:0], W, H), np.zeros(W * H))

@@ -368,6 +368,7 @@ def bench_esi(args):
         line["serving"] = serving_leg(esi)
         line["serving_mixed"] = mixed_serving_leg(esi)
         line["other_configs"] = other_configs_leg(esi, torch)
+        line["diagnostics"] = diagnostics_leg(esi, torch)
     elif not args.no_extras:
         line["e2e"] = None
     esi.esi_destroy(h)
@@ -586,6 +587,56 @@ def other_configs_leg(esi, torch):
                          "frames_per_s": n_w / (ms / 1e3),
                          "step_hbm_frac": step_bytes / (ms / 1e3) / 1e9 / peak}
         out[label] = res
+    return out
+
+
+def diagnostics_leg(esi, torch, reps=5):
+    """Fig. 4 diagnostics: per-pixel event counts of config 2's 1 s stream
+    (events and counts on the device) and the noise map ln(1 + |S|) of a
+    4000x3000 state.  Each launch is timed by the library's CUDA events on
+    the handle's stream, with a 256 MB write before it to flush L2."""
+    import synth
+    peak, _ = load_peaks()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+
+    def timed(h, st, call, kind):
+        esi.check(call(), kind)                      # warm-up
+        esi.check(esi.esi_profile_reset(h))
+        esi.check(esi.esi_profile_enable(h, 1))
+        for _ in range(reps):
+            with torch.cuda.stream(st):
+                flush.zero_()
+            esi.check(call(), kind)
+        esi.check(esi.esi_profile_enable(h, 0))
+        rc, prof = esi.esi_profile_read(h)
+        nl, tot = prof[kind]
+        return tot / nl
+
+    sc = synth.CONFIGS[2]()
+    ev = synth.generate(sc)
+    n = len(ev)
+    st = torch.cuda.Stream()
+    rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**PARAMS), st.cuda_stream)
+    esi.check(rc, "esi_create")
+    dev_ev = torch.from_numpy(ev.view(np.uint8)).cuda()
+    counts = torch.empty(sc.W * sc.H, dtype=torch.int32, device="cuda")
+    ms = timed(h, st, lambda: esi.esi_count_events(h, dev_ev, n, 1, counts, 1), "esi_count")
+    esi.esi_destroy(h)
+    gbs = 16.0 * n / (ms / 1e3) / 1e9
+    out["event_counts"] = {"workload": f"config2: {sc.W}x{sc.H}, {n} events", "ms": ms,
+                           "events_per_s": n / (ms / 1e3), "achieved_gbs": gbs,
+                           "frac": gbs / peak, "bytes": "16 B per event read"}
+    del dev_ev, counts
+    W, H = 4000, 3000
+    rc, h = esi.esi_create(W, H, esi.make_params(**PARAMS), st.cuda_stream)
+    esi.check(rc, "esi_create")
+    nmap = torch.empty(W * H, dtype=torch.float32, device="cuda")
+    ms = timed(h, st, lambda: esi.esi_noise_map(h, nmap, 1), "esi_noise_map")
+    esi.esi_destroy(h)
+    gbs = 8.0 * W * H / (ms / 1e3) / 1e9
+    out["noise_map"] = {"workload": f"{W}x{H} state", "ms": ms, "achieved_gbs": gbs,
+                        "frac": gbs / peak, "bytes": "4 B per pixel read + 4 B written"}
     return out
 
 

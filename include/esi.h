@@ -199,6 +199,29 @@ int esi_set_state(esi_handle *h, const float *S, const int64_t *T, int on_device
 /* Wait for the handle's queued device work; returns a device-side error. */
 int esi_synchronize(esi_handle *h);
 
+/*
+ * Noise-accumulation map of Fig. 4 (Sec. III-B): out[y * W + x] =
+ * ln(1 + |S(x, y)|) of the current state, float32, W * H, row-major.  The
+ * figure draws it for the plain integration of Eq. 2 in event units
+ * (method ESI_METHOD_ALG1, k = 0, C = 1); there, with a 15 % contrast
+ * threshold, 1.8 means a doubled and 2.2 a tripled intensity.  Queued
+ * events are not part of S.  Waits for the result; reports device-side
+ * errors.
+ */
+int esi_noise_map(esi_handle *h, float *out, int out_on_device);
+
+/*
+ * Per-pixel event counts of the handle's sensor (Sec. III-B's event-trigger
+ * rate, times the window): counts[y * W + x] = the number of the n events
+ * at (x, y), uint32, W * H, overwritten.  Events with x >= W or y >= H are
+ * not counted; the events need not be in time order and are not queued.
+ * Host buffers are staged through device memory the handle keeps.  Waits
+ * for the result.  Errors: ESI_EINVAL, ESI_ERANGE (n > 2^40), ESI_ENOMEM,
+ * ESI_ECUDA.
+ */
+int esi_count_events(esi_handle *h, const esi_event *events, size_t n, int events_on_device,
+                     uint32_t *counts, int counts_on_device);
+
 /* Counters; waits for queued work so that the drop count is exact. */
 int esi_get_stats(esi_handle *h, esi_stats *out);
 

@@ -150,24 +150,6 @@ int esi::sync_all(esi_handle *h)
 }
 
 template <class T>
-static int ensure_device(esi_handle *h, T **p, size_t *cap, size_t need)
-{
-    if (need <= *cap) return ESI_OK;
-    size_t nc = std::max(need, *cap * 2);
-    if (*p) {
-        int rc = sync_all(h);
-        if (rc) return rc;
-        cudaFree(*p);
-        *p = nullptr;
-        *cap = 0;
-    }
-    cudaError_t e = cudaMalloc((void **)p, nc * sizeof(T));
-    if (e != cudaSuccess) return cuda_fail(h, e);
-    *cap = nc;
-    return ESI_OK;
-}
-
-template <class T>
 static int ensure_pinned(esi_handle *h, T **p, size_t *cap, size_t need)
 {
     if (need <= *cap) return ESI_OK;
@@ -529,6 +511,7 @@ void esi_destroy(esi_handle *h)
     if (h->ev_tdone) cudaEventDestroy(h->ev_tdone);
     cudaFree(h->dwin);
     cudaFree(h->dframes);
+    cudaFree(h->diag);
     cudaFree(h->dstatus);
     cudaFreeHost(h->hstatus);
     cudaFreeHost(h->hwin);

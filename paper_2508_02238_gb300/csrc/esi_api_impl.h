@@ -9,9 +9,12 @@
 
 namespace esi {
 
-enum KernelKind { kKindBin = 0, kKindTile = 1, kKindFill = 2, kKindTick = 3, kNumKernelKinds = 4 };
-static const char *const kKernelNames[kNumKernelKinds] = {"esi_bin", "esi_tile", "esi_fill",
-                                                          "esi_tick"};
+enum KernelKind {
+    kKindBin = 0, kKindTile = 1, kKindFill = 2, kKindTick = 3, kKindNoise = 4, kKindCount = 5,
+    kNumKernelKinds = 6
+};
+static const char *const kKernelNames[kNumKernelKinds] = {"esi_bin",   "esi_tile",      "esi_fill",
+                                                          "esi_tick",  "esi_noise_map", "esi_count"};
 
 struct ProfRec {
     int kind;
@@ -101,6 +104,9 @@ struct esi_handle {
     unsigned char *dframes = nullptr;    // frames staged for host outputs
     size_t dframes_cap = 0;
 
+    unsigned char *diag = nullptr;       // scratch of esi_noise_map / esi_count_events
+    size_t diag_cap = 0;
+
     esi::DevStatus *dstatus = nullptr;
     esi::DevStatus *hstatus = nullptr;   // pinned
 
@@ -133,6 +139,26 @@ int prof_end(esi_handle *h, int kind, cudaEvent_t start, cudaStream_t s);
 int sync_all(esi_handle *h);
 int init_state(esi_handle *h);
 int render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int out_on_device);
+
+// Grows a device buffer to at least `need` elements (contents are not kept;
+// the handle's streams are drained before the old buffer is freed).
+template <class T>
+int ensure_device(esi_handle *h, T **p, size_t *cap, size_t need)
+{
+    if (need <= *cap) return ESI_OK;
+    size_t nc = need > *cap * 2 ? need : *cap * 2;
+    if (*p) {
+        int rc = sync_all(h);
+        if (rc) return rc;
+        cudaFree(*p);
+        *p = nullptr;
+        *cap = 0;
+    }
+    cudaError_t e = cudaMalloc((void **)p, nc * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    *cap = nc;
+    return ESI_OK;
+}
 int fill_i64(esi_handle *h, long long *dst, long long n, long long value);
 cudaError_t launch_fill_i64(long long *dst, long long n, long long value, cudaStream_t s);
 // Checks events a0 + first .. a0 + first + cnt of an n-event push starting at

@@ -96,6 +96,8 @@ SIGNATURES = {
     "esi_get_state": (_i32, [_P, _P, _P, _i32]),
     "esi_set_state": (_i32, [_P, _P, _P, _i32]),
     "esi_synchronize": (_i32, [_P]),
+    "esi_noise_map": (_i32, [_P, _P, _i32]),
+    "esi_count_events": (_i32, [_P, _P, ctypes.c_size_t, _i32, _P, _i32]),
     "esi_get_stats": (_i32, [_P, ctypes.POINTER(esi_stats)]),
     "esi_set_tuning": (_i32, [_P, ctypes.POINTER(esi_tuning)]),
     "esi_get_tuning": (_i32, [_P, ctypes.POINTER(esi_tuning)]),
@@ -202,6 +204,15 @@ def esi_set_state(h, S, T, on_device: int) -> int:
 
 def esi_synchronize(h) -> int:
     return _fn("esi_synchronize")(h)
+
+
+def esi_noise_map(h, out, on_device: int) -> int:
+    return _fn("esi_noise_map")(h, _P(ptr(out) or None), int(on_device))
+
+
+def esi_count_events(h, events, n: int, events_on_device: int, counts, counts_on_device: int) -> int:
+    return _fn("esi_count_events")(h, _P(ptr(events) or None), int(n), int(events_on_device),
+                                   _P(ptr(counts) or None), int(counts_on_device))
 
 
 def esi_get_stats(h):

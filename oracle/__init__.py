@@ -15,6 +15,7 @@ multiply-add); this module only marshals numpy arrays.  It follows:
 * ``method`` 2 -- Eq. 3 with d(t) = exp(-k t), no clamp, kept as the exact
   regrouping S <- S exp(-k (t - T)) + p C; T <- t of its sum.
 * Fig. 4 -- the noise-accumulation map ln(1 + |S|); per-pixel event counts.
+* Continuous-time output -- S of each event's pixel right after the event.
 
 Pinned by ``tests/test_oracle_pins.py`` against closed forms the paper fixes
 (Eq. 2, the corrected Eq. 5, Eq. 6), hand-worked cases, invariants and a
@@ -74,6 +75,8 @@ def _load():
         lib.oracle_replay.argtypes = [P, i64, i32, i32, d, d, d, d, d, i32, i32,
                                       P, i64, P, P, P, P]
         lib.oracle_replay.restype = i64
+        lib.oracle_event_states.argtypes = [P, i64, i32, i32, d, d, d, d, d, i32, P, P, P]
+        lib.oracle_event_states.restype = None
         lib.oracle_noise_map.argtypes = [P, i64, P]
         lib.oracle_noise_map.restype = None
         lib.oracle_count_events.argtypes = [P, i64, i32, i32, P]
@@ -130,6 +133,16 @@ class OracleState:
         return int(_load().oracle_integrate(
             _ptr(ev), len(ev), self.W, self.H, p.C, p.k_per_s, p.b, p.s_min,
             p.s_max, int(p.method), _ptr(self.S), _ptr(self.T), _ptr(self.dropped)))
+
+    def event_states(self, events: np.ndarray) -> np.ndarray:
+        """Apply events in push order; S right after each (NaN if outside the sensor)."""
+        ev = np.ascontiguousarray(events, dtype=EVENT_DTYPE)
+        out = np.empty(len(ev), dtype=np.float64)
+        p = self.params
+        _load().oracle_event_states(
+            _ptr(ev), len(ev), self.W, self.H, p.C, p.k_per_s, p.b, p.s_min,
+            p.s_max, int(p.method), _ptr(self.S), _ptr(self.T), _ptr(out))
+        return out
 
     def render(self, t_frame_us: int, render_decay: int | None = None) -> np.ndarray:
         """Eq. 14 frame (uint8, H x W) at t_frame."""

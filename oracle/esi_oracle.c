@@ -34,7 +34,8 @@
  * the decay view uses the method's own d.
  *
  * Diagnostics (Sec. III-B, Fig. 4): the noise-accumulation map ln(1 + |S|)
- * and per-pixel event counts.
+ * and per-pixel event counts.  Continuous-time output: S right after every
+ * event.
  *
  * Other readings: polarity p > 0 counts +1, anything else -1 (Sec. III-A gives
  * p in {+1, -1}); events with x >= W or y >= H are dropped and counted, never
@@ -217,5 +218,28 @@ void oracle_count_events(const oracle_event *ev, int64_t n, int W, int H,
         if ((int)ev[i].x >= W || (int)ev[i].y >= H)
             continue;
         counts[(int64_t)ev[i].y * W + ev[i].x] += 1;
+    }
+}
+
+/*
+ * Per-event states (continuous-time output): the event loop of `method` over
+ * n events in push order, as oracle_integrate, writing out[i] = S of event
+ * i's pixel right after event i is applied; NaN for an event outside the
+ * sensor (never applied).  S and T are updated in place.
+ */
+void oracle_event_states(const oracle_event *ev, int64_t n, int W, int H,
+                         double C, double k_per_s, double b, double s_min,
+                         double s_max, int method, double *S, int64_t *T,
+                         double *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const oracle_event *e = &ev[i];
+        if ((int)e->x >= W || (int)e->y >= H) {
+            out[i] = NAN;
+            continue;
+        }
+        int64_t pix = (int64_t)e->y * W + e->x;
+        oracle_step(S, T, pix, e->p, e->t, C, k_per_s, b, s_min, s_max, method);
+        out[i] = S[pix];
     }
 }

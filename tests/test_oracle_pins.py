@@ -553,3 +553,54 @@ def test_count_events_is_a_histogram():
     expect = np.bincount(pix, minlength=W * H)
     assert np.array_equal(oracle.count_events(ev, W, H), expect)
     assert np.array_equal(oracle.count_events(ev[:0], W, H), np.zeros(W * H))
+
+
+# ------------------------------------------------ continuous-time output
+@pytest.mark.parametrize("method,b", [(1, 2.0), (1, 0.7), (2, 1.0)])
+def test_event_states_are_eq5_prefixes(method, b):
+    # S right after event j of a pixel is the clamp-free closed form over
+    # that pixel's events up to j: the corrected Eq. 5 (methods 0/1) or
+    # Eq. 3's sum (method 2); the last one is the final state
+    rng = np.random.default_rng(80 + method)
+    W, H, k, C = 5, 4, 8.0, 0.3
+    ev = random_stream(rng, W + 1, H, 2500, 300_000)         # a column outside
+    p = OracleParams(C=C, k_per_s=k, b=b, s_min=-0.2, s_max=0.2, method=method)
+    st = OracleState(W, H, p)
+    vals = st.event_states(ev)
+    inside = ev["x"] < W
+    assert np.all(np.isnan(vals[~inside])) and not np.any(np.isnan(vals[inside]))
+    pix = ev["y"].astype(np.int64) * W + ev["x"]
+    for q in range(W * H):
+        sel = np.nonzero(inside & (pix == q))[0]
+        if len(sel) == 0:
+            continue
+        t = ev["t"][sel]
+        s = np.where(ev["p"][sel] > 0, 1.0, -1.0)
+        for j in range(len(sel)):
+            if method == 2:
+                expect = C * np.sum(s[:j + 1] * np.exp(-k * 1e-6 * (t[j] - t[:j + 1])))
+            else:
+                tt = np.concatenate([[0], t[:j + 1]])
+                expect = C * np.sum(s[:j + 1] * np.cumprod(d_np(np.diff(tt), k, b)[::-1])[::-1])
+            assert vals[sel[j]] == pytest.approx(expect, rel=1e-11, abs=1e-15)
+        assert vals[sel[-1]] == st.S[q]
+    ref = OracleState(W, H, p)
+    ref.integrate(ev)
+    assert np.array_equal(ref.S, st.S) and np.array_equal(ref.T, st.T)
+
+
+def test_event_states_with_clamp_stay_in_bounds_and_match_frames():
+    # Alg. 2: each value is clamped; a frame with render_decay = 0 shows, per
+    # pixel, the value after that pixel's last event up to the frame time
+    rng = np.random.default_rng(85)
+    W, H = 6, 5
+    ev = random_stream(rng, W, H, 3000, 400_000, pol_bias=0.7)
+    p = OracleParams(C=0.25, k_per_s=5.0, b=2.0, s_min=-0.5, s_max=0.75)
+    vals = OracleState(W, H, p).event_states(ev)
+    assert np.all((vals >= -0.5) & (vals <= 0.75))
+    frames, _ = OracleState(W, H, p).replay(ev, [200_000])
+    pix = ev["y"].astype(np.int64) * W + ev["x"]
+    for q in range(W * H):
+        sel = np.nonzero((pix == q) & (ev["t"] <= 200_000))[0]
+        v = vals[sel[-1]] if len(sel) else 0.0
+        assert frames[0].ravel()[q] == int(np.clip(np.rint(255 * (v + 0.5) / 1.25), 0, 255))

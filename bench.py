@@ -628,6 +628,31 @@ def diagnostics_leg(esi, torch, reps=5):
                            "events_per_s": n / (ms / 1e3), "achieved_gbs": gbs,
                            "frac": gbs / peak, "bytes": "16 B per event read"}
     del dev_ev, counts
+    # continuous-time output: S after every event of the config-1 step
+    sc1, ev1 = make_stream()
+    n1 = len(ev1)
+    rc, h = esi.esi_create(sc1.W, sc1.H, esi.make_params(**PARAMS), st.cuda_stream)
+    esi.check(rc, "esi_create")
+    vals = torch.empty(n1, dtype=torch.float32, device="cuda")
+    steps = []
+    for k in range(1 + reps):
+        esi.check(esi.esi_push_events(h, shifted(ev1, k), n1, 0), "push")
+        with torch.cuda.stream(st):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        rc, m = esi.esi_event_states(h, vals, n1, 1)
+        esi.check(rc, "event_states")
+        e1.record(st)
+        torch.cuda.synchronize()
+        if k:
+            steps.append(e0.elapsed_time(e1))
+    esi.esi_destroy(h)
+    ms = float(np.median(steps))
+    out["event_states"] = {"workload": f"config1: {sc1.W}x{sc1.H}, {n1} events per call",
+                           "ms": ms, "events_per_s": n1 / (ms / 1e3),
+                           "note": "binning + one warp per tile; S written per event (4 B)"}
+    del vals
     W, H = 4000, 3000
     rc, h = esi.esi_create(W, H, esi.make_params(**PARAMS), st.cuda_stream)
     esi.check(rc, "esi_create")

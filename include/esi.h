@@ -200,6 +200,20 @@ int esi_set_state(esi_handle *h, const float *S, const int64_t *T, int on_device
 int esi_synchronize(esi_handle *h);
 
 /*
+ * Continuous-time output (Alg. 2 per event; Alg. 1 or Eq. 3 by the method):
+ * applies every queued event to the state, as a render at the last queued
+ * time would, and writes out[i] = S of the i-th queued event's pixel (push
+ * order) right after that event is applied: float32, one value per event,
+ * NaN for an event outside the sensor.  *n_out receives the number of events
+ * (events_pending before the call; 0 leaves out untouched).  out holds cap
+ * floats (ESI_ERANGE if cap < events_pending).  No frame is rendered; later
+ * frames must not be earlier than the last applied event.  The state
+ * afterwards is bit-identical to the one such a render leaves.  Waits for
+ * the result; reports device-side errors.
+ */
+int esi_event_states(esi_handle *h, float *out, size_t cap, int out_on_device, size_t *n_out);
+
+/*
  * Noise-accumulation map of Fig. 4 (Sec. III-B): out[y * W + x] =
  * ln(1 + |S(x, y)|) of the current state, float32, W * H, row-major.  The
  * figure draws it for the plain integration of Eq. 2 in event units

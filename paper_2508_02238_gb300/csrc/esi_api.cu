@@ -512,6 +512,8 @@ void esi_destroy(esi_handle *h)
     cudaFree(h->dwin);
     cudaFree(h->dframes);
     cudaFree(h->diag);
+    cudaFree(h->rec_idx[0]);
+    cudaFree(h->rec_idx[1]);
     cudaFree(h->dstatus);
     cudaFreeHost(h->hstatus);
     cudaFreeHost(h->hwin);
@@ -828,28 +830,13 @@ int esi::init_state(esi_handle *h)
     return fill_i64(h, h->T, h->P, h->prm.t_origin_us);
 }
 
-namespace {
-struct SubBatch {
-    unsigned long long i0, i1;  // pending-relative event range
-    int w0, w1;                 // frames completed by this launch
-    long long t_base;
-};
-}  // namespace
-
-int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int out_on_device)
+int esi::plan_subbatches(esi_handle *h, unsigned long long n_split, const int64_t *tf, int m,
+                         std::vector<SubBatch> *plan_out)
 {
-    const long long t_last = tf[m - 1];
-    unsigned long long n_end = 0;
-    int rc = upper_bound_t(h, h->head, h->tail, t_last, &n_end);
-    if (rc) return rc;
-    const unsigned long long n_split = n_end - h->head;
-    const esi_tuning &tu = h->tun;
-    const int chunk = tu.chunk_events;
-    const unsigned long long maxb = (unsigned long long)tu.max_batch_events;
-
-    // plan: sub-batches of at most max_batch_events whose record times fit in
-    // 32 bits; each completes the frames that end before its successor starts
-    std::vector<SubBatch> plan;
+    const unsigned long long maxb = (unsigned long long)h->tun.max_batch_events;
+    std::vector<SubBatch> &plan = *plan_out;
+    plan.clear();
+    int rc = ESI_OK;
     {
         unsigned long long i = 0;
         int w = 0;
@@ -899,6 +886,25 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
             if (i >= n_split && w >= m) break;
         }
     }
+    return ESI_OK;
+}
+
+int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int out_on_device)
+{
+    const long long t_last = tf[m - 1];
+    unsigned long long n_end = 0;
+    int rc = upper_bound_t(h, h->head, h->tail, t_last, &n_end);
+    if (rc) return rc;
+    const unsigned long long n_split = n_end - h->head;
+    const esi_tuning &tu = h->tun;
+    const int chunk = tu.chunk_events;
+    const unsigned long long maxb = (unsigned long long)tu.max_batch_events;
+
+    // plan: sub-batches of at most max_batch_events whose record times fit in
+    // 32 bits; each completes the frames that end before its successor starts
+    std::vector<SubBatch> plan;
+    rc = plan_subbatches(h, n_split, tf, m, &plan);
+    if (rc) return rc;
     // the staging buffer may still feed the previous render's queued copy
     if (h->hwin_busy) {
         cudaError_t e0 = cudaEventSynchronize(h->hwin_ev);

@@ -11,10 +11,10 @@ namespace esi {
 
 enum KernelKind {
     kKindBin = 0, kKindTile = 1, kKindFill = 2, kKindTick = 3, kKindNoise = 4, kKindCount = 5,
-    kNumKernelKinds = 6
+    kKindEvState = 6, kNumKernelKinds = 7
 };
-static const char *const kKernelNames[kNumKernelKinds] = {"esi_bin",   "esi_tile",      "esi_fill",
-                                                          "esi_tick",  "esi_noise_map", "esi_count"};
+static const char *const kKernelNames[kNumKernelKinds] = {
+    "esi_bin", "esi_tile", "esi_fill", "esi_tick", "esi_noise_map", "esi_count", "esi_event_state"};
 
 struct ProfRec {
     int kind;
@@ -104,7 +104,9 @@ struct esi_handle {
     unsigned char *dframes = nullptr;    // frames staged for host outputs
     size_t dframes_cap = 0;
 
-    unsigned char *diag = nullptr;       // scratch of esi_noise_map / esi_count_events
+    unsigned *rec_idx[2] = {nullptr, nullptr};  // event index beside each record (esi_event_states)
+    size_t rec_idx_cap[2] = {0, 0};
+    unsigned char *diag = nullptr;       // scratch of esi_noise_map / esi_count_events / esi_event_states
     size_t diag_cap = 0;
 
     esi::DevStatus *dstatus = nullptr;
@@ -139,6 +141,20 @@ int prof_end(esi_handle *h, int kind, cudaEvent_t start, cudaStream_t s);
 int sync_all(esi_handle *h);
 int init_state(esi_handle *h);
 int render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int out_on_device);
+
+// One binning + tile launch pair of a render: pending events i0 .. i1
+// (relative to head), frames w0 .. w1 completed by it, record times offset
+// from t_base.
+struct SubBatch {
+    unsigned long long i0, i1;
+    int w0, w1;
+    long long t_base;
+};
+// Splits the first n_split pending events into sub-batches of at most
+// max_batch_events whose record times fit in 32 bits; each completes the
+// frames (of tf[0 .. m)) that end before its successor starts.  m may be 0.
+int plan_subbatches(esi_handle *h, unsigned long long n_split, const int64_t *tf, int m,
+                    std::vector<SubBatch> *plan);
 
 // Grows a device buffer to at least `need` elements (contents are not kept;
 // the handle's streams are drained before the old buffer is freed).

@@ -270,6 +270,23 @@ __device__ __forceinline__ float decay_view_k(float dt, const DecayParams &dp)
     }
 }
 
+// One event of a pixel (Alg. 2): S <- clamp((S + p C) d) with c = +-C.  The
+// general decay kind also runs Eq. 3's order, S d + p C (b_mode kBModeExp);
+// Alg. 1 and Eq. 3 come with infinite clamp bounds.
+template <int DK>
+__device__ __forceinline__ float event_step(float s, float c, float d, const DecayParams &dp,
+                                            const MapParams &mp)
+{
+    float v;
+    if (DK == kDecayGeneral) {
+        const bool after = dp.b_mode == kBModeExp;
+        v = fmaf(s + (after ? 0.0f : c), d, after ? c : 0.0f);
+    } else {
+        v = (s + c) * d;
+    }
+    return fminf(fmaxf(v, mp.s_min), mp.s_max);
+}
+
 // Round half to even and saturate to [0, 255] in one conversion.
 __device__ __forceinline__ unsigned quantize_u8(float x)
 {

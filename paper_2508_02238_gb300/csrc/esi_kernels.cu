@@ -145,10 +145,12 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
         if (k < s1) {
             const int4 e = sev[k];
             const int x = e.z & 0xffff, y = (int)((unsigned)e.z >> 16);
-            if (x < W && y < H)
+            if (x < W && y < H) {
                 tile = (y >> thl) * tiles_x + (x >> twl);
-            else
+            } else {
                 ++drop;
+                if (a.ev_out) a.ev_out[c0 + k] = __int_as_float(0x7fc00000);
+            }
         }
         const bool valid = tile >= 0;
         unsigned peers;
@@ -210,8 +212,9 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
         const long long t = ((long long)(unsigned)e.y << 32) | (unsigned)e.x;
         const unsigned pit = ((unsigned)(y & th_mask) << twl) | (unsigned)(x & ((1 << twl) - 1));
         const bool pos = (signed char)(e.w & 0xff) > 0;
-        ssort[tstart[tile] + cnt[w * ntp + tile] + loff[k]] =
-            make_record((unsigned)(t - a.t_base), pit, pos ? 1u : 0u);
+        const unsigned q = tstart[tile] + cnt[w * ntp + tile] + loff[k];
+        ssort[q] = make_record((unsigned)(t - a.t_base), pit, pos ? 1u : 0u);
+        if (a.rec_idx) a.rec_idx[c0 + q] = (unsigned)(c0 + k);
     }
     __syncthreads();
 

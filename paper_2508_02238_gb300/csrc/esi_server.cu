@@ -718,6 +718,8 @@ int esi_server_tick(esi_server *s, int64_t now_us)
         B.args.hrow = s->hrow + hrow_off;
         B.args.use_mask = s->bin_mask ? 1 : 0;
         B.args.status = s->dstatus;
+        B.args.rec_idx = nullptr;
+        B.args.ev_out = nullptr;
         B.first_chunk = n_chunks;
         for (int c = 0; c < chunks; ++c) cj[n_chunks + c] = j;
         // tile job

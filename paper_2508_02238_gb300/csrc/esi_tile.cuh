@@ -173,17 +173,10 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
         const long long t_prev = first ? o_mem : (long long)t_prev_rec;
         const float d = valid ? decay_state_k<DK>((long long)toff - t_prev, dp) : 0.0f;
         const float c = ((r >> 32) & 1u) ? mp.C : -mp.C;
-        // Alg. 1 and 2 add p C before the decay; Eq. 3 (general kind only)
-        // after it: S d + p C
-        const bool add_after = DK == kDecayGeneral && dp.b_mode == kBModeExp;
-        const float c_pre = add_after ? 0.0f : c, c_post = add_after ? c : 0.0f;
         const unsigned maxr = __reduce_max_sync(kFull, valid ? rank : 0u);
         float s_out = 0.0f;
         for (unsigned k = 0;; ++k) {
-            if (valid && rank == k) {
-                const float v = DK == kDecayGeneral ? fmaf(s_in + c_pre, d, c_post) : (s_in + c) * d;
-                s_out = fminf(fmaxf(v, mp.s_min), mp.s_max);
-            }
+            if (valid && rank == k) s_out = event_step<DK>(s_in, c, d, dp, mp);
             if (k == maxr) break;
             const float got = __shfl_sync(kFull, s_out, prev);
             if (valid && rank == k + 1) s_in = got;

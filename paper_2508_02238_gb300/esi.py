@@ -97,6 +97,7 @@ SIGNATURES = {
     "esi_set_state": (_i32, [_P, _P, _P, _i32]),
     "esi_synchronize": (_i32, [_P]),
     "esi_noise_map": (_i32, [_P, _P, _i32]),
+    "esi_event_states": (_i32, [_P, _P, ctypes.c_size_t, _i32, ctypes.POINTER(ctypes.c_size_t)]),
     "esi_count_events": (_i32, [_P, _P, ctypes.c_size_t, _i32, _P, _i32]),
     "esi_get_stats": (_i32, [_P, ctypes.POINTER(esi_stats)]),
     "esi_set_tuning": (_i32, [_P, ctypes.POINTER(esi_tuning)]),
@@ -204,6 +205,13 @@ def esi_set_state(h, S, T, on_device: int) -> int:
 
 def esi_synchronize(h) -> int:
     return _fn("esi_synchronize")(h)
+
+
+def esi_event_states(h, out, cap: int, on_device: int):
+    """Returns (rc, number of events applied)."""
+    n = ctypes.c_size_t(0)
+    rc = _fn("esi_event_states")(h, _P(ptr(out) or None), int(cap), int(on_device), ctypes.byref(n))
+    return rc, int(n.value)
 
 
 def esi_noise_map(h, out, on_device: int) -> int:

@@ -67,6 +67,9 @@ def parse_args():
     ap.add_argument("--ncu-case", action="store_true",
                     help="run the small profiling case (0.4 s of the stream, 40 frames, 3 renders) "
                          "and print no bench line; for ncu captures")
+    ap.add_argument("--diagnostics-only", action="store_true",
+                    help="run only the diagnostics leg (event counts, per-event states, noise "
+                         "map) and print its JSON; also the case for their ncu captures")
     return ap.parse_args()
 
 
@@ -797,6 +800,12 @@ def main():
     args = parse_args()
     if args.ncu_case:
         ncu_case()
+        return
+    if args.diagnostics_only:
+        import torch
+        from paper_2508_02238_gb300 import esi
+        esi.load_library(build_if_missing=True)
+        print(json.dumps({"diagnostics": diagnostics_leg(esi, torch)}), flush=True)
         return
     if args.serving_only:
         import torch  # noqa: F401  (CUDA context as in the bench)

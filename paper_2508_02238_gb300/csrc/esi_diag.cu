@@ -13,17 +13,13 @@ namespace {
 
 constexpr int kDiagThreads = 256;
 
-// Blocks for a grid-stride loop over `units`: enough to fill every SM
-// several times, no more than the work needs.
-int diag_blocks(long long units)
+// Blocks for a grid-stride loop over `units` on the handle's device: enough
+// to fill every SM several times, no more than the work needs.
+int diag_blocks(const esi_handle *h, long long units)
 {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0)
+        sms = 1;
     const long long need = (units + kDiagThreads - 1) / kDiagThreads;
     const long long cap = (long long)sms * 8;
     return (int)(need < 1 ? 1 : need < cap ? need : cap);
@@ -98,7 +94,7 @@ extern "C" int esi_noise_map(esi_handle *h, float *out, int out_on_device)
     cudaEvent_t ev = nullptr;
     int rc = prof_begin(h, &ev, h->stream);
     if (rc) return rc;
-    esi_noise_map_kernel<<<diag_blocks(vec4 ? (h->P + 3) / 4 : h->P), kDiagThreads, 0, h->stream>>>(
+    esi_noise_map_kernel<<<diag_blocks(h, vec4 ? (h->P + 3) / 4 : h->P), kDiagThreads, 0, h->stream>>>(
         h->S, h->P, dst, vec4);
     rc = cuda_fail(h, cudaGetLastError());
     if (!rc) rc = prof_end(h, kKindNoise, ev, h->stream);
@@ -131,7 +127,7 @@ extern "C" int esi_count_events(esi_handle *h, const esi_event *events, size_t n
                                               cudaMemcpyHostToDevice, h->stream));
         if (rc) return rc;
     }
-    esi_zero_u32_kernel<<<diag_blocks(h->P), kDiagThreads, 0, h->stream>>>(dcounts, h->P);
+    esi_zero_u32_kernel<<<diag_blocks(h, h->P), kDiagThreads, 0, h->stream>>>(dcounts, h->P);
     int rc = cuda_fail(h, cudaGetLastError());
     if (rc) return rc;
     h->launches += 1;
@@ -139,7 +135,7 @@ extern "C" int esi_count_events(esi_handle *h, const esi_event *events, size_t n
         cudaEvent_t ev = nullptr;
         rc = prof_begin(h, &ev, h->stream);
         if (rc) return rc;
-        esi_count_kernel<<<diag_blocks((long long)n), kDiagThreads, 0, h->stream>>>(dev, (long long)n, h->W,
+        esi_count_kernel<<<diag_blocks(h, (long long)n), kDiagThreads, 0, h->stream>>>(dev, (long long)n, h->W,
                                                                                      h->H, dcounts);
         rc = cuda_fail(h, cudaGetLastError());
         if (!rc) rc = prof_end(h, kKindCount, ev, h->stream);

@@ -654,7 +654,7 @@ def diagnostics_leg(esi, torch, reps=5):
     ms = float(np.median(steps))
     out["event_states"] = {"workload": f"config1: {sc1.W}x{sc1.H}, {n1} events per call",
                            "ms": ms, "events_per_s": n1 / (ms / 1e3),
-                           "note": "binning + one warp per tile; S written per event (4 B)"}
+                           "note": "binning + the tile kernel with per-event output; S written per event (4 B)"}
     del vals
     W, H = 4000, 3000
     rc, h = esi.esi_create(W, H, esi.make_params(**PARAMS), st.cuda_stream)

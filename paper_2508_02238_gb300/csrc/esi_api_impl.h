@@ -14,7 +14,7 @@ enum KernelKind {
     kKindEvState = 6, kNumKernelKinds = 7
 };
 static const char *const kKernelNames[kNumKernelKinds] = {
-    "esi_bin", "esi_tile", "esi_fill", "esi_tick", "esi_noise_map", "esi_count", "esi_event_state"};
+    "esi_bin", "esi_tile", "esi_fill", "esi_tick", "esi_noise_map", "esi_count", "esi_tile_ev"};
 
 struct ProfRec {
     int kind;

@@ -114,6 +114,9 @@ struct TileArgs {
     long long P;
     int batch;                    // records sorted per shared-memory batch
     DevStatus *status;
+    // per-event output (esi_event_states' instantiations only; null otherwise)
+    const unsigned *rec_idx = nullptr;  // event index (in the sub-batch) beside each record
+    float *ev_out = nullptr;            // S right after each event, at its index
 };
 
 // One stream segment of a batched binning launch: the chunks
@@ -159,12 +162,20 @@ inline int index_bits(int n)
 size_t bin_smem_bytes(int chunk, int n_tiles, bool mask);
 bool bin_mask_fits(int chunk, int n_tiles);
 size_t tile_smem_bytes(int tile_h, int batch, int n_chunks);
+// The same for the per-event-output instantiations (index arrays added).
+size_t tile_smem_bytes_ev(int batch, int n_chunks);
 size_t tile_static_smem_bytes(int tile_h, int tile_w);
 cudaError_t launch_bin(const BinArgs &a, int n_chunks, cudaStream_t s);
 cudaError_t launch_tile(const TileArgs &a, int tile_h, int tile_w, bool vec, cudaStream_t s);
+// Tile kernel that writes S after every event (a.rec_idx, a.ev_out) and
+// renders no frame (a.w_begin == a.w_end).
+cudaError_t launch_tile_ev(const TileArgs &a, int tile_h, int tile_w, cudaStream_t s);
 cudaError_t launch_tile_w128(const TileArgs &a, int tile_h, bool vec, cudaStream_t s);
 cudaError_t launch_tile_w32(const TileArgs &a, int tile_h, cudaStream_t s);
 cudaError_t launch_tile_w64(const TileArgs &a, int tile_h, bool vec, cudaStream_t s);
+cudaError_t launch_tile_ev_w128(const TileArgs &a, int tile_h, cudaStream_t s);
+cudaError_t launch_tile_ev_w64(const TileArgs &a, int tile_h, cudaStream_t s);
+cudaError_t launch_tile_ev_w32(const TileArgs &a, int tile_h, cudaStream_t s);
 cudaError_t launch_tile_tab_w128(const unsigned char *tab, int group, int grid, int tile_h, int rd,
                                  int dk, bool vec, int batch, int max_chunks, cudaStream_t s);
 cudaError_t set_tile_attributes_w128();

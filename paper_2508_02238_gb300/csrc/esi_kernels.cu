@@ -259,6 +259,12 @@ size_t tile_smem_bytes(int tile_h, int batch, int n_chunks)
 }
 
 
+size_t tile_smem_bytes_ev(int batch, int n_chunks)
+{
+    size_t a, b;
+    return tile_layout_ev(batch, n_chunks, &a, &b);
+}
+
 size_t tile_static_smem_bytes(int tile_h, int tile_w)
 {
     // pixel state (S, F, O and a peer mask per pixel), staged frames and the
@@ -304,6 +310,13 @@ cudaError_t launch_tile(const TileArgs &a, int tile_h, int tile_w, bool vec, cud
     if (tile_w == 32) return launch_tile_w32(a, tile_h, s);
     if (tile_w == 64) return launch_tile_w64(a, tile_h, vec, s);
     return launch_tile_w128(a, tile_h, vec, s);
+}
+
+cudaError_t launch_tile_ev(const TileArgs &a, int tile_h, int tile_w, cudaStream_t s)
+{
+    if (tile_w == 32) return launch_tile_ev_w32(a, tile_h, s);
+    if (tile_w == 64) return launch_tile_ev_w64(a, tile_h, s);
+    return launch_tile_ev_w128(a, tile_h, s);
 }
 
 cudaError_t launch_tile_batch_tab(const unsigned char *tab, int group, int grid, int tile_h, int rd,

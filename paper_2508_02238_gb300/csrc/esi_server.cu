@@ -745,6 +745,8 @@ int esi_server_tick(esi_server *s, int64_t now_us)
         A.P = st.P;
         A.batch = kBatch;
         A.status = s->dstatus;
+        A.rec_idx = nullptr;
+        A.ev_out = nullptr;
         for (size_t w = 0; w < fr.size(); ++w) {
             const long long d = fr[w] - t_base;
             win[n_frames + w].lim = std::min(std::max(d, -1ll), 0xffffffffll);

@@ -32,6 +32,19 @@ static __host__ __device__ inline size_t tile_layout(int batch, int n_chunks, si
     return o;
 }
 
+// Per-event output: two u32 index arrays beside A and B, after the layout.
+static __host__ __device__ inline size_t tile_layout_ev(int batch, int n_chunks, size_t *off_ia,
+                                                        size_t *off_ib)
+{
+    size_t a, b, c, d;
+    size_t o = tile_round_up((int)tile_layout(batch, n_chunks, &a, &b, &c, &d), 16);
+    *off_ia = o;
+    o += (size_t)(batch + 2) * 4;
+    *off_ib = o;
+    o += (size_t)batch * 4;
+    return o;
+}
+
 // Largest c in [0, n) with pre[c] <= g (pre[0] = 0 <= g < pre[n]).
 __device__ __forceinline__ int run_of(const unsigned *pre, int n, unsigned g)
 {
@@ -54,8 +67,10 @@ __device__ __forceinline__ int run_of(const unsigned *pre, int n, unsigned g)
 // shared memory.  RD: render_decay; DK: decay kind; VEC
 // (PPL = 4 or 2): rows start PPL-byte aligned (W % PPL == 0), so a lane's
 // pixels move as one float4 / two longlong2 / one 32-bit frame word (PPL = 4)
-// or one 16-bit frame word (PPL = 2).
-template <int TH, int PPL, int RD, int DK, bool VEC>
+// or one 16-bit frame word (PPL = 2).  EV: every record's event index is
+// carried beside it and S after each event is stored at that index
+// (esi_event_states; launched with no frames).
+template <int TH, int PPL, int RD, int DK, bool VEC, bool EV = false>
 __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
 {
     constexpr int NT = TH * 32;
@@ -82,6 +97,13 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
     unsigned *runpre = reinterpret_cast<unsigned *>(smem + off_runpre);
     unsigned *runoff = reinterpret_cast<unsigned *>(smem + off_runoff);
     unsigned short *lpos = reinterpret_cast<unsigned short *>(smem + off_lpos);
+    unsigned *IA = nullptr, *IB = nullptr;
+    if constexpr (EV) {
+        size_t off_ia, off_ib;
+        tile_layout_ev(R, n_chunks, &off_ia, &off_ib);
+        IA = reinterpret_cast<unsigned *>(smem + off_ia);
+        IB = reinterpret_cast<unsigned *>(smem + off_ib);
+    }
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int x0 = (tile % a.tiles_x) * TWP + PPL * lane;
@@ -150,7 +172,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
     // S = clamp((S + p C) d) runs in rank order per pixel, S passing from
     // lane to lane by shuffle.  Same operations in the same order as the
     // sequential loop, so the result is bit-identical to it.
-    auto apply_group = [&](unsigned long long r, bool valid) {
+    auto apply_group = [&](unsigned long long r, bool valid, unsigned ev_idx) {
         const int x = (int)((r >> 33) & (unsigned)(TWP - 1));
         const unsigned toff = (unsigned)r;
         // the pixel's state as the group starts (no lane writes it before the
@@ -180,6 +202,9 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
             if (k == maxr) break;
             const float got = __shfl_sync(kFull, s_out, prev);
             if (valid && rank == k + 1) s_in = got;
+        }
+        if constexpr (EV) {
+            if (valid) a.ev_out[ev_idx] = s_out;
         }
         // the last record of each pixel writes its state back
         if (valid && (peers >> lane) == 1u) {
@@ -211,6 +236,10 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
                 const unsigned long long *src =
                     a.rec + (size_t)c * a.chunk + runoff[c] + (rs - runpre[c]);
                 for (unsigned i = sub; i + rs < re; i += kGatherLanes) cp_async8(&A[rs - b0 + i], src + i);
+                if constexpr (EV) {
+                    const unsigned *isrc = a.rec_idx + (size_t)c * a.chunk + runoff[c] + (rs - runpre[c]);
+                    for (unsigned i = sub; i + rs < re; i += kGatherLanes) cp_async4(&IA[rs - b0 + i], isrc + i);
+                }
             }
         }
         cp_async_wait_all();
@@ -253,6 +282,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
             const unsigned long long r = A[k];
             const int row = (int)(r >> (33 + XB));
             B[rcnt[warp][row] + lpos[k]] = r;
+            if constexpr (EV) IB[rcnt[warp][row] + lpos[k]] = IA[k];
         }
         __syncthreads();
 
@@ -273,7 +303,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
                 }
                 const unsigned vm = __ballot_sync(kFull, valid);
                 if (vm == 0u) break;
-                apply_group(r, valid);
+                apply_group(r, valid, EV && valid ? IB[k] : 0u);
                 const int nv = __popc(vm);
                 cur += nv;
                 if (nv < 32) break;
@@ -330,7 +360,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
         for (; cur < re; cur += 32) {
             const int k = cur + lane;
             const bool valid = k < re;
-            apply_group(valid ? B[k] : 0ull, valid);
+            apply_group(valid ? B[k] : 0ull, valid, EV && valid ? IB[k] : 0u);
         }
         if (last) break;
         __syncthreads();  // A, B, rcnt are rewritten by the next batch

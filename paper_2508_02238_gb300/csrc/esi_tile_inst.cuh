@@ -8,10 +8,10 @@ namespace esi {
 
 #define ESI_TILE_BOUNDS(TH) __launch_bounds__(TH * 32, (TH * 32 >= 1024) ? 1 : 1024 / (TH * 32))
 
-template <int TH, int PPL, int RD, int DK, bool VEC>
+template <int TH, int PPL, int RD, int DK, bool VEC, bool EV = false>
 __global__ void ESI_TILE_BOUNDS(TH) esi_tile_kernel(TileArgs a)
 {
-    tile_body<TH, PPL, RD, DK, VEC>(a, blockIdx.x);
+    tile_body<TH, PPL, RD, DK, VEC, EV>(a, blockIdx.x);
 }
 
 // Batched tiles of a serving tick: a persistent grid walks the work items

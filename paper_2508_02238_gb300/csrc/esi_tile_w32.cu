@@ -11,6 +11,10 @@ namespace esi {
 
 #define ESI_W32_ALL ESI_W32_VARIANTS(16) ESI_W32_VARIANTS(32)
 
+// per-event output (esi_event_states): no frames, so one render mode and no
+// frame-word variant
+#define ESI_W32_EV Y(16, kDecayGeneral) Y(16, kDecaySquare) Y(16, kDecayNone) Y(32, kDecayGeneral) Y(32, kDecaySquare) Y(32, kDecayNone)
+
 cudaError_t set_tile_attributes_w32()
 {
     cudaError_t e = cudaSuccess;
@@ -18,6 +22,10 @@ cudaError_t set_tile_attributes_w32()
     if (e == cudaSuccess) e = allow_dynamic_smem_impl((const void *)esi_tile_kernel<TH, 1, RD, DK, false>);
     ESI_W32_ALL
 #undef X
+#define Y(TH, DK)                                                                              \
+    if (e == cudaSuccess) e = allow_dynamic_smem_impl((const void *)esi_tile_kernel<TH, 1, 0, DK, false, true>);
+    ESI_W32_EV
+#undef Y
     return e;
 }
 
@@ -33,6 +41,20 @@ cudaError_t launch_tile_w32(const TileArgs &a, int tile_h, cudaStream_t s)
     }
     ESI_W32_ALL
 #undef X
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tile_ev_w32(const TileArgs &a, int tile_h, cudaStream_t s)
+{
+    const size_t smem = tile_smem_bytes_ev(a.batch, a.n_chunks);
+    const int dk = decay_kind_of(a.dp);
+#define Y(TH, DK)                                                                       \
+    if (tile_h == TH && dk == DK) {                                                     \
+        esi_tile_kernel<TH, 1, 0, DK, false, true><<<a.n_tiles, TH * 32, smem, s>>>(a); \
+        return cudaGetLastError();                                                      \
+    }
+    ESI_W32_EV
+#undef Y
     return cudaErrorInvalidValue;
 }
 

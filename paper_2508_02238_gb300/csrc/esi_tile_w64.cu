@@ -14,6 +14,10 @@ namespace esi {
 
 #define ESI_W64_ALL ESI_W64_VARIANTS(4) ESI_W64_VARIANTS(8) ESI_W64_VARIANTS(16)
 
+// per-event output (esi_event_states): no frames, so one render mode and no
+// frame-word variant
+#define ESI_W64_EV Y(4, kDecayGeneral) Y(4, kDecaySquare) Y(4, kDecayNone) Y(8, kDecayGeneral) Y(8, kDecaySquare) Y(8, kDecayNone) Y(16, kDecayGeneral) Y(16, kDecaySquare) Y(16, kDecayNone)
+
 cudaError_t set_tile_attributes_w64()
 {
     cudaError_t e = cudaSuccess;
@@ -21,6 +25,10 @@ cudaError_t set_tile_attributes_w64()
     if (e == cudaSuccess) e = allow_dynamic_smem_impl((const void *)esi_tile_kernel<TH, 2, RD, DK, V>);
     ESI_W64_ALL
 #undef X
+#define Y(TH, DK)                                                                              \
+    if (e == cudaSuccess) e = allow_dynamic_smem_impl((const void *)esi_tile_kernel<TH, 2, 0, DK, false, true>);
+    ESI_W64_EV
+#undef Y
     return e;
 }
 
@@ -36,6 +44,20 @@ cudaError_t launch_tile_w64(const TileArgs &a, int tile_h, bool vec, cudaStream_
     }
     ESI_W64_ALL
 #undef X
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tile_ev_w64(const TileArgs &a, int tile_h, cudaStream_t s)
+{
+    const size_t smem = tile_smem_bytes_ev(a.batch, a.n_chunks);
+    const int dk = decay_kind_of(a.dp);
+#define Y(TH, DK)                                                                       \
+    if (tile_h == TH && dk == DK) {                                                     \
+        esi_tile_kernel<TH, 2, 0, DK, false, true><<<a.n_tiles, TH * 32, smem, s>>>(a); \
+        return cudaGetLastError();                                                      \
+    }
+    ESI_W64_EV
+#undef Y
     return cudaErrorInvalidValue;
 }
 

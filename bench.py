@@ -51,7 +51,7 @@ WORKLOAD = "config1: 640x480, 2 s, ~10M events (40 Gaussian blobs), 200 x 10 ms 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the same launch shape (4 M events, 80 frames per launch);
 # profiles/esi_tile_kernel_config1_small.md, profiles/esi_bin_kernel_config1_small.md.
-NCU_TRAFFIC_PER_LAUNCH = {"esi_tile": 38438656, "esi_bin": 68096000}
+NCU_TRAFFIC_PER_LAUNCH = {"esi_tile": 38525696, "esi_bin": 67803648}
 
 
 def parse_args():

@@ -79,7 +79,7 @@ struct BinArgs {
     unsigned int *hrow;           // out: [tile][chunk] (start << 16 | count)
     int use_mask;                 // same-tile lanes by shared mask words (up to 1024 tiles)
     DevStatus *status;
-    // per-event output (esi_event_states), both null for renders:
+    // per-event output (esi_event_states; both set, or both null for renders):
     unsigned *rec_idx = nullptr;  // out: beside each record, its event's index in the sub-batch
     float *ev_out = nullptr;      // out: NaN at the index of every event outside the sensor
 };

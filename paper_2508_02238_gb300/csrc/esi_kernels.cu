@@ -73,6 +73,9 @@ bool bin_mask_fits(int chunk, int n_tiles)
 
 // One chunk of events: block-level body shared by the single-sensor and the
 // batched binning kernels.  cidx is the chunk's index within a.n's events.
+// EV: also write each record's event index (a.rec_idx) and NaN for events
+// outside the sensor (a.ev_out), for esi_event_states.
+template <bool EV = false>
 __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
 {
     constexpr int NT = kBinThreads, NW = NT / 32;
@@ -149,7 +152,7 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
                 tile = (y >> thl) * tiles_x + (x >> twl);
             } else {
                 ++drop;
-                if (a.ev_out) a.ev_out[c0 + k] = __int_as_float(0x7fc00000);
+                if constexpr (EV) a.ev_out[c0 + k] = __int_as_float(0x7fc00000);
             }
         }
         const bool valid = tile >= 0;
@@ -214,7 +217,7 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
         const bool pos = (signed char)(e.w & 0xff) > 0;
         const unsigned q = tstart[tile] + cnt[w * ntp + tile] + loff[k];
         ssort[q] = make_record((unsigned)(t - a.t_base), pit, pos ? 1u : 0u);
-        if (a.rec_idx) a.rec_idx[c0 + q] = (unsigned)(c0 + k);
+        if constexpr (EV) a.rec_idx[c0 + q] = (unsigned)(c0 + k);
     }
     __syncthreads();
 
@@ -225,6 +228,8 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
 }
 
 __global__ void __launch_bounds__(kBinThreads) esi_bin_kernel(BinArgs a) { bin_chunk(a, blockIdx.x); }
+
+__global__ void __launch_bounds__(kBinThreads) esi_bin_ev_kernel(BinArgs a) { bin_chunk<true>(a, blockIdx.x); }
 
 // Batched binning of a serving tick: block c bins chunk c of the tick; the
 // tick directory names the stream segment (job) each chunk belongs to.  The
@@ -283,6 +288,7 @@ int decay_kind_of(const DecayParams &dp)
 cudaError_t set_kernel_attributes()
 {
     cudaError_t e = allow_dynamic_smem_impl((const void *)esi_bin_kernel);
+    if (e == cudaSuccess) e = allow_dynamic_smem_impl((const void *)esi_bin_ev_kernel);
     if (e == cudaSuccess) e = allow_dynamic_smem_impl((const void *)esi_bin_tab_kernel);
     if (e == cudaSuccess) e = set_tile_attributes_w128();
     if (e == cudaSuccess) e = set_tile_attributes_w32();
@@ -293,7 +299,10 @@ cudaError_t set_kernel_attributes()
 cudaError_t launch_bin(const BinArgs &a, int n_chunks, cudaStream_t s)
 {
     const size_t smem = bin_smem_bytes(a.chunk, a.n_tiles, a.use_mask != 0);
-    esi_bin_kernel<<<n_chunks, kBinThreads, smem, s>>>(a);
+    if (a.rec_idx)
+        esi_bin_ev_kernel<<<n_chunks, kBinThreads, smem, s>>>(a);
+    else
+        esi_bin_kernel<<<n_chunks, kBinThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -74,4 +74,16 @@ def test_null_handle_calls_are_rejected():
     assert esi.esi_render_frame(None, 0, None, 0) == esi.ESI_EINVAL
     assert esi.esi_synchronize(None) == esi.ESI_EINVAL
     assert esi.esi_autotune(None, None, 0, None, 0)[0] == esi.ESI_EINVAL
+    assert esi.esi_noise_map(None, None, 0) == esi.ESI_EINVAL
+    assert esi.esi_count_events(None, None, 0, 0, None, 0) == esi.ESI_EINVAL
+    assert esi.esi_event_states(None, None, 0, 0)[0] == esi.ESI_EINVAL
     esi.esi_destroy(None)  # no-op
+
+
+def test_method_constants_match_the_header():
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "esi.h")).read()
+    for name in ("ESI_METHOD_ALG2", "ESI_METHOD_ALG1", "ESI_METHOD_EQ3_EXP"):
+        m = re.search(r"#define\s+%s\s+(\d+)" % name, hdr)
+        assert m and int(m.group(1)) == getattr(esi, name), name

@@ -17,9 +17,11 @@ reported beside it).  With --gpus N (torchrun) every rank runs its own replica
 on its own GPU (no collective on the data path; weak scaling).
 
 Further legs on rank 0 (skipped with --no-extras): single-frame latency;
-serving of config 3 (64 streams) and config 4 (192 mixed streams with joins
-and leaves), batched and plain; configs 0 and 2 with the default and the
-autotuned launch shape; the oracle on one host core and on all of them.
+serving of 64 streams of 346x260 and of 192 mixed-resolution streams with
+joins and leaves, batched and plain; the 346x260 sinusoid and the 1280x720
+checkerboard workloads with the default and the autotuned launch shape; the
+Fig. 4 diagnostics and per-event states; the oracle on one host core and on
+all of them.
 
 --impl reference times the FP64 CPU oracle (the test reference) on the host
 cores instead, on a bounded sample of the same workload.
@@ -46,11 +48,11 @@ WINDOW_US = 10_000
 DURATION_US = 2_000_000
 PARAMS = dict(C=0.15, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, t_origin_us=0,
               render_decay=1)
-WORKLOAD = "config1: 640x480, 2 s, ~10M events (40 Gaussian blobs), 200 x 10 ms frames, decay view"
+WORKLOAD = "blobs 640x480, 2 s, ~10M events (40 Gaussian blobs), 200 x 10 ms frames, decay view"
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the same launch shape (4 M events, 80 frames per launch);
-# profiles/esi_tile_kernel_config1_small.md, profiles/esi_bin_kernel_config1_small.md.
+# profiles/esi_tile_kernel_blobs640x480_small.md, profiles/esi_bin_kernel_blobs640x480_small.md.
 NCU_TRAFFIC_PER_LAUNCH = {"esi_tile": 38525696, "esi_bin": 67803648}
 
 
@@ -158,7 +160,7 @@ def whole_job_rate(units_per_rank_step: int, steps: int, ws: int, ms: float) -> 
 
 def make_stream():
     import synth
-    sc = synth.config1()
+    sc = synth.blobs_640x480()
     return sc, synth.generate(sc)
 
 
@@ -349,7 +351,7 @@ def bench_esi(args):
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded generator, config-1 scene), state FP32, times int64 us",
+        "data": "synthetic (seeded generator, 640x480 blob scene), state FP32, times int64 us",
         "config": {"workload": WORKLOAD, "events_per_step": n_ev, "frames_per_step": n_windows,
                    "sensor": f"{sc.W}x{sc.H}", "params": PARAMS,
                    "l2": "inputs larger than L2 (160 MB of events per step)",
@@ -370,7 +372,7 @@ def bench_esi(args):
         line["latency"] = latency_leg(esi, torch, sc, ev)
         line["serving"] = serving_leg(esi)
         line["serving_mixed"] = mixed_serving_leg(esi)
-        line["other_configs"] = other_configs_leg(esi, torch)
+        line["other_workloads"] = other_workloads_leg(esi, torch)
         line["diagnostics"] = diagnostics_leg(esi, torch)
     elif not args.no_extras:
         line["e2e"] = None
@@ -456,7 +458,7 @@ SERVING_SECONDS = 0.25
 
 
 def serving_workload(n_streams=SERVING_STREAMS, seconds=SERVING_SECONDS, seed=1003):
-    """64 config-0 form 346x260 streams, lognormal rates, Poisson packets (1 ms mean)."""
+    """64 sinusoid form 346x260 streams, lognormal rates, Poisson packets (1 ms mean)."""
     import synth
     rates = synth.lognormal_rates(n_streams, seed)
     streams = []
@@ -496,7 +498,7 @@ def serving_leg(esi):
     t_end = int(SERVING_SECONDS * 1e6)
     n_ev = int(sum(len(s[2]) for s in streams))
     params = esi.make_params(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1)
-    out = {"workload": f"{len(streams)} streams 346x260 (config-0 form), lognormal rates "
+    out = {"workload": f"{len(streams)} streams 346x260 (sinusoid form), lognormal rates "
                        f"{rates.min() / 1e6:.2f}-{rates.max() / 1e6:.2f} Mev/s (median "
                        f"{np.median(rates) / 1e6:.2f}), Poisson packets 1 ms, 100 frames/s, "
                        f"{SERVING_SECONDS} s", "events": n_ev}
@@ -535,22 +537,24 @@ def serving_leg(esi):
     return out
 
 
-def other_configs_leg(esi, torch):
+def other_workloads_leg(esi, torch):
     """Device-resident throughput of the other single-stream workloads, measured
     as the main step: K replays of the stream shifted in time, pushed before
     timing, rendered to device memory, CUDA events on the handle's stream."""
     import synth
     peak, _ = load_peaks()
     out = {}
-    cases = [("config0: 346x260, 1 s, ~1 M events, 100 x 10 ms frames", 0, 10_000, 12),
-             ("config2: 1280x720, 1 s, ~50 M events, 100 x 10 ms frames", 2, 10_000, 3),
-             ("config2: 1280x720, 1 s, ~50 M events, 1000 x 1 ms frames", 2, 1_000, 3)]
+    cases = [("sinusoid 346x260, 1 s, ~1 M events, 100 x 10 ms frames", synth.sinusoid_346x260, 10_000, 12),
+             ("checkerboard 1280x720, 1 s, ~50 M events, 100 x 10 ms frames",
+              synth.checkerboard_1280x720, 10_000, 3),
+             ("checkerboard 1280x720, 1 s, ~50 M events, 1000 x 1 ms frames",
+              synth.checkerboard_1280x720, 1_000, 3)]
     streams = {}
-    for label, cfg, win, K in cases:
-        if cfg not in streams:
-            sc = synth.CONFIGS[cfg]()
-            streams[cfg] = (sc, synth.generate(sc))
-        sc, ev = streams[cfg]
+    for label, make, win, K in cases:
+        if make not in streams:
+            sc = make()
+            streams[make] = (sc, synth.generate(sc))
+        sc, ev = streams[make]
         n_ev = len(ev)
         span = int(round(sc.duration_s * 1e6))
         n_w = span // win
@@ -594,7 +598,7 @@ def other_configs_leg(esi, torch):
 
 
 def diagnostics_leg(esi, torch, reps=5):
-    """Fig. 4 diagnostics: per-pixel event counts of config 2's 1 s stream
+    """Fig. 4 diagnostics: per-pixel event counts of the 1280x720 checkerboard's 1 s stream
     (events and counts on the device) and the noise map ln(1 + |S|) of a
     4000x3000 state.  Each launch is timed by the library's CUDA events on
     the handle's stream, with a 256 MB write before it to flush L2."""
@@ -616,7 +620,7 @@ def diagnostics_leg(esi, torch, reps=5):
         nl, tot = prof[kind]
         return tot / nl
 
-    sc = synth.CONFIGS[2]()
+    sc = synth.checkerboard_1280x720()
     ev = synth.generate(sc)
     n = len(ev)
     st = torch.cuda.Stream()
@@ -627,11 +631,11 @@ def diagnostics_leg(esi, torch, reps=5):
     ms = timed(h, st, lambda: esi.esi_count_events(h, dev_ev, n, 1, counts, 1), "esi_count")
     esi.esi_destroy(h)
     gbs = 16.0 * n / (ms / 1e3) / 1e9
-    out["event_counts"] = {"workload": f"config2: {sc.W}x{sc.H}, {n} events", "ms": ms,
+    out["event_counts"] = {"workload": f"checkerboard {sc.W}x{sc.H}, {n} events", "ms": ms,
                            "events_per_s": n / (ms / 1e3), "achieved_gbs": gbs,
                            "frac": gbs / peak, "bytes": "16 B per event read"}
     del dev_ev, counts
-    # continuous-time output: S after every event of the config-1 step
+    # continuous-time output: S after every event of the main step's stream
     sc1, ev1 = make_stream()
     n1 = len(ev1)
     rc, h = esi.esi_create(sc1.W, sc1.H, esi.make_params(**PARAMS), st.cuda_stream)
@@ -652,7 +656,7 @@ def diagnostics_leg(esi, torch, reps=5):
             steps.append(e0.elapsed_time(e1))
     esi.esi_destroy(h)
     ms = float(np.median(steps))
-    out["event_states"] = {"workload": f"config1: {sc1.W}x{sc1.H}, {n1} events per call",
+    out["event_states"] = {"workload": f"blobs {sc1.W}x{sc1.H}, {n1} events per call",
                            "ms": ms, "events_per_s": n1 / (ms / 1e3),
                            "note": "binning + the tile kernel with per-event output; S written per event (4 B)"}
     del vals
@@ -672,8 +676,8 @@ MIXED_SECONDS = 0.25
 
 
 def mixed_serving_leg(esi, seconds=MIXED_SECONDS, seed=1004):
-    """Mixed resolutions with join/leave: 16 x 1280x720 (config-2 form), 48 x
-    640x480 (config-1 form), 128 x 346x260 (config-0 form) streams, lognormal
+    """Mixed resolutions with join/leave: 16 x 1280x720 (checkerboard form), 48 x
+    640x480 (blob form), 128 x 346x260 (sinusoid form) streams, lognormal
     rates in [0.1, 20] Mev/s, Poisson packets (1 ms mean), a quarter joining in
     the first half and a fifth leaving in the second, admission by state
     memory, tile height autotuned per sensor size, 100 frames/s per stream."""
@@ -734,7 +738,7 @@ def mixed_serving_leg(esi, seconds=MIXED_SECONDS, seed=1004):
     expected = sum(((w["t_leave_us"] if w["t_leave_us"] is not None else t_end) - w["t_join_us"])
                    // 10_000 for w in ws)
     rates = np.array([w["rate"] for w in ws])
-    out = {"workload": "config-4 form: 16 x 1280x720 + 48 x 640x480 + 128 x 346x260 streams "
+    out = {"workload": "mixed: 16 x 1280x720 + 48 x 640x480 + 128 x 346x260 streams "
                        f"({sum(w['W'] * w['H'] for w in ws) / 1e6:.1f} M pixels), lognormal rates "
                        f"{rates.min() / 1e6:.2f}-{rates.max() / 1e6:.2f} Mev/s (sum "
                        f"{rates.sum() / 1e6:.0f} Mev/s), {sum(w['t_join_us'] > 0 for w in ws)} join "
@@ -769,12 +773,12 @@ def mixed_serving_leg(esi, seconds=MIXED_SECONDS, seed=1004):
 
 def ncu_case():
     """A small case of the same launch shape for kernel captures: 0.8 s of the
-    config-1 stream (about 4 M events, 64 MB, one sub-batch per render as in
+    640x480 blob stream (about 4 M events, 64 MB, one sub-batch per render as in
     the bench), 80 frames per render, three renders."""
     import torch  # noqa: F401  (CUDA context as in the bench)
     import synth
     from paper_2508_02238_gb300 import esi
-    sc = synth.config1(duration_s=0.8)
+    sc = synth.blobs_640x480(duration_s=0.8)
     ev = synth.generate(sc)
     span = 800_000
     rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**PARAMS), 0)

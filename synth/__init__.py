@@ -7,19 +7,19 @@ oracle and the CUDA path consume its output; neither is imported here.
 Event layout (16 bytes, little endian): int64 t (microseconds), uint16 x,
 uint16 y, int8 p (polarity, >0 means +1), 3 padding bytes.
 
-Workload recipes (seeds 1000 + config index):
+Workload recipes (seeds 1000, 1001, 1002):
 
-* ``config0`` 346x260, 1 s: sinusoid of 0.05 cycles/px translating at 200 px/s,
+* ``sinusoid_346x260`` 346x260, 1 s: sinusoid of 0.05 cycles/px translating at 200 px/s,
   C = 0.2 (2 % per-pixel mismatch), 0.1 Hz/px noise, amplitude tuned to
   about 1 M events.
-* ``config1`` 640x480, 2 s: 40 Gaussian blobs in log intensity (sigma 5-30 px,
+* ``blobs_640x480`` 640x480, 2 s: 40 Gaussian blobs in log intensity (sigma 5-30 px,
   linear motion up to 1000 px/s, toroidal wrap), per-pixel C ~ N(0.15, 0.03),
   0.1 Hz/px noise, about 10 M events.
-* ``config2`` 1280x720, 1 s: 32 px checkerboard rotating at 2 rad/s (log
+* ``checkerboard_1280x720`` 1280x720, 1 s: 32 px checkerboard rotating at 2 rad/s (log
   contrast 0.40, 1.5 px edges), two bursts (20 ms, 10 ms) of 100 Hz flicker of
   +-22 % intensity, 0.05 % hot pixels at 1-20 kHz (80 % positive), C = 0.2
   (3 % mismatch), about 50 M events with heavy-tailed per-pixel counts.
-* ``serving_stream`` config-0 form with a given seed, phase and event rate.
+* ``serving_stream`` sinusoid form with a given seed, phase and event rate.
 """
 from __future__ import annotations
 
@@ -187,7 +187,7 @@ def _s0_nominal(rate_ev_s: float, W: int, H: int) -> float:
                                   left=None, right=None))) * W * H
 
 
-def config0(duration_s: float = 1.0, seed: int = 1000, t0_us: int = 0,
+def sinusoid_346x260(duration_s: float = 1.0, seed: int = 1000, t0_us: int = 0,
             rate_ev_s: float = 1.0e6, W: int = 346, H: int = 260,
             phase_px: float = 0.0) -> Scene:
     s = _base(0, W, H, duration_s, seed, 0.2, 0.02, 0.1, t0_us)
@@ -197,7 +197,7 @@ def config0(duration_s: float = 1.0, seed: int = 1000, t0_us: int = 0,
     return s
 
 
-def config1(duration_s: float = 2.0, seed: int = 1001, t0_us: int = 0,
+def blobs_640x480(duration_s: float = 2.0, seed: int = 1001, t0_us: int = 0,
             W: int = 640, H: int = 480, n_blobs: int = 40) -> Scene:
     s = _base(1, W, H, duration_s, seed, 0.15, 0.2, 0.1, t0_us)
     s.n_blobs = n_blobs
@@ -207,7 +207,7 @@ def config1(duration_s: float = 2.0, seed: int = 1001, t0_us: int = 0,
     return s
 
 
-def config2(duration_s: float = 1.0, seed: int = 1002, t0_us: int = 0,
+def checkerboard_1280x720(duration_s: float = 1.0, seed: int = 1002, t0_us: int = 0,
             W: int = 1280, H: int = 720) -> Scene:
     s = _base(2, W, H, duration_s, seed, 0.2, 0.03, 0.1, t0_us)
     s.checker_px, s.rot_rad_s, s.checker_log_contrast, s.edge_px = 32.0, 2.0, 0.40, 1.5
@@ -223,8 +223,8 @@ def config2(duration_s: float = 1.0, seed: int = 1002, t0_us: int = 0,
 def serving_stream(index: int, rate_ev_s: float, duration_s: float,
                    W: int = 346, H: int = 260, base_seed: int = 1003,
                    t0_us: int = 0) -> Scene:
-    """Config-0 form stream number ``index`` (own seed and phase) at a target rate."""
-    return config0(duration_s=duration_s, seed=base_seed * 1000 + index,
+    """Sinusoid form stream number ``index`` (own seed and phase) at a target rate."""
+    return sinusoid_346x260(duration_s=duration_s, seed=base_seed * 1000 + index,
                    t0_us=t0_us, rate_ev_s=rate_ev_s, W=W, H=H,
                    phase_px=(index * 7.3) % 20.0)
 
@@ -236,22 +236,20 @@ def lognormal_rates(n: int, seed: int, median: float = 1.0e6, sigma: float = 0.8
     return np.clip(median * np.exp(sigma * rng.standard_normal(n)), lo, hi)
 
 
-CONFIGS = {0: config0, 1: config1, 2: config2}
-
-# Generated events/s of the config-1 and config-2 scenes at their default sizes
+# Generated events/s of the blob and checkerboard scenes at their default sizes
 # (over their first 0.25 s); thinning brings a stream of either form down to a
 # lower target rate.
-C1_NATURAL_RATE = 4.9e6
-C2_NATURAL_RATE = 46.0e6
-# the config-0 calibration above reaches 8 Mev/s at 346x260
+BLOBS_NATURAL_RATE = 4.9e6
+CHECKER_NATURAL_RATE = 46.0e6
+# the sinusoid calibration above reaches 8 Mev/s at 346x260
 C0_MAX_RATE = 8.0e6
 
 
 def mixed_serving(duration_s: float = 0.25, seed: int = 1004, counts=(16, 48, 128),
                   median: float = 1.0e6, sigma: float = 1.0, lo: float = 0.1e6,
                   hi: float = 20.0e6, late_join: float = 0.25, leave: float = 0.2):
-    """Mixed-resolution serving workload: counts[0] 1280x720 config-2 form,
-    counts[1] 640x480 config-1 form and counts[2] 346x260 config-0 form
+    """Mixed-resolution serving workload: counts[0] 1280x720 checkerboard form,
+    counts[1] 640x480 blob form and counts[2] 346x260 sinusoid form
     streams.  Rates are lognormal(median, sigma) clipped to [lo, hi] and to
     what each scene generates.  A fraction late_join of the streams joins at a
     seeded time in the first half (on a 1 ms grid), a fraction leave leaves at
@@ -273,16 +271,16 @@ def mixed_serving(duration_s: float = 0.25, seed: int = 1004, counts=(16, 48, 12
         sd = seed * 1000 + i
         if form == 0:
             rate = float(min(rates[i], C0_MAX_RATE))
-            sc = config0(duration_s=dur, seed=sd, t0_us=t_join, rate_ev_s=rate,
+            sc = sinusoid_346x260(duration_s=dur, seed=sd, t0_us=t_join, rate_ev_s=rate,
                          phase_px=(i * 7.3) % 20.0)
         elif form == 1:
-            rate = float(min(rates[i], C1_NATURAL_RATE))
-            sc = config1(duration_s=dur, seed=sd, t0_us=t_join)
-            sc.keep_prob = rate / C1_NATURAL_RATE
+            rate = float(min(rates[i], BLOBS_NATURAL_RATE))
+            sc = blobs_640x480(duration_s=dur, seed=sd, t0_us=t_join)
+            sc.keep_prob = rate / BLOBS_NATURAL_RATE
         else:
-            rate = float(min(rates[i], C2_NATURAL_RATE))
-            sc = config2(duration_s=dur, seed=sd, t0_us=t_join)
-            sc.keep_prob = rate / C2_NATURAL_RATE
+            rate = float(min(rates[i], CHECKER_NATURAL_RATE))
+            sc = checkerboard_1280x720(duration_s=dur, seed=sd, t0_us=t_join)
+            sc.keep_prob = rate / CHECKER_NATURAL_RATE
         out.append(dict(form=form, W=sc.W, H=sc.H, rate=rate, t_join_us=t_join,
                         t_leave_us=t_leave, scene=sc))
     return out

@@ -29,7 +29,7 @@ def _valid(t):
 
 
 def test_autotune_keeps_state_and_matches_oracle():
-    sc = synth.config0()
+    sc = synth.sinusoid_346x260()
     ev = synth.generate(sc)
     W, H = sc.W, sc.H
     tf = np.arange(10_000, 1_000_001, 10_000)
@@ -57,7 +57,7 @@ def test_autotune_keeps_state_and_matches_oracle():
         S, T = g.state()
     ref = run_oracle(ev, W, H, P, tf)
     gpu = {"S": S, "T": T, "frames": np.concatenate([f0, f1])}
-    compare(gpu, ref, P["C"], "config0 autotuned")
+    compare(gpu, ref, P["C"], "sinusoid 346x260 autotuned")
 
 
 def test_autotune_cache_is_reused():

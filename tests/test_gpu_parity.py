@@ -95,54 +95,57 @@ def test_launch_shapes_give_bit_identical_results():
 
 # ------------------------------------------------------------- the workloads
 @pytest.fixture(scope="module")
-def config_streams():
+def scene_streams():
     return {}
 
 
-def _config(config_streams, cfg):
-    if cfg not in config_streams:
-        sc = synth.CONFIGS[cfg]()
-        config_streams[cfg] = (sc, synth.generate(sc))
-    return config_streams[cfg]
+def _scene(scene_streams, make):
+    """The full-size stream of a scene generator, generated once per module."""
+    if make not in scene_streams:
+        sc = make()
+        scene_streams[make] = (sc, synth.generate(sc))
+    return scene_streams[make]
 
 
-CFG_C = {0: 0.2, 1: 0.15, 2: 0.2}
+# contrast step C of each scene (its generator's mean threshold)
+SCENE_C = {synth.sinusoid_346x260: 0.2, synth.blobs_640x480: 0.15,
+           synth.checkerboard_1280x720: 0.2}
 
 
 @pytest.mark.parametrize("rd", [0, 1])
-def test_config0_full(config_streams, rd):
-    sc, ev = _config(config_streams, 0)
-    p = P(C=CFG_C[0], render_decay=rd)
+def test_sinusoid_346x260_full(scene_streams, rd):
+    sc, ev = _scene(scene_streams, synth.sinusoid_346x260)
+    p = P(C=SCENE_C[synth.sinusoid_346x260], render_decay=rd)
     tf = np.arange(10_000, 1_000_001, 10_000)
     res = compare(run_gpu(ev, sc.W, sc.H, p, tf), run_oracle(ev, sc.W, sc.H, p, tf), p["C"],
-                  "config0")
-    print("config0", rd, res)
+                  "sinusoid 346x260")
+    print("sinusoid 346x260", rd, res)
 
 
-def test_config1_full(config_streams):
-    sc, ev = _config(config_streams, 1)
-    p = P(C=CFG_C[1], render_decay=1)
+def test_blobs_640x480_full(scene_streams):
+    sc, ev = _scene(scene_streams, synth.blobs_640x480)
+    p = P(C=SCENE_C[synth.blobs_640x480], render_decay=1)
     tf = np.arange(10_000, 2_000_001, 10_000)
     res = compare(run_gpu(ev, sc.W, sc.H, p, tf), run_oracle(ev, sc.W, sc.H, p, tf), p["C"],
-                  "config1")
-    print("config1", res)
+                  "blobs 640x480")
+    print("blobs 640x480", res)
 
 
-def test_config2_full_10ms(config_streams):
-    sc, ev = _config(config_streams, 2)
-    p = P(C=CFG_C[2], render_decay=1)
+def test_checkerboard_1280x720_full_10ms(scene_streams):
+    sc, ev = _scene(scene_streams, synth.checkerboard_1280x720)
+    p = P(C=SCENE_C[synth.checkerboard_1280x720], render_decay=1)
     tf = np.arange(10_000, 1_000_001, 10_000)
     res = compare(run_gpu(ev, sc.W, sc.H, p, tf), run_oracle(ev, sc.W, sc.H, p, tf), p["C"],
-                  "config2")
-    print("config2", res)
+                  "checkerboard 1280x720")
+    print("checkerboard 1280x720", res)
 
 
-def test_config2_1ms_windows_sampled(config_streams):
+def test_checkerboard_1280x720_1ms_windows_sampled(scene_streams):
     # 1000 frames of 1280x720: compare the final state in full and a sample of
     # frames the oracle renders one by one (frames never change the state)
     import torch
-    sc, ev = _config(config_streams, 2)
-    p = P(C=CFG_C[2], render_decay=1)
+    sc, ev = _scene(scene_streams, synth.checkerboard_1280x720)
+    p = P(C=SCENE_C[synth.checkerboard_1280x720], render_decay=1)
     tf = np.arange(1_000, 1_000_001, 1_000)
     with GpuStream(sc.W, sc.H, p) as g:
         assert g.push(ev) == 0
@@ -162,8 +165,8 @@ def test_config2_1ms_windows_sampled(config_streams):
         ref_frames.append(st.render(tf[w]))
     st.integrate(ev[i:])
     res = compare({"S": S, "T": T, "frames": frames},
-                  {"S": st.S, "T": st.T, "frames": np.stack(ref_frames)}, p["C"], "config2-1ms")
-    print("config2 1ms", res)
+                  {"S": st.S, "T": st.T, "frames": np.stack(ref_frames)}, p["C"], "checkerboard 1280x720, 1 ms")
+    print("checkerboard 1280x720, 1 ms", res)
 
 
 # ---------------------------------------------------------------- edge cases

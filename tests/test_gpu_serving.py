@@ -338,8 +338,8 @@ def test_executor_join_leave_and_admission():
         if W == 346:
             sc = synth.serving_stream(k, rate, dur, t0_us=tj)
         else:
-            sc = synth.config1(duration_s=dur, seed=5000 + k, t0_us=tj)
-            sc.keep_prob = rate / synth.C1_NATURAL_RATE
+            sc = synth.blobs_640x480(duration_s=dur, seed=5000 + k, t0_us=tj)
+            sc.keep_prob = rate / synth.BLOBS_NATURAL_RATE
         evs.append(synth.generate(sc))
         sp = esi.esi_stream_spec()
         sp.width, sp.height, sp.tile_h = W, H, (4, 8, 16, 8, 4)[k]

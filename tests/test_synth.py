@@ -17,8 +17,8 @@ def _check_stream(ev, sc):
     assert np.all(np.diff(pix)[same] >= 0)
 
 
-def test_config0_short_is_deterministic_and_ordered():
-    sc = synth.config0(duration_s=0.1, t0_us=5000)
+def test_sinusoid_short_is_deterministic_and_ordered():
+    sc = synth.sinusoid_346x260(duration_s=0.1, t0_us=5000)
     a = synth.generate(sc, threads=1)
     b = synth.generate(sc, threads=4)
     assert len(a) > 50_000
@@ -26,8 +26,8 @@ def test_config0_short_is_deterministic_and_ordered():
     _check_stream(a, sc)
 
 
-def test_config1_small_sensor():
-    sc = synth.config1(duration_s=0.2, W=96, H=64, n_blobs=6)
+def test_blobs_small_sensor():
+    sc = synth.blobs_640x480(duration_s=0.2, W=96, H=64, n_blobs=6)
     ev = synth.generate(sc)
     assert len(ev) > 1000
     _check_stream(ev, sc)
@@ -35,8 +35,8 @@ def test_config1_small_sensor():
     assert (ev["p"] > 0).mean() > 0.2 and (ev["p"] < 0).mean() > 0.2
 
 
-def test_config2_small_sensor_has_hot_pixels_and_bursts():
-    sc = synth.config2(duration_s=0.4, W=160, H=96)
+def test_checkerboard_small_sensor_has_hot_pixels_and_bursts():
+    sc = synth.checkerboard_1280x720(duration_s=0.4, W=160, H=96)
     sc.hot_frac = 0.01
     ev = synth.generate(sc)
     _check_stream(ev, sc)
@@ -58,7 +58,7 @@ def _keys(ev):
 
 
 def test_thinning_keeps_a_subset_at_the_asked_fraction():
-    sc = synth.config1(duration_s=0.05, W=160, H=120, n_blobs=10)
+    sc = synth.blobs_640x480(duration_s=0.05, W=160, H=120, n_blobs=10)
     full = synth.generate(sc)
     sc.keep_prob = 0.3
     thin = synth.generate(sc)

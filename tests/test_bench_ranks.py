@@ -62,3 +62,27 @@ def test_reference_arm_is_rank_zero_only(monkeypatch, capsys):
         gpus, steps, warmup = 2, 1, 0
     bench.bench_reference(A())
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_the_contract_line():
+    # rank 0, N = 1: one JSON line timing the FP64 oracle on a bounded sample,
+    # on the same workload, metric and unit as the CUDA arm
+    import json
+    import subprocess
+    sys.path.insert(0, ROOT)
+    import bench
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0"], cwd=ROOT, env=env, capture_output=True,
+                         text=True, timeout=300, check=True).stdout
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 1 and line["steps"] == 1
+    assert line["metric"] == bench.METRIC and line["unit"] == "events/s"
+    assert line["config"]["workload"] == bench.WORKLOAD
+    assert line["higher_is_better"] is True and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "events/s",
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

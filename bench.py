@@ -1,27 +1,31 @@
 #!/usr/bin/env python3
 """Throughput of the ESI hot path on one GB300 (events/s and frames/s).
 
-Workload (one step): the 640x480, 2 s synthetic stream of configuration 1
-(40 Gaussian blobs, per-pixel C ~ N(0.15, 0.03), ~10 M events, int64 us),
-rendered as 200 frames of 10 ms with the decay view (render_decay = 1),
-C = 0.15, k = 10 /s, b = 2, clamp [-1, 1].  Step k replays the stream shifted
-by k * 2 s, so the state carries on as one continuous stream.
+Headline workload (one step): the 1280x720, 1 s synthetic stream of the
+checkerboard scene (32 px squares rotating at 2 rad/s, two bursts of 100 Hz
+flicker, 0.05 % hot pixels at 1-20 kHz; ~50 M events, int64 us), rendered as
+100 frames of 10 ms with the decay view (render_decay = 1), C = 0.2,
+k = 10 /s, b = 2, clamp [-1, 1].  It is the largest single-sensor workload.
+Step k replays the stream shifted by k seconds, so the state carries on as
+one continuous stream.
 
 value: events/s with every step's events already resident in device memory
 (pushed before the timed region), frames written to device memory; inputs
-per step (160 MB) exceed the 129 MB L2.  e2e: the same metric through the C
+per step (800 MB) exceed the 129 MB L2.  e2e: the same metric through the C
 ABI with pinned host buffers inside the timed region: each step pushes its
 events from host memory and renders its frames into a host buffer, the next
 step's push overlapping this step's render (the synchronous variant is
 reported beside it).  With --gpus N (torchrun) every rank runs its own replica
 on its own GPU (no collective on the data path; weak scaling).
 
-Further legs on rank 0 (skipped with --no-extras): single-frame latency;
-serving of 64 streams of 346x260 and of 192 mixed-resolution streams with
-joins and leaves, batched and plain; the 346x260 sinusoid and the 1280x720
-checkerboard workloads with the default and the autotuned launch shape; the
-Fig. 4 diagnostics and per-event states; the oracle on one host core and on
-all of them.
+Further legs on rank 0 (skipped with --no-extras): the other single-sensor
+workloads (346x260 sinusoid, 640x480 blobs, the 1280x720 stream in 1 ms
+frames); single-frame latency; batched serving of 64 streams of 346x260 and of
+192 mixed-resolution streams with joins and leaves, batched and plain; the
+Fig. 4 diagnostics and per-event states; and the oracle leg: the FP64 oracle
+timed on one host core and on all of them, and its results compared with
+the GPU's on every workload (the per-workload maximum errors).  A compact
+summary closes the line.
 
 --impl reference times the FP64 CPU oracle (the test reference) on the host
 cores instead, on a bounded sample of the same workload.
@@ -45,15 +49,26 @@ import numpy as np  # noqa: E402
 
 METRIC = "events/s and frames/s at 1 GB300 (% HBM roofline); p50/p99 frame latency, batched vs plain"
 WINDOW_US = 10_000
-DURATION_US = 2_000_000
-PARAMS = dict(C=0.15, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, t_origin_us=0,
+PARAMS = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, t_origin_us=0,
               render_decay=1)
-WORKLOAD = "blobs 640x480, 2 s, ~10M events (40 Gaussian blobs), 200 x 10 ms frames, decay view"
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of the same launch shape (4 M events, 80 frames per launch);
-# profiles/esi_tile_kernel_blobs640x480_small.md, profiles/esi_bin_kernel_blobs640x480_small.md.
-NCU_TRAFFIC_PER_LAUNCH = {"esi_tile": 38525696, "esi_bin": 67803648}
+# name: (label, generator, duration in us, frame period in us, C)
+WORKLOADS = {
+    "c0": ("sinusoid 346x260, 1 s, ~1 M events, 100 x 10 ms frames", "sinusoid_346x260",
+           1_000_000, 10_000, 0.2),
+    "c1": ("blobs 640x480, 2 s, ~10 M events (40 Gaussian blobs), 200 x 10 ms frames",
+           "blobs_640x480", 2_000_000, 10_000, 0.15),
+    "c2": ("checkerboard 1280x720, 1 s, ~50 M events (rotating, flicker bursts, hot pixels), "
+           "100 x 10 ms frames", "checkerboard_1280x720", 1_000_000, 10_000, 0.2),
+    "c2_1ms": ("checkerboard 1280x720, 1 s, ~50 M events, 1000 x 1 ms frames",
+               "checkerboard_1280x720", 1_000_000, 1_000, 0.2),
+}
+HEADLINE = "c2"
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel, from one ncu capture of the headline's launch shape
+# (--ncu-case), keyed by kernel; None until a capture of the kernel as built.
+NCU_TRAFFIC_PER_LAUNCH = {}
 
 
 def parse_args():
@@ -63,15 +78,19 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["esi", "reference"], default="esi")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the e2e, latency and CPU-baseline legs")
+                    help="skip every leg but the headline measurement")
     ap.add_argument("--serving-only", action="store_true",
                     help="run only the two serving legs and print their JSON")
+    ap.add_argument("--serving-seconds", type=float, default=None,
+                    help="stream time of the serving legs (default 5 s)")
     ap.add_argument("--ncu-case", action="store_true",
-                    help="run the small profiling case (0.4 s of the stream, 40 frames, 3 renders) "
-                         "and print no bench line; for ncu captures")
+                    help="run the small profiling case (0.25 s of the headline stream, 25 frames, "
+                         "3 renders) and print no bench line; for ncu captures")
     ap.add_argument("--diagnostics-only", action="store_true",
                     help="run only the diagnostics leg (event counts, per-event states, noise "
                          "map) and print its JSON; also the case for their ncu captures")
+    ap.add_argument("--parity-only", action="store_true",
+                    help="run only the oracle comparison of every workload and print its JSON")
     return ap.parse_args()
 
 
@@ -158,74 +177,103 @@ def whole_job_rate(units_per_rank_step: int, steps: int, ws: int, ms: float) -> 
     return units_per_rank_step * steps * ws / (ms / 1e3)
 
 
-def make_stream():
+_STREAMS = {}
+
+
+def workload(name):
+    """(scene, events, span_us, frame period, params) of a named workload."""
     import synth
-    sc = synth.blobs_640x480()
-    return sc, synth.generate(sc)
+    label, gen, span, win, C = WORKLOADS[name]
+    if gen not in _STREAMS:
+        sc = getattr(synth, gen)()
+        _STREAMS[gen] = (sc, synth.generate(sc))
+    sc, ev = _STREAMS[gen]
+    return sc, ev, span, win, dict(PARAMS, C=C)
 
 
-def shifted(ev, k):
+def shifted(ev, dt):
     e = ev.copy()
-    e["t"] += k * DURATION_US
+    e["t"] += dt
     return e
 
 
-def frame_times(k, n_windows):
-    return np.arange(1, n_windows + 1, dtype=np.int64) * WINDOW_US + k * DURATION_US
+def frame_times(k, span, win):
+    return np.arange(1, span // win + 1, dtype=np.int64) * win + k * span
 
 
-def cpu_baseline(sc, ev, budget_s: float = 10.0):
-    """The oracle as it stands on one host core: whole-stream replays until budget_s."""
-    import oracle
-    reps, used, t0 = 0, 0, time.perf_counter()
-    n_windows = DURATION_US // WINDOW_US
-    while True:
-        st = oracle.OracleState(sc.W, sc.H, oracle.OracleParams(**PARAMS))
-        _, u = st.replay(ev, frame_times(0, n_windows))
-        used += u
-        reps += 1
-        if time.perf_counter() - t0 >= budget_s or reps >= 8:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": used / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
-            "sample": f"{reps} replay(s) of the whole 2 s stream ({len(ev)} events, "
-                      f"{n_windows} frames each), {dt:.1f} s"}
+def tile_roofline(prof, P, frames_per_step, steps, n_ev, peak, peak_kind, traffic=None):
+    """Roofline of the dominant kernel: algorithmic bytes per launch over its
+    average CUDA-event duration.  Tile kernel: 24 B per pixel of state (S, T
+    read and written once per launch) + 1 B per pixel per frame; binning:
+    16 B per event read."""
+    if not prof:
+        return None
+    name, (nl, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    if name == "esi_bin":
+        bytes_per_launch = 16.0 * n_ev * steps / nl
+    else:
+        bytes_per_launch = (24.0 * P * nl + frames_per_step * P * steps) / nl
+    achieved = bytes_per_launch / (tot_ms / nl / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+            "peak_kind": f"of {peak_kind}", "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "launches": nl, "avg_launch_us": tot_ms / nl * 1e3,
+            "bytes_per_launch": bytes_per_launch}
 
 
-def _oracle_band(job):
-    """Worker: the oracle over the events of one band of rows (pixels of
-    different bands never interact, Eq. 5), timed inside the worker."""
-    band, n_bands, path, W, H = job
-    import oracle
-    ev = np.load(path, mmap_mode="r")
-    y0, y1 = band * H // n_bands, (band + 1) * H // n_bands
-    sel = np.array(ev[(ev["y"] >= y0) & (ev["y"] < y1)])
-    sel["y"] -= y0     # the band as a sensor of its own: only its pixels render
-    st = oracle.OracleState(W, y1 - y0, oracle.OracleParams(**PARAMS))
-    t0 = time.perf_counter()
-    _, used = st.replay(sel, frame_times(0, DURATION_US // WINDOW_US))
-    return used, time.perf_counter() - t0
+def kernel_shares(prof):
+    tot = max(1e-9, sum(x[1] for x in prof.values()))
+    return {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / tot} for k, v in prof.items()}
 
 
-def cpu_baseline_parallel(sc, ev):
-    """The same oracle on every host core: one process per band of rows
-    (spawned, so no CUDA state is inherited); throughput = all events / the
-    slowest band's compute time."""
-    import multiprocessing as mp
-    cores = os.cpu_count() or 1
-    fd, path = tempfile.mkstemp(suffix=".npy")
-    os.close(fd)
-    try:
-        np.save(path, ev)
-        with mp.get_context("spawn").Pool(cores) as pool:
-            res = pool.map(_oracle_band, [(b, cores, path, sc.W, sc.H) for b in range(cores)])
-    finally:
-        os.unlink(path)
-    used = sum(r[0] for r in res)
-    slowest = max(r[1] for r in res)
-    return {"value": used / slowest, "unit": "events/s", "cores": cores, "kind": "oracle",
-            "sample": f"the whole 2 s stream ({used} events, 200 frames) split into {cores} "
-                      f"bands of rows, one process each; {slowest:.2f} s for the slowest band"}
+def device_steps(esi, torch, name, warmup, steps, ws=1, clocks_gpu=None, tuning=None):
+    """K timed steps of a workload with every step's events resident on the
+    device before timing; CUDA events on the handle's stream."""
+    sc, ev, span, win, prm = workload(name)
+    n_ev, P = len(ev), sc.W * sc.H
+    M = span // win
+    stream = torch.cuda.Stream()
+    rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**prm), stream.cuda_stream)
+    esi.check(rc, "esi_create")
+    if tuning is not None:
+        esi.check(esi.esi_set_tuning(h, tuning), "tuning")
+    out = torch.empty((M, sc.H, sc.W), dtype=torch.uint8, device="cuda")
+    total = warmup + steps
+    for k in range(total):
+        esi.check(esi.esi_push_events(h, shifted(ev, k * span), n_ev, 0), "push")
+    tfs = [frame_times(k, span, win) for k in range(total)]
+    for k in range(warmup):
+        esi.check(esi.esi_render_frames(h, tfs[k], M, out, 1), "render")
+    esi.check(esi.esi_synchronize(h), "sync")
+    rc, st0 = esi.esi_get_stats(h)
+    esi.check(esi.esi_profile_reset(h))
+    esi.check(esi.esi_profile_enable(h, 1))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(clocks_gpu) if clocks_gpu is not None else None
+    if clocks:
+        clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(warmup, total):
+        esi.check(esi.esi_render_frames(h, tfs[k], M, out, 1), "render")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
+    esi.check(esi.esi_profile_enable(h, 0))
+    rc, prof = esi.esi_profile_read(h)
+    rc, st1 = esi.esi_get_stats(h)
+    rc, tun = esi.esi_get_tuning(h)
+    return {"handle": h, "stream": stream, "out": out, "ms": ms, "prof": prof, "clocks": clk,
+            "launches": int(st1.kernel_launches - st0.kernel_launches), "n_ev": n_ev, "P": P,
+            "M": M, "span": span, "win": win, "total": total, "sc": sc, "ev": ev, "prm": prm,
+            "shape": {f: getattr(tun, f) for f in ("tile_w", "tile_h", "chunk_events",
+                                                    "batch_records", "max_batch_events")}}
 
 
 def bench_reference(args):
@@ -233,14 +281,14 @@ def bench_reference(args):
     if rank != 0:
         return
     import oracle
-    sc, ev = make_stream()
-    # each step: the first 0.4 s of the stream (40 frames) from a fresh state
-    n_w = 40
-    sample = ev[ev["t"] <= n_w * WINDOW_US]
-    tf = frame_times(0, n_w)
+    sc, ev, span, win, prm = workload(HEADLINE)
+    # each step: the first 0.1 s of the stream (10 frames) from a fresh state
+    n_w = 10
+    sample = ev[ev["t"] <= n_w * win]
+    tf = frame_times(0, span, win)[:n_w]
 
     def step():
-        st = oracle.OracleState(sc.W, sc.H, oracle.OracleParams(**PARAMS))
+        st = oracle.OracleState(sc.W, sc.H, oracle.OracleParams(**prm))
         st.replay(sample, tf)
 
     for _ in range(args.warmup):
@@ -255,10 +303,10 @@ def bench_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "first 0.4 s (40 frames) per step"},
+        "config": {"workload": WORKLOADS[HEADLINE][0], "sample": "first 0.1 s (10 frames) per step"},
         "frames_per_s": n_w * args.steps / dt,
         "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first 0.4 s of the stream ({len(sample)} events, "
+                         "sample": f"first 0.1 s of the stream ({len(sample)} events, "
                                    f"{n_w} frames) per step"},
         "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -281,80 +329,26 @@ def bench_esi(args):
     dev = torch.cuda.current_device()
     esi.load_library(build_if_missing=True)
 
-    sc, ev = make_stream()
-    n_ev = len(ev)
-    n_windows = DURATION_US // WINDOW_US
-    P = sc.W * sc.H
-    stream = torch.cuda.Stream()
-    rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**PARAMS), stream.cuda_stream)
-    esi.check(rc, "esi_create")
-    out = torch.empty((n_windows, sc.H, sc.W), dtype=torch.uint8, device="cuda")
-
-    # device-resident inputs: every step's events pushed before timing
-    total_steps = args.warmup + args.steps
-    for k in range(total_steps):
-        esi.check(esi.esi_push_events(h, shifted(ev, k), n_ev, 0), "push")
-    tfs = [frame_times(k, n_windows) for k in range(total_steps)]
-
-    def step(k):
-        esi.check(esi.esi_render_frames(h, tfs[k], n_windows, out, 1), "render")
-
-    for k in range(args.warmup):
-        step(k)
-    esi.check(esi.esi_synchronize(h), "sync")
-    rc, st0 = esi.esi_get_stats(h)
-    esi.check(esi.esi_profile_reset(h))
-    esi.check(esi.esi_profile_enable(h, 1))
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(dev)
-    clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(args.warmup, total_steps):
-        step(k)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
-    esi.check(esi.esi_profile_enable(h, 0))
-    rc, prof = esi.esi_profile_read(h)
-    rc, st1 = esi.esi_get_stats(h)
-    launches = int(st1.kernel_launches - st0.kernel_launches)
-
+    r = device_steps(esi, torch, HEADLINE, args.warmup, args.steps, ws, clocks_gpu=dev)
+    ms, n_ev, P, M = r["ms"], r["n_ev"], r["P"], r["M"]
     value = whole_job_rate(n_ev, args.steps, ws, ms)
-    frames_per_s = whole_job_rate(n_windows, args.steps, ws, ms)
-
-    # roofline of the dominant kernel (algorithmic bytes / measured duration)
+    frames_per_s = whole_job_rate(M, args.steps, ws, ms)
     peak, peak_kind = load_peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
-    roof = None
-    step_bytes = 16 * n_ev + 24 * P + n_windows * P
-    if dom:
-        name, (nl, tot_ms) = dom
-        if name == "esi_bin":
-            bytes_per_launch = 16.0 * n_ev * args.steps / nl
-        else:
-            bytes_per_launch = (24.0 * P * nl + n_windows * P * args.steps) / nl
-        achieved = bytes_per_launch / (tot_ms / nl / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
-                "peak_kind": f"of {peak_kind}", "unit": "GB/s", "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC_PER_LAUNCH.get(name), "launches": nl,
-                "avg_launch_us": tot_ms / nl * 1e3, "bytes_per_launch": bytes_per_launch}
-    kernels = {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / max(1e-9, sum(x[1] for x in prof.values()))}
-               for k, v in prof.items()}
-
+    roof = tile_roofline(r["prof"], P, M, args.steps, n_ev, peak, peak_kind)
+    if roof:
+        roof["traffic"] = NCU_TRAFFIC_PER_LAUNCH.get(roof["kernel"])
+    step_bytes = 16 * n_ev + 24 * P + M * P
+    sc = r["sc"]
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded generator, 640x480 blob scene), state FP32, times int64 us",
-        "config": {"workload": WORKLOAD, "events_per_step": n_ev, "frames_per_step": n_windows,
-                   "sensor": f"{sc.W}x{sc.H}", "params": PARAMS,
-                   "l2": "inputs larger than L2 (160 MB of events per step)",
+        "data": "synthetic (seeded generator, 1280x720 checkerboard scene), state FP32, "
+                "times int64 us",
+        "config": {"workload": WORKLOADS[HEADLINE][0], "events_per_step": n_ev,
+                   "frames_per_step": M, "sensor": f"{sc.W}x{sc.H}", "params": r["prm"],
+                   "launch_shape": r["shape"],
+                   "l2": f"inputs larger than L2 ({16 * n_ev / 1e6:.0f} MB of events per step)",
                    "parallelism": f"replicas x{ws}"},
         "frames_per_s": frames_per_s,
         "roofline": roof,
@@ -362,24 +356,30 @@ def bench_esi(args):
                           "achieved_gbs": step_bytes / (ms / args.steps / 1e3) / 1e9,
                           "frac": step_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
                           "note": "16 B/event + S,T read and written once + 1 B/pixel/frame"},
-        "kernels": kernels,
-        "gpu_launches": launches,
-        "clocks": clk,
+        "kernels": kernel_shares(r["prof"]),
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
     }
-
-    if not args.no_extras and rank == 0:
-        line["e2e"] = e2e_leg(esi, torch, h, stream, sc, ev, out, total_steps, args.steps, n_windows)
-        line["latency"] = latency_leg(esi, torch, sc, ev)
-        line["serving"] = serving_leg(esi)
-        line["serving_mixed"] = mixed_serving_leg(esi)
-        line["other_workloads"] = other_workloads_leg(esi, torch)
-        line["diagnostics"] = diagnostics_leg(esi, torch)
+    extras = not args.no_extras and rank == 0
+    if extras:
+        line["e2e"] = e2e_leg(esi, torch, r, args.steps)
     elif not args.no_extras:
         line["e2e"] = None
-    esi.esi_destroy(h)
-    if rank == 0 and not args.no_extras:
-        line["cpu_baseline"] = cpu_baseline(sc, ev)
-        line["cpu_baseline_all_cores"] = cpu_baseline_parallel(sc, ev)
+    esi.esi_destroy(r["handle"])
+    del r
+    if extras:
+        line["other_workloads"] = other_workloads_leg(esi, torch)
+        line["latency"] = latency_leg(esi)
+        sec = args.serving_seconds or SERVING_SECONDS
+        line["serving"] = serving_leg(esi, sec)
+        line["serving_mixed"] = mixed_serving_leg(esi, sec)
+        line["diagnostics"] = diagnostics_leg(esi, torch)
+        # the oracle leg: the oracle timed on the host cores, and its results
+        # against the GPU's on every workload
+        line["cpu_baseline"] = cpu_baseline(HEADLINE)
+        line["cpu_baseline_all_cores"] = cpu_baseline_parallel(HEADLINE)
+        line["parity"] = parity_leg(esi, torch)
+        line["summary"] = summary(line)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -387,60 +387,66 @@ def bench_esi(args):
         print(json.dumps(line), flush=True)
 
 
-def e2e_leg(esi, torch, h, stream, sc, ev, out, k0, steps, n_windows):
+def e2e_leg(esi, torch, r, steps):
     """Steps through the public API with pinned host input and output.
 
     Pipelined (the reported value): each step pushes its events from host
     memory (the call returns once they are on the device) and queues its
     render into a host buffer (out_on_device = 2), so the next step's push
     overlaps this step's render; one esi_synchronize ends the timed region.
-    Synchronous (reported beside it): each render waits for its frames."""
+    Synchronous (reported beside it): each render waits for its frames.
+    Three pinned input buffers are refilled (their times shifted) between
+    the timed runs, outside the timed region."""
+    h, ev, span, win, M, sc = r["handle"], r["ev"], r["span"], r["win"], r["M"], r["sc"]
     n_ev = len(ev)
-    steps = min(steps, 6)   # distinct pinned inputs: 2 x steps + 4 of 160 MB each
-    host_in = []
-    for i in range(2 * steps + 4):
-        buf = torch.empty(n_ev * 16, dtype=torch.uint8, pin_memory=True)
-        buf.numpy().view(ev.dtype)[:] = shifted(ev, k0 + i)
-        host_in.append(buf)
-    host_out = [torch.empty((n_windows, sc.H, sc.W), dtype=torch.uint8, pin_memory=True)
-                for _ in range(2)]
+    k0 = r["total"]
+    nb = 3
+    host_in = [torch.empty(n_ev * 16, dtype=torch.uint8, pin_memory=True) for _ in range(nb)]
+    views = [b.numpy().view(ev.dtype) for b in host_in]
+    host_out = [torch.empty((M, sc.H, sc.W), dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+    k = [k0]
 
-    def step(i, mode):
-        esi.check(esi.esi_push_events(h, host_in[i], n_ev, 0), "push")
-        esi.check(esi.esi_render_frames(h, frame_times(k0 + i, n_windows), n_windows,
-                                        host_out[i % 2], mode), "render")
+    def fill():
+        for i in range(nb):
+            views[i][:] = ev
+            views[i]["t"] += (k[0] + i) * span
 
-    def run(first, mode):
+    def run(mode):
         t0 = time.perf_counter()
-        for i in range(first, first + steps):
-            step(i, mode)
+        for i in range(nb):
+            esi.check(esi.esi_push_events(h, host_in[i], n_ev, 0), "push")
+            esi.check(esi.esi_render_frames(h, frame_times(k[0] + i, span, win), M,
+                                            host_out[i % 2], mode), "render")
         esi.check(esi.esi_synchronize(h), "sync")
-        return time.perf_counter() - t0
+        dt = time.perf_counter() - t0
+        k[0] += nb
+        return dt
 
-    step(0, 0)  # warm, both modes
-    step(1, 2)
-    step(2, 2)
-    esi.check(esi.esi_synchronize(h), "sync")
-    torch.cuda.synchronize()
-    dt = run(3, 2)
-    dt_sync = run(3 + steps, 0)
-    return {"value": n_ev * steps / dt, "unit": "events/s",
-            "h2d_bytes_per_step": n_ev * 16, "d2h_bytes_per_step": n_windows * sc.W * sc.H,
-            "frames_per_s": n_windows * steps / dt,
+    fill()
+    run(2)               # warm
+    fill()
+    dt = run(2)
+    fill()
+    dt_sync = run(0)
+    return {"value": n_ev * nb / dt, "unit": "events/s",
+            "h2d_bytes_per_step": n_ev * 16, "d2h_bytes_per_step": M * sc.W * sc.H,
+            "frames_per_s": M * nb / dt, "steps": nb,
             "mode": "pipelined: push of step k+1 overlaps the render of step k (out_on_device=2)",
-            "synchronous": {"value": n_ev * steps / dt_sync, "unit": "events/s",
+            "synchronous": {"value": n_ev * nb / dt_sync, "unit": "events/s",
                             "mode": "each render waits for its frames (out_on_device=0)"}}
 
 
-def latency_leg(esi, torch, sc, ev):
-    """Plain single-stream path: one 10 ms packet pushed, one frame rendered to host."""
-    rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**PARAMS), 0)
+def latency_leg(esi):
+    """Plain single-stream path on the headline workload: one 10 ms packet
+    pushed from host memory, one frame rendered into host memory."""
+    sc, ev, span, win, prm = workload(HEADLINE)
+    rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**prm), 0)
     esi.check(rc)
     out = np.empty((sc.H, sc.W), dtype=np.uint8)
-    n_windows = DURATION_US // WINDOW_US
-    cuts = np.searchsorted(ev["t"], np.arange(0, n_windows + 1) * WINDOW_US, side="right")
+    n_w = span // WINDOW_US
+    cuts = np.searchsorted(ev["t"], np.arange(0, n_w + 1) * WINDOW_US, side="right")
     lat = []
-    for w in range(n_windows):
+    for w in range(n_w):
         pkt = np.ascontiguousarray(ev[cuts[w]:cuts[w + 1]])
         t0 = time.perf_counter()
         esi.check(esi.esi_push_events(h, pkt, len(pkt), 0))
@@ -448,152 +454,204 @@ def latency_leg(esi, torch, sc, ev):
         lat.append((time.perf_counter() - t0) * 1e3)
     esi.esi_destroy(h)
     lat = np.array(lat[5:])
-    return {"path": "plain: push 10 ms packet (host) + render one frame (host out)",
+    return {"path": "plain: push a 10 ms packet (host) + render one frame (host out), "
+                    "headline workload",
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "frames": int(len(lat))}
 
 
-SERVING_STREAMS = 64
-SERVING_SECONDS = 0.25
+def other_workloads_leg(esi, torch, K=6):
+    """Device-resident throughput of the other single-sensor workloads,
+    measured as the headline (K timed steps after two warm-up steps), with
+    their tile-kernel roofline.  The 346x260 workload also runs with the
+    autotuner's launch shape."""
+    peak, peak_kind = load_peaks()
+    out = {}
+    for name in ("c0", "c1", "c2_1ms"):
+        tunings = [("default", None)]
+        if name == "c0":
+            sc, ev, span, win, prm = workload(name)
+            rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**prm), 0)
+            esi.check(rc, "esi_create")
+            samp = ev[ev["t"] < span // 4]
+            stf = np.arange(1, span // 4 // win + 1, dtype=np.int64) * win
+            rc, t = esi.esi_autotune(h, samp, len(samp), stf, len(stf), 0)
+            esi.check(rc, "autotune")
+            esi.esi_destroy(h)
+            tunings.append(("autotuned", t))
+        res = {"workload": WORKLOADS[name][0]}
+        for mode, tun in tunings:
+            r = device_steps(esi, torch, name, 2, 12 if name == "c0" else K, tuning=tun)
+            esi.esi_destroy(r["handle"])
+            steps = 12 if name == "c0" else K
+            ms = r["ms"] / steps
+            step_bytes = 16 * r["n_ev"] + 24 * r["P"] + r["M"] * r["P"]
+            roof = tile_roofline(r["prof"], r["P"], r["M"], steps, r["n_ev"], peak, peak_kind)
+            res[mode] = {"ms_per_step": ms, "events_per_s": r["n_ev"] / (ms / 1e3),
+                         "frames_per_s": r["M"] / (ms / 1e3),
+                         "step_hbm_frac": step_bytes / (ms / 1e3) / 1e9 / peak,
+                         "dominant": {k: roof[k] for k in ("kernel", "frac", "avg_launch_us")}
+                         if roof else None,
+                         "launch_shape": r["shape"]}
+        res["events_per_step"] = r["n_ev"]
+        res["frames_per_step"] = r["M"]
+        out[name] = res
+    return out
 
 
-def serving_workload(n_streams=SERVING_STREAMS, seconds=SERVING_SECONDS, seed=1003):
-    """64 sinusoid form 346x260 streams, lognormal rates, Poisson packets (1 ms mean)."""
+SERVING_SECONDS = 5.0
+SERVING_PARAMS = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1)
+
+
+def _packets(esi, items):
+    items.sort(key=lambda x: (x[0], x[1], x[2]))
+    pk = (esi.esi_packet * len(items))()
+    for j, (a, _, k, p_, n, kind) in enumerate(items):
+        pk[j].stream, pk[j].kind, pk[j].arrival_us, pk[j].ev, pk[j].n = k, kind, a, p_, n
+    return pk
+
+
+def _event_items(esi, k, ev, arr):
+    items, lo = [], 0
+    cuts = np.searchsorted(ev["t"], arr, side="right")
+    for a, hi in zip(arr.tolist(), cuts.tolist()):
+        items.append((a, 1, k, ev.ctypes.data + lo * 16, hi - lo, esi.ESI_PACKET_EVENTS))
+        lo = hi
+    return items
+
+
+def serving_64(seconds):
+    """The 64-stream workload: (rates, streams with generated events)."""
     import synth
-    rates = synth.lognormal_rates(n_streams, seed)
-    streams = []
-    rng = np.random.default_rng(seed)
-    for i in range(n_streams):
-        sc = synth.serving_stream(i, float(rates[i]), seconds)
-        ev = synth.generate(sc)
-        # Poisson packet arrivals (mean 1 ms); a packet carries the events since the last one
-        gaps = rng.exponential(1000.0, size=int(seconds * 1e6 / 1000) * 3 + 10)
-        arr = np.cumsum(gaps).astype(np.int64) + 1
-        arr = arr[arr < int(seconds * 1e6)]
-        arr = np.append(arr, int(seconds * 1e6))
-        cuts = np.searchsorted(ev["t"], arr, side="right")
-        streams.append((sc.W, sc.H, ev, arr, cuts))
+    rates, streams = synth.serving_streams(64, seconds)
+    for s in streams:
+        s["events"] = synth.generate(s["scene"])
     return rates, streams
 
 
-def build_packets(esi, streams, ids):
-    import ctypes
-    items = []
-    for k, (W, H, ev, arr, cuts) in enumerate(streams):
-        lo = 0
-        base = ev.ctypes.data
-        for a, hi in zip(arr, cuts):
-            items.append((int(a), ids[k], base + lo * 16, int(hi - lo)))
-            lo = int(hi)
-    items.sort(key=lambda x: (x[0], x[1]))
-    pk = (esi.esi_packet * len(items))()
-    for j, (a, sid, ptr_, n) in enumerate(items):
-        pk[j].stream, pk[j].arrival_us, pk[j].ev, pk[j].n = sid, a, ptr_, n
-    return pk, len(items)
+def _stats(st, dt, realtime, n_ev, expected=None):
+    d = {"frames": int(st.frames),
+         "frame_latency_p50_ms": st.frame_latency_p50_ms,
+         "frame_latency_p99_ms": st.frame_latency_p99_ms,
+         "packet_to_frame_p50_ms": st.packet_latency_p50_ms,
+         "packet_to_frame_p99_ms": st.packet_latency_p99_ms,
+         "gpu_ms_per_tick": st.gpu_ms_per_tick,
+         "kernel_launches_per_tick": int(st.kernel_launches_per_tick),
+         "wall_s": dt, "events_per_s": n_ev / dt if not realtime else None,
+         "frames_per_s": st.frames / dt}
+    if expected is not None:
+        d["expected_frames"] = int(expected)
+    return d
 
 
-def serving_leg(esi):
-    """Batched (one graph per tick) vs plain (per-stream launches), wall-clock paced."""
-    rates, streams = serving_workload()
-    t_end = int(SERVING_SECONDS * 1e6)
-    n_ev = int(sum(len(s[2]) for s in streams))
-    params = esi.make_params(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1)
+def serving_leg(esi, seconds=SERVING_SECONDS):
+    """Batched (one graph per tick) vs plain (per-stream launches), paced by
+    the wall clock, and batched as fast as possible: 64 streams of 346x260."""
+    rates, streams = serving_64(seconds)
+    t_end = int(round(seconds * 1e6))
+    n_ev = int(sum(len(s["events"]) for s in streams))
+    params = esi.make_params(**SERVING_PARAMS)
     out = {"workload": f"{len(streams)} streams 346x260 (sinusoid form), lognormal rates "
                        f"{rates.min() / 1e6:.2f}-{rates.max() / 1e6:.2f} Mev/s (median "
                        f"{np.median(rates) / 1e6:.2f}), Poisson packets 1 ms, 100 frames/s, "
-                       f"{SERVING_SECONDS} s", "events": n_ev}
+                       f"{seconds} s", "events": n_ev}
+    expected = len(streams) * (t_end // WINDOW_US)
     for mode in ("batched", "batched_throughput"):
         rc, srv = esi.esi_server_create(1 << 30, None, 0)
         esi.check(rc, "server")
-        ids = []
-        for W, H, *_ in streams:
-            rc, sid = esi.esi_stream_open(srv, W, H, params)
+        items = []
+        for k, s in enumerate(streams):
+            rc, sid = esi.esi_stream_open(srv, s["W"], s["H"], params)
             esi.check(rc, "open")
-            ids.append(sid)
-        pk, npk = build_packets(esi, streams, ids)
+            items += _event_items(esi, sid, s["events"], s["arrivals"])
+        pk = _packets(esi, items)
+        realtime = 1 if mode == "batched" else 0
+        t0 = time.perf_counter()
+        esi.check(esi.esi_server_run(srv, pk, len(items), 1000, t_end, realtime), "run")
+        dt = time.perf_counter() - t0
+        rc, st = esi.esi_server_get_stats(srv)
+        esi.esi_server_destroy(srv)
+        out[mode] = _stats(st, dt, realtime, n_ev, expected)
+    items = []
+    for k, s in enumerate(streams):
+        items += _event_items(esi, k, s["events"], s["arrivals"])
+    pk = _packets(esi, items)
+    t0 = time.perf_counter()
+    rc, st = esi.esi_plain_run([s["W"] for s in streams], [s["H"] for s in streams],
+                               [params] * len(streams), pk, len(items), 1000, t_end, WINDOW_US, 1)
+    esi.check(rc, "plain")
+    out["plain"] = _stats(st, time.perf_counter() - t0, 1, n_ev, expected)
+    return out
+
+
+def mixed_workload(esi, seconds, sinks=False):
+    """Mixed resolutions with join/leave: 16 x 1280x720 (checkerboard form),
+    48 x 640x480 (blob form), 128 x 346x260 (sinusoid form) streams, lognormal
+    rates in [0.1, 20] Mev/s, Poisson packets (1 ms mean), a quarter joining
+    in the first half and a fifth leaving in the second.  Returns the
+    workload, its packets, specs and per-stream events (and frame sinks)."""
+    import ctypes
+    import synth
+    ws = synth.mixed_serving(duration_s=seconds)
+    arrs = synth.mixed_arrivals(ws, duration_s=seconds)
+    t_end = int(round(seconds * 1e6))
+    evs = [synth.generate(w["scene"]) for w in ws]
+    specs, items, sink = [], [], []
+    tile_h = {2: 16, 1: 8, 0: 8}
+    for k, (w, arr) in enumerate(zip(ws, arrs)):
+        sp = esi.esi_stream_spec()
+        sp.width, sp.height = w["W"], w["H"]
+        sp.tile_h = tile_h[w["form"]]
+        sp.params = esi.make_params(**SERVING_PARAMS, t_origin_us=w["t_join_us"])
+        t1 = w["t_leave_us"] if w["t_leave_us"] is not None else t_end
+        if sinks:
+            nf = (t1 - w["t_join_us"]) // WINDOW_US
+            buf = np.zeros((max(nf, 1), w["H"], w["W"]), dtype=np.uint8)
+            tfs = np.zeros(max(nf, 1), dtype=np.int64)
+            sp.frame_sink, sp.sink_frames, sp.sink_t_frames = buf.ctypes.data, nf, tfs.ctypes.data
+            sink.append((buf, tfs, nf))
+        specs.append(sp)
+        items.append((w["t_join_us"], 0, k, ctypes.addressof(sp), 0, esi.ESI_PACKET_OPEN))
+        items += _event_items(esi, k, evs[k], arr)
+        if w["t_leave_us"] is not None:
+            items.append((t1, 2, k, 0, 0, esi.ESI_PACKET_CLOSE))
+    return ws, _packets(esi, items), len(items), specs, evs, sink
+
+
+def mixed_serving_leg(esi, seconds=SERVING_SECONDS):
+    """Mixed-resolution serving: batched, paced by the wall clock, and as
+    fast as possible; 100 frames/s per stream, admission by state memory."""
+    t_end = int(round(seconds * 1e6))
+    ws, pk, npk, specs, evs, _ = mixed_workload(esi, seconds)
+    budget = 768 << 20
+    opts = esi.esi_server_opts()
+    opts.use_graph, opts.max_streams = 1, 256
+    n_ev = int(sum(len(e) for e in evs))
+    expected = sum(((w["t_leave_us"] if w["t_leave_us"] is not None else t_end) - w["t_join_us"])
+                   // WINDOW_US for w in ws)
+    rates = np.array([w["rate"] for w in ws])
+    out = {"workload": "mixed: 16 x 1280x720 + 48 x 640x480 + 128 x 346x260 streams "
+                       f"({sum(w['W'] * w['H'] for w in ws) / 1e6:.1f} M pixels), lognormal rates "
+                       f"{rates.min() / 1e6:.2f}-{rates.max() / 1e6:.2f} Mev/s (sum "
+                       f"{rates.sum() / 1e6:.0f} Mev/s), {sum(w['t_join_us'] > 0 for w in ws)} join "
+                       f"late, {sum(w['t_leave_us'] is not None for w in ws)} leave, Poisson packets "
+                       f"1 ms, 100 frames/s, {seconds} s",
+           "events": n_ev, "state_budget_bytes": budget,
+           "tile_h": "16 rows for 1280x720, 8 for the others"}
+    for mode in ("batched", "batched_throughput"):
+        for sp in specs:
+            sp.stream_id = -1
+        rc, srv = esi.esi_server_create(budget, opts, 0)
+        esi.check(rc, "server")
         realtime = 1 if mode == "batched" else 0
         t0 = time.perf_counter()
         esi.check(esi.esi_server_run(srv, pk, npk, 1000, t_end, realtime), "run")
         dt = time.perf_counter() - t0
         rc, st = esi.esi_server_get_stats(srv)
         esi.esi_server_destroy(srv)
-        out[mode] = {"frames": int(st.frames), "expected_frames": len(streams) * (t_end // 10000),
-                     "frame_latency_p50_ms": st.frame_latency_p50_ms,
-                     "frame_latency_p99_ms": st.frame_latency_p99_ms,
-                     "packet_to_frame_p50_ms": st.packet_latency_p50_ms,
-                     "packet_to_frame_p99_ms": st.packet_latency_p99_ms,
-                     "gpu_ms_per_tick": st.gpu_ms_per_tick,
-                     "kernel_launches_per_tick": int(st.kernel_launches_per_tick),
-                     "wall_s": dt, "events_per_s": n_ev / dt if realtime == 0 else None,
-                     "frames_per_s": st.frames / dt}
-    pk, npk = build_packets(esi, streams, list(range(len(streams))))
-    rc, st = esi.esi_plain_run([s[0] for s in streams], [s[1] for s in streams],
-                               [params] * len(streams), pk, npk, 1000, t_end, 10000, 1)
-    esi.check(rc, "plain")
-    out["plain"] = {"frames": int(st.frames), "frame_latency_p50_ms": st.frame_latency_p50_ms,
-                    "frame_latency_p99_ms": st.frame_latency_p99_ms,
-                    "packet_to_frame_p50_ms": st.packet_latency_p50_ms,
-                    "packet_to_frame_p99_ms": st.packet_latency_p99_ms}
-    return out
-
-
-def other_workloads_leg(esi, torch):
-    """Device-resident throughput of the other single-stream workloads, measured
-    as the main step: K replays of the stream shifted in time, pushed before
-    timing, rendered to device memory, CUDA events on the handle's stream."""
-    import synth
-    peak, _ = load_peaks()
-    out = {}
-    cases = [("sinusoid 346x260, 1 s, ~1 M events, 100 x 10 ms frames", synth.sinusoid_346x260, 10_000, 12),
-             ("checkerboard 1280x720, 1 s, ~50 M events, 100 x 10 ms frames",
-              synth.checkerboard_1280x720, 10_000, 3),
-             ("checkerboard 1280x720, 1 s, ~50 M events, 1000 x 1 ms frames",
-              synth.checkerboard_1280x720, 1_000, 3)]
-    streams = {}
-    for label, make, win, K in cases:
-        if make not in streams:
-            sc = make()
-            streams[make] = (sc, synth.generate(sc))
-        sc, ev = streams[make]
-        n_ev = len(ev)
-        span = int(round(sc.duration_s * 1e6))
-        n_w = span // win
-        prm = dict(PARAMS, C=0.2)
-        P = sc.W * sc.H
-        step_bytes = 16 * n_ev + 24 * P + n_w * P
-        fr = torch.empty((n_w, sc.H, sc.W), dtype=torch.uint8, device="cuda")
-        tfs = [np.arange(1, n_w + 1, dtype=np.int64) * win + k * span for k in range(1 + K)]
-        res = {"events_per_step": n_ev, "frames_per_step": n_w, "steps": K}
-        for mode in ("default", "autotuned"):
-            st = torch.cuda.Stream()
-            rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**prm), st.cuda_stream)
-            esi.check(rc, "esi_create")
-            if mode == "autotuned":
-                # a quarter of the stream as the sample, with its own frame times
-                samp = ev[ev["t"] < span // 4]
-                stf = np.arange(1, span // 4 // win + 1, dtype=np.int64) * win
-                rc, t = esi.esi_autotune(h, samp, len(samp), stf, len(stf), 0)
-                esi.check(rc, "autotune")
-                res["autotuned_shape"] = {f: getattr(t, f) for f in (
-                    "tile_w", "tile_h", "chunk_events", "batch_records", "max_batch_events")}
-            for k in range(1 + K):
-                e = ev.copy()
-                e["t"] += k * span
-                esi.check(esi.esi_push_events(h, e, n_ev, 0), "push")
-            esi.check(esi.esi_render_frames(h, tfs[0], n_w, fr, 1), "render")
-            esi.check(esi.esi_synchronize(h), "sync")
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            for k in range(1, 1 + K):
-                esi.check(esi.esi_render_frames(h, tfs[k], n_w, fr, 1), "render")
-            e1.record(st)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / K
-            esi.esi_destroy(h)
-            res[mode] = {"ms_per_step": ms, "events_per_s": n_ev / (ms / 1e3),
-                         "frames_per_s": n_w / (ms / 1e3),
-                         "step_hbm_frac": step_bytes / (ms / 1e3) / 1e9 / peak}
-        out[label] = res
+        out[mode] = _stats(st, dt, realtime, n_ev, expected)
+        out[mode]["streams_admitted"] = int(st.streams_admitted)
+        out[mode]["streams_refused"] = int(st.streams_refused)
     return out
 
 
@@ -601,8 +659,8 @@ def diagnostics_leg(esi, torch, reps=5):
     """Fig. 4 diagnostics: per-pixel event counts of the 1280x720 checkerboard's 1 s stream
     (events and counts on the device) and the noise map ln(1 + |S|) of a
     4000x3000 state.  Each launch is timed by the library's CUDA events on
-    the handle's stream, with a 256 MB write before it to flush L2."""
-    import synth
+    the handle's stream, with a 256 MB write before it to flush L2; per-event
+    states of the 640x480 blob stream."""
     peak, _ = load_peaks()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     out = {}
@@ -620,11 +678,10 @@ def diagnostics_leg(esi, torch, reps=5):
         nl, tot = prof[kind]
         return tot / nl
 
-    sc = synth.checkerboard_1280x720()
-    ev = synth.generate(sc)
+    sc, ev, _, _, prm = workload("c2")
     n = len(ev)
     st = torch.cuda.Stream()
-    rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**PARAMS), st.cuda_stream)
+    rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**prm), st.cuda_stream)
     esi.check(rc, "esi_create")
     dev_ev = torch.from_numpy(ev.view(np.uint8)).cuda()
     counts = torch.empty(sc.W * sc.H, dtype=torch.int32, device="cuda")
@@ -635,15 +692,15 @@ def diagnostics_leg(esi, torch, reps=5):
                            "events_per_s": n / (ms / 1e3), "achieved_gbs": gbs,
                            "frac": gbs / peak, "bytes": "16 B per event read"}
     del dev_ev, counts
-    # continuous-time output: S after every event of the main step's stream
-    sc1, ev1 = make_stream()
+    # continuous-time output: S after every event of the 640x480 stream
+    sc1, ev1, span1, _, prm1 = workload("c1")
     n1 = len(ev1)
-    rc, h = esi.esi_create(sc1.W, sc1.H, esi.make_params(**PARAMS), st.cuda_stream)
+    rc, h = esi.esi_create(sc1.W, sc1.H, esi.make_params(**prm1), st.cuda_stream)
     esi.check(rc, "esi_create")
     vals = torch.empty(n1, dtype=torch.float32, device="cuda")
     steps = []
     for k in range(1 + reps):
-        esi.check(esi.esi_push_events(h, shifted(ev1, k), n1, 0), "push")
+        esi.check(esi.esi_push_events(h, shifted(ev1, k * span1), n1, 0), "push")
         with torch.cuda.stream(st):
             flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -672,132 +729,260 @@ def diagnostics_leg(esi, torch, reps=5):
     return out
 
 
-MIXED_SECONDS = 0.25
+# --------------------------------------------------------------- oracle leg
+def cpu_baseline(name, budget_s: float = 12.0):
+    """The oracle as it stands on one host core: whole-stream replays until budget_s."""
+    import oracle
+    sc, ev, span, win, prm = workload(name)
+    reps, used, t0 = 0, 0, time.perf_counter()
+    tf = frame_times(0, span, win)
+    while True:
+        st = oracle.OracleState(sc.W, sc.H, oracle.OracleParams(**prm))
+        _, u = st.replay(ev, tf)
+        used += u
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s or reps >= 8:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": used / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} replay(s) of the whole {span / 1e6:g} s stream ({len(ev)} events, "
+                      f"{len(tf)} frames each), {dt:.1f} s"}
 
 
-def mixed_serving_leg(esi, seconds=MIXED_SECONDS, seed=1004):
-    """Mixed resolutions with join/leave: 16 x 1280x720 (checkerboard form), 48 x
-    640x480 (blob form), 128 x 346x260 (sinusoid form) streams, lognormal
-    rates in [0.1, 20] Mev/s, Poisson packets (1 ms mean), a quarter joining in
-    the first half and a fifth leaving in the second, admission by state
-    memory, tile height autotuned per sensor size, 100 frames/s per stream."""
-    import ctypes
-    import synth
-    ws = synth.mixed_serving(duration_s=seconds, seed=seed)
-    t_end = int(round(seconds * 1e6))
-    rng = np.random.default_rng(seed + 1)
-    evs = [synth.generate(w["scene"]) for w in ws]
-    params = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1)
-    budget = 768 << 20
-    opts = esi.esi_server_opts()
-    opts.use_graph, opts.max_streams = 1, 256
+def _oracle_band(job):
+    """Worker: the oracle over the events of one band of rows (pixels of
+    different bands never interact, Eq. 5), timed inside the worker."""
+    band, n_bands, path, W, H, prm, tf = job
+    import oracle
+    ev = np.load(path, mmap_mode="r")
+    y0, y1 = band * H // n_bands, (band + 1) * H // n_bands
+    sel = np.array(ev[(ev["y"] >= y0) & (ev["y"] < y1)])
+    sel["y"] -= y0     # the band as a sensor of its own: only its pixels render
+    st = oracle.OracleState(W, y1 - y0, oracle.OracleParams(**prm))
+    t0 = time.perf_counter()
+    _, used = st.replay(sel, tf)
+    return used, time.perf_counter() - t0
 
-    # autotuned tile height per sensor size, on 50 ms of its median-rate stream
-    tile_h = {}
-    rc, srv = esi.esi_server_create(budget, opts, 0)
-    esi.check(rc, "server")
-    for dims in sorted({(w["W"], w["H"]) for w in ws}):
-        idx = [i for i, w in enumerate(ws) if (w["W"], w["H"]) == dims]
-        med = sorted(idx, key=lambda i: ws[i]["rate"])[len(idx) // 2]
-        ev = evs[med]
-        samp = ev[ev["t"] < ws[med]["t_join_us"] + 50_000]
-        rc, sid = esi.esi_stream_open(srv, dims[0], dims[1], esi.make_params(**params))
-        esi.check(rc, "open")
-        rc, th = esi.esi_stream_autotune(srv, sid, samp, len(samp), 0)
-        esi.check(rc, "autotune")
-        tile_h[f"{dims[0]}x{dims[1]}"] = th
-        esi.check(esi.esi_stream_close(srv, sid), "close")
-    esi.esi_server_destroy(srv)
 
-    specs = []
-    items = []
-    for k, w in enumerate(ws):
-        sp = esi.esi_stream_spec()
-        sp.width, sp.height = w["W"], w["H"]
-        sp.tile_h = tile_h[f"{w['W']}x{w['H']}"]
-        sp.params = esi.make_params(**params, t_origin_us=w["t_join_us"])
-        specs.append(sp)
-        t0, t1 = w["t_join_us"], w["t_leave_us"] if w["t_leave_us"] is not None else t_end
-        items.append((t0, 0, k, ctypes.addressof(sp), 0, esi.ESI_PACKET_OPEN))
-        gaps = rng.exponential(1000.0, size=int((t1 - t0) / 1000) * 3 + 10)
-        arr = t0 + np.cumsum(gaps).astype(np.int64) + 1
-        arr = np.append(arr[arr < t1], t1)
-        ev = evs[k]
-        cuts = np.searchsorted(ev["t"], arr, side="right")
-        lo = 0
-        for a, hi in zip(arr.tolist(), cuts.tolist()):
-            items.append((a, 1, k, ev.ctypes.data + lo * 16, hi - lo, esi.ESI_PACKET_EVENTS))
-            lo = hi
-        if w["t_leave_us"] is not None:
-            items.append((t1, 2, k, 0, 0, esi.ESI_PACKET_CLOSE))
-    items.sort(key=lambda x: (x[0], x[1], x[2]))
-    pk = (esi.esi_packet * len(items))()
-    for j, (a, _, k, p_, n, kind) in enumerate(items):
-        pk[j].stream, pk[j].kind, pk[j].arrival_us, pk[j].ev, pk[j].n = k, kind, a, p_, n
-    n_ev = int(sum(len(e) for e in evs))
-    expected = sum(((w["t_leave_us"] if w["t_leave_us"] is not None else t_end) - w["t_join_us"])
-                   // 10_000 for w in ws)
-    rates = np.array([w["rate"] for w in ws])
-    out = {"workload": "mixed: 16 x 1280x720 + 48 x 640x480 + 128 x 346x260 streams "
-                       f"({sum(w['W'] * w['H'] for w in ws) / 1e6:.1f} M pixels), lognormal rates "
-                       f"{rates.min() / 1e6:.2f}-{rates.max() / 1e6:.2f} Mev/s (sum "
-                       f"{rates.sum() / 1e6:.0f} Mev/s), {sum(w['t_join_us'] > 0 for w in ws)} join "
-                       f"late, {sum(w['t_leave_us'] is not None for w in ws)} leave, Poisson packets "
-                       f"1 ms, 100 frames/s, {seconds} s",
-           "events": n_ev, "expected_frames": int(expected), "state_budget_bytes": budget,
-           "autotuned_tile_h": tile_h}
-    for mode in ("batched", "batched_throughput"):
-        for sp in specs:
-            sp.stream_id = -1
-        rc, srv = esi.esi_server_create(budget, opts, 0)
-        esi.check(rc, "server")
-        realtime = 1 if mode == "batched" else 0
-        t0 = time.perf_counter()
-        esi.check(esi.esi_server_run(srv, pk, len(items), 1000, t_end, realtime), "run")
-        dt = time.perf_counter() - t0
-        rc, st = esi.esi_server_get_stats(srv)
-        esi.esi_server_destroy(srv)
-        out[mode] = {"frames": int(st.frames), "events": int(st.events),
-                     "streams_admitted": int(st.streams_admitted),
-                     "streams_refused": int(st.streams_refused),
-                     "frame_latency_p50_ms": st.frame_latency_p50_ms,
-                     "frame_latency_p99_ms": st.frame_latency_p99_ms,
-                     "packet_to_frame_p50_ms": st.packet_latency_p50_ms,
-                     "packet_to_frame_p99_ms": st.packet_latency_p99_ms,
-                     "gpu_ms_per_tick": st.gpu_ms_per_tick,
-                     "kernel_launches_per_tick": int(st.kernel_launches_per_tick),
-                     "wall_s": dt, "events_per_s": n_ev / dt if realtime == 0 else None,
-                     "frames_per_s": st.frames / dt}
+def cpu_baseline_parallel(name):
+    """The same oracle on every host core: one process per band of rows
+    (spawned, so no CUDA state is inherited); throughput = all events / the
+    slowest band's compute time."""
+    import multiprocessing as mp
+    sc, ev, span, win, prm = workload(name)
+    tf = frame_times(0, span, win)
+    cores = os.cpu_count() or 1
+    fd, path = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    try:
+        np.save(path, ev)
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_band, [(b, cores, path, sc.W, sc.H, prm, tf)
+                                          for b in range(cores)])
+    finally:
+        os.unlink(path)
+    used = sum(r[0] for r in res)
+    slowest = max(r[1] for r in res)
+    return {"value": used / slowest, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "sample": f"the whole {span / 1e6:g} s stream ({used} events, {len(tf)} frames) split "
+                      f"into {cores} bands of rows, one process each; {slowest:.2f} s for the "
+                      f"slowest band"}
+
+
+class ParityAcc:
+    """Maximum errors of GPU results against the oracle's, for one workload:
+    state error |dS| / max(|S_ref|, C) (the tests' bar, 1e-5) and with the
+    floor 1e-3 C, T exactness, frame LSB differences."""
+
+    def __init__(self):
+        self.err_c = self.err_mc = 0.0
+        self.t_exact = True
+        self.lsb = self.off = self.frames = self.pixels = 0
+
+    def state(self, S, T, S_ref, T_ref, C):
+        d = np.abs(np.asarray(S, np.float64) - S_ref)
+        if d.size:
+            self.err_c = max(self.err_c, float(np.max(d / np.maximum(np.abs(S_ref), C))))
+            self.err_mc = max(self.err_mc, float(np.max(d / np.maximum(np.abs(S_ref), 1e-3 * C))))
+        self.t_exact &= bool(np.array_equal(T, T_ref))
+        self.pixels += int(d.size)
+
+    def frames_(self, got, ref):
+        d = np.abs(got.astype(np.int16) - ref.astype(np.int16))
+        if d.size:
+            self.lsb = max(self.lsb, int(d.max()))
+            self.off += int(np.count_nonzero(d))
+        self.frames += int(got.shape[0]) if got.ndim == 3 else 1
+
+    def out(self):
+        return {"state_err": self.err_c, "state_err_floor_1e-3C": self.err_mc,
+                "T_exact": self.t_exact, "frame_max_lsb": self.lsb,
+                "frame_off_by_one": self.off, "frames": self.frames, "pixels": self.pixels,
+                "pass": self.err_c <= 1e-5 and self.t_exact and self.lsb <= 1}
+
+
+def parity_leg(esi, torch):
+    """The GPU's frames and final state against the FP64 oracle's on every
+    workload: the single-sensor ones rendered in one call (the headline's
+    launch shape), the 64-stream and the mixed serving workloads served by the
+    executor as fast as possible with every frame kept (0.25 s of stream
+    time), each stream against the oracle run on it alone."""
+    import oracle
+    out = {}
+    for name in ("c0", "c1", "c2", "c2_1ms"):
+        sc, ev, span, win, prm = workload(name)
+        tf = frame_times(0, span, win)
+        rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**prm), 0)
+        esi.check(rc, "esi_create")
+        esi.check(esi.esi_push_events(h, ev, len(ev), 0), "push")
+        fr = torch.empty((len(tf), sc.H, sc.W), dtype=torch.uint8, device="cuda")
+        esi.check(esi.esi_render_frames(h, tf, len(tf), fr, 1), "render")
+        S = np.empty(sc.W * sc.H, dtype=np.float32)
+        T = np.empty(sc.W * sc.H, dtype=np.int64)
+        esi.check(esi.esi_get_state(h, S, T, 0), "state")
+        esi.esi_destroy(h)
+        # 1 ms frames: every 10th frame is compared (the oracle renders only
+        # those; its state passes through the same events either way)
+        every = 10 if len(tf) > 200 else 1
+        got = fr[::every].cpu().numpy()
+        del fr
+        ref = oracle.OracleState(sc.W, sc.H, oracle.OracleParams(**prm))
+        ref_frames, _ = ref.replay(ev, tf[::every])
+        acc = ParityAcc()
+        acc.state(S, T, ref.S, ref.T, prm["C"])
+        acc.frames_(got, ref_frames)
+        out[name] = acc.out()
+        del got, ref_frames
+    out["c3"] = _parity_serving_64(esi, oracle)
+    out["c4"] = _parity_mixed(esi, oracle)
     return out
 
 
+def _parity_serving_64(esi, oracle, seconds=0.25):
+    rates, streams = serving_64(seconds)
+    t_end = int(round(seconds * 1e6))
+    nf = t_end // WINDOW_US
+    params = esi.make_params(**SERVING_PARAMS)
+    rc, srv = esi.esi_server_create(1 << 30, None, 0)
+    esi.check(rc, "server")
+    items, sinks, ids = [], [], []
+    for s in streams:
+        rc, sid = esi.esi_stream_open(srv, s["W"], s["H"], params)
+        esi.check(rc, "open")
+        buf = np.zeros((nf, s["H"], s["W"]), dtype=np.uint8)
+        tfs = np.zeros(nf, dtype=np.int64)
+        esi.check(esi.esi_stream_set_frame_sink(srv, sid, buf, nf, tfs), "sink")
+        sinks.append((buf, tfs))
+        ids.append(sid)
+        items += _event_items(esi, sid, s["events"], s["arrivals"])
+    pk = _packets(esi, items)
+    esi.check(esi.esi_server_run(srv, pk, len(items), 1000, t_end, 0), "run")
+    acc = ParityAcc()
+    for s, sid, (buf, tfs) in zip(streams, ids, sinks):
+        S = np.empty(s["W"] * s["H"], dtype=np.float32)
+        T = np.empty(s["W"] * s["H"], dtype=np.int64)
+        esi.check(esi.esi_stream_state(srv, sid, S, T), "state")
+        tf = np.arange(1, nf + 1, dtype=np.int64) * WINDOW_US
+        ok_t = np.array_equal(tfs, tf)
+        ref = oracle.OracleState(s["W"], s["H"], oracle.OracleParams(**SERVING_PARAMS))
+        ev = s["events"]
+        ref_frames, used = ref.replay(ev, tf)
+        ref.integrate(ev[used:])
+        acc.state(S, T, ref.S, ref.T, SERVING_PARAMS["C"])
+        acc.frames_(buf, ref_frames)
+        acc.t_exact &= ok_t
+    esi.esi_server_destroy(srv)
+    r = acc.out()
+    r["streams"] = len(streams)
+    return r
+
+
+def _parity_mixed(esi, oracle, seconds=0.25):
+    t_end = int(round(seconds * 1e6))
+    ws, pk, npk, specs, evs, sinks = mixed_workload(esi, seconds, sinks=True)
+    opts = esi.esi_server_opts()
+    opts.use_graph, opts.max_streams = 1, 256
+    rc, srv = esi.esi_server_create(768 << 20, opts, 0)
+    esi.check(rc, "server")
+    esi.check(esi.esi_server_run(srv, pk, npk, 1000, t_end, 0), "run")
+    acc = ParityAcc()
+    for w, sp, ev, (buf, tfs, nf) in zip(ws, specs, evs, sinks):
+        t0 = w["t_join_us"]
+        tf = t0 + np.arange(1, nf + 1, dtype=np.int64) * WINDOW_US
+        acc.t_exact &= bool(np.array_equal(tfs[:nf], tf))
+        prm = dict(SERVING_PARAMS, t_origin_us=t0)
+        ref = oracle.OracleState(w["W"], w["H"], oracle.OracleParams(**prm))
+        ref_frames, used = ref.replay(ev, tf)
+        acc.frames_(buf[:nf], ref_frames)
+        if sp.stream_id >= 0:       # still open: its state too
+            S = np.empty(w["W"] * w["H"], dtype=np.float32)
+            T = np.empty(w["W"] * w["H"], dtype=np.int64)
+            esi.check(esi.esi_stream_state(srv, sp.stream_id, S, T), "state")
+            ref.integrate(ev[used:])
+            acc.state(S, T, ref.S, ref.T, prm["C"])
+    esi.esi_server_destroy(srv)
+    r = acc.out()
+    r["streams"] = len(ws)
+    r["left"] = sum(w["t_leave_us"] is not None for w in ws)
+    return r
+
+
+def summary(line):
+    """The numbers to read first, compact (the line's last key)."""
+    def g(x, nd=3):
+        return None if x is None else round(x / 1e9, nd)
+
+    def lat(d):
+        return [round(d[k], 3) for k in ("frame_latency_p50_ms", "frame_latency_p99_ms",
+                                          "packet_to_frame_p50_ms", "packet_to_frame_p99_ms")]
+    s = {"Gev_s": {HEADLINE: g(line["value"])},
+         "tile_frac": {HEADLINE: round(line["roofline"]["frac"], 4) if line.get("roofline") else None},
+         "step_frac": {HEADLINE: round(line["step_roofline"]["frac"], 4)},
+         "e2e_Gev_s": g(line["e2e"]["value"]) if line.get("e2e") else None}
+    for name, r in (line.get("other_workloads") or {}).items():
+        s["Gev_s"][name] = g(r["default"]["events_per_s"])
+        s["step_frac"][name] = round(r["default"]["step_hbm_frac"], 4)
+        if r["default"].get("dominant"):
+            s["tile_frac"][name] = round(r["default"]["dominant"]["frac"], 4)
+    sv = {}
+    for key, tag in (("serving", "c3"), ("serving_mixed", "c4")):
+        d = line.get(key)
+        if not d:
+            continue
+        e = {"lat_ms(f50,f99,p50,p99)": {m: lat(d[m]) for m in ("batched", "plain") if m in d},
+             "frames": f"{d['batched']['frames']}/{d['batched'].get('expected_frames')}",
+             "max_Gev_s": g(d["batched_throughput"]["events_per_s"])}
+        sv[tag] = e
+    s["serving"] = sv
+    s["parity(err,err1e-3C,lsb,off,frames)"] = {
+        k: [float(f"{v['state_err']:.2e}"), float(f"{v['state_err_floor_1e-3C']:.2e}"),
+            v["frame_max_lsb"], v["frame_off_by_one"], v["frames"]]
+        for k, v in (line.get("parity") or {}).items()}
+    return s
+
+
 def ncu_case():
-    """A small case of the same launch shape for kernel captures: 0.8 s of the
-    640x480 blob stream (about 4 M events, 64 MB, one sub-batch per render as in
-    the bench), 80 frames per render, three renders."""
+    """A small case of the headline's launch shape for kernel captures: the
+    first 0.25 s of the 1280x720 stream (about 12 M events, 200 MB, three
+    4 M-event sub-batches per render as in the bench), 25 frames per render,
+    three renders."""
     import torch  # noqa: F401  (CUDA context as in the bench)
     import synth
     from paper_2508_02238_gb300 import esi
-    sc = synth.blobs_640x480(duration_s=0.8)
+    sc = synth.checkerboard_1280x720(duration_s=0.25)
     ev = synth.generate(sc)
-    span = 800_000
+    span = 250_000
     rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**PARAMS), 0)
     esi.check(rc, "create")
-    out = torch.empty((80, sc.H, sc.W), dtype=torch.uint8, device="cuda")
+    out = torch.empty((25, sc.H, sc.W), dtype=torch.uint8, device="cuda")
     for k in range(3):
-        esi.check(esi.esi_push_events(h, _shift(ev, k * span), len(ev), 0))
+        esi.check(esi.esi_push_events(h, shifted(ev, k * span), len(ev), 0))
     for k in range(3):
-        tf = np.arange(1, 81, dtype=np.int64) * WINDOW_US + k * span
-        esi.check(esi.esi_render_frames(h, tf, 80, out, 1), "render")
+        tf = np.arange(1, 26, dtype=np.int64) * WINDOW_US + k * span
+        esi.check(esi.esi_render_frames(h, tf, 25, out, 1), "render")
     esi.check(esi.esi_synchronize(h))
     esi.esi_destroy(h)
     print(f"ncu case done: {len(ev)} events x 3 renders")
-
-
-def _shift(ev, dt):
-    e = ev.copy()
-    e["t"] += dt
-    return e
 
 
 def main():
@@ -805,18 +990,19 @@ def main():
     if args.ncu_case:
         ncu_case()
         return
-    if args.diagnostics_only:
+    if args.diagnostics_only or args.serving_only or args.parity_only:
         import torch
         from paper_2508_02238_gb300 import esi
         esi.load_library(build_if_missing=True)
-        print(json.dumps({"diagnostics": diagnostics_leg(esi, torch)}), flush=True)
-        return
-    if args.serving_only:
-        import torch  # noqa: F401  (CUDA context as in the bench)
-        from paper_2508_02238_gb300 import esi
-        esi.load_library(build_if_missing=True)
-        print(json.dumps({"serving": serving_leg(esi), "serving_mixed": mixed_serving_leg(esi)}),
-              flush=True)
+        torch.cuda.set_device(0)
+        if args.diagnostics_only:
+            print(json.dumps({"diagnostics": diagnostics_leg(esi, torch)}), flush=True)
+        elif args.serving_only:
+            sec = args.serving_seconds or SERVING_SECONDS
+            print(json.dumps({"serving": serving_leg(esi, sec),
+                              "serving_mixed": mixed_serving_leg(esi, sec)}), flush=True)
+        else:
+            print(json.dumps({"parity": parity_leg(esi, torch)}), flush=True)
         return
     if args.impl == "reference":
         bench_reference(args)

@@ -236,6 +236,36 @@ int esi_noise_map(esi_handle *h, float *out, int out_on_device);
 int esi_count_events(esi_handle *h, const esi_event *events, size_t n, int events_on_device,
                      uint32_t *counts, int counts_on_device);
 
+/*
+ * Inspection of the render's first sorting level.  Alg. 2 applies events in
+ * stream order; on the GPU a render first reorders them by pixel, which is
+ * legal because a pixel's state depends only on its own events in time order
+ * (Eq. 5, Sec. III-B), and the sort must be stable to keep that order.  This
+ * call runs the render's binning kernel alone: events first .. first + n - 1
+ * of a device ring of ring_capacity events (a power of two, index i at
+ * ring[i % ring_capacity], 16-byte aligned; n <= ring_capacity) are cut into
+ * chunks of shape->chunk_events consecutive events, and each chunk's records
+ * are stably sorted by pixel tile (shape->tile_w x shape->tile_h pixels;
+ * zeros take 128 x 8 and 2048-event chunks).  Output, device buffers owned by
+ * the caller:
+ *   records  ceil(n / chunk) * chunk uint64; chunk c's records start at
+ *            c * chunk: record = (t - t_base) mod 2^32 in the low 32 bits,
+ *            ((row_in_tile * tile_w + x_in_tile) << 1 | (p > 0)) in the high
+ *            32 bits; events outside the sensor are left out, so the chunk's
+ *            valid records are its first (events - dropped) slots.
+ *   runs     [tile][chunk] uint32, tiles row-major over the sensor (tile
+ *            index (y / tile_h) * ceil(W / tile_w) + x / tile_w): the tile's
+ *            records in the chunk start at (runs >> 16) and number
+ *            (runs & 0xffff).
+ * *dropped (may be NULL) receives the count of events outside the sensor.
+ * Waits for the result.  Errors: ESI_EINVAL (sizes, shape, pointers),
+ * ESI_ERANGE (more tiles than the binning holds), ESI_ENOMEM, ESI_ECUDA,
+ * ESI_ETIMEOUT (a bounded device wait gave up).
+ */
+int esi_bin_events(int width, int height, const esi_tuning *shape, const esi_event *ring,
+                   uint64_t ring_capacity, uint64_t first, size_t n, int64_t t_base,
+                   uint64_t *records, uint32_t *runs, uint64_t *dropped, void *cuda_stream);
+
 /* Counters; waits for queued work so that the drop count is exact. */
 int esi_get_stats(esi_handle *h, esi_stats *out);
 
@@ -364,6 +394,24 @@ int esi_server_tick(esi_server *srv, int64_t now_us);
 int esi_stream_frame(esi_server *srv, int stream_id, uint8_t *out, int64_t *t_frame,
                      double *latency_ms);
 
+/* Frames by number, for callers that read less often than frames finish:
+ * frame seq (0, 1, ... in frame-time order) of a stream is held until frame
+ * seq + frame_slots is handed to a tick.  esi_stream_frames_done writes the
+ * number of the stream's finished frames; esi_stream_frame_seq copies frame
+ * seq (W * H bytes) into the host buffer out and its time into *t_frame (may
+ * be NULL): ESI_ESTATE if it has not finished, ESI_ERANGE if its slot has
+ * been reused. */
+int esi_stream_frames_done(esi_server *srv, int stream_id, uint64_t *n_done);
+/* Keep every frame: from now on, each finished frame seq < max_frames of the
+ * stream is also copied by the host, when its tick is seen finished, to
+ * out + seq * W * H (a host buffer of max_frames * W * H bytes), and its time
+ * to t_frames[seq] (may be NULL).  max_frames = 0 removes the sink.  The
+ * buffers must stay valid until the stream closes or the sink is removed. */
+int esi_stream_set_frame_sink(esi_server *srv, int stream_id, uint8_t *out,
+                              uint64_t max_frames, int64_t *t_frames);
+int esi_stream_frame_seq(esi_server *srv, int stream_id, uint64_t seq, uint8_t *out,
+                         int64_t *t_frame);
+
 /* Tile height (4, 8 or 16 rows of 128 pixels) of one stream's work items
  * from the next tick on; the state layout does not depend on it.  ESI_ERANGE
  * when the stream would have more tiles than the server's tables hold. */
@@ -414,6 +462,9 @@ typedef struct {
     int32_t stream_id;    /* out: the server stream id while it is open, -1
                              once refused admission or closed               */
     esi_params params;    /* frames at params.t_origin_us + k * frame period   */
+    uint8_t *frame_sink;  /* NULL, or a frame sink as esi_stream_set_frame_sink */
+    uint64_t sink_frames;
+    int64_t *sink_t_frames;
 } esi_stream_spec;
 
 /*
@@ -468,15 +519,23 @@ int esi_plain_run(int n_streams, const int *widths, const int *heights,
  * the kernels' shared-memory limits, with that device current); make that
  * first call before any stream capture.  All calls share the array, so calls
  * that overlap on the GPU (other streams, other host threads) race and must
- * be serialised by the caller.  The call waits for its own work.
+ * be serialised by the caller.  Each call synchronises the stream it is
+ * given (it reads the device-side checks back) before it returns.
  *
  * Inputs and outputs, all owned by the caller:
- *   events    device array of n events, non-decreasing in time, none later
- *             than t_frames[m-1] (ESI_EINVAL) or earlier than its pixel's T
+ *   events    device array of n events, 16-byte aligned (ESI_EINVAL
+ *             otherwise: the events are staged by 16-byte bulk copies),
+ *             non-decreasing in time (ESI_ETIMEORDER), none later than
+ *             t_frames[m-1] (ESI_EINVAL) or earlier than its pixel's T
  *             (ESI_ETIMEORDER); out-of-range pixels are skipped.  n may be 0.
+ *             An input error is found before any state changes: S, T and
+ *             frames are then left as they were.
  *   t_frames  host array of m non-decreasing frame times.
- *   S, T      device arrays of W * H float32 / int64: the state, read and
- *             updated in place (start from S = 0, T = t_origin).
+ *   S, T      device arrays of W * H float32 / int64 with their natural
+ *             alignment (ESI_EINVAL otherwise): the state, read and updated
+ *             in place (start from S = 0, T = t_origin).  When S and T are
+ *             16-byte aligned and W % 4 == 0 (and frames 4-byte aligned) the
+ *             kernels move four pixels per access; otherwise one at a time.
  *   frames    device array of m * W * H bytes, frame w at offset w * W * H.
  * Limits (ESI_ERANGE beyond them): n <= 1048576 events, m <= 4096 frames,
  * ceil(W / 128) * ceil(H / 8) <= 2048 pixel tiles, and the last event at

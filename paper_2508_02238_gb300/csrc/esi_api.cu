@@ -177,8 +177,10 @@ static int ensure_ring(esi_handle *h, unsigned long long need)
     esi_event *nr = nullptr;
     cudaError_t e = cudaMalloc((void **)&nr, nc * sizeof(esi_event));
     if (e != cudaSuccess) return cuda_fail(h, e);
+    // the full time mirror (8 B per slot) exists only once a small host push
+    // has used it (esi_push_events allocates it then)
     long long *nm = nullptr, *ns = nullptr;
-    e = cudaMallocHost((void **)&nm, nc * sizeof(long long));
+    if (h->tmirror) e = cudaMallocHost((void **)&nm, nc * sizeof(long long));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ns, nc / kSparse * sizeof(long long));
     if (e != cudaSuccess) {
         cudaFree(nr);
@@ -197,7 +199,7 @@ static int ensure_ring(esi_handle *h, unsigned long long need)
             cudaFreeHost(ns);
             return cuda_fail(h, e);
         }
-        std::memcpy(&nm[pn], &h->tmirror[po], len * sizeof(long long));
+        if (nm) std::memcpy(&nm[pn], &h->tmirror[po], len * sizeof(long long));
         a += len;
     }
     // the sparse times of the pending events (and of the block holding head)
@@ -594,6 +596,13 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
             i += len;
         }
     };
+    if (!ev_on_device && n <= kHostCheckMax && !h->tmirror) {
+        e = cudaMallocHost((void **)&h->tmirror, h->cap * sizeof(long long));
+        if (e != cudaSuccess) {
+            h->tmirror = nullptr;
+            return cuda_fail(h, e);
+        }
+    }
     if (!ev_on_device && n <= kHostCheckMax) {
         // the copy starts first; the time-order check and the host mirror of
         // the times run meanwhile (a rejected batch leaves ring slots past

@@ -110,6 +110,11 @@ extern "C" int esi_render_frames_noalloc(int width, int height, const esi_params
     int rc = validate_params(width, height, params);
     if (rc) return rc;
     if ((n && !events) || !t_frames || m == 0 || !S || !T || !frames) return ESI_EINVAL;
+    // the binning stages events with 16-byte bulk copies (TMA), whose global
+    // source must be 16-byte aligned; S and T need their natural alignment
+    if (n && (reinterpret_cast<uintptr_t>(events) & 15u)) return ESI_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(S) & 3u) || (reinterpret_cast<uintptr_t>(T) & 7u))
+        return ESI_EINVAL;
     if (n > (size_t)kNaMaxEvents || m > (size_t)kNaMaxFrames) return ESI_ERANGE;
     const int tiles_x = (width + kTileW - 1) / kTileW;
     const int n_tiles = tiles_x * ((height + kNaTileH - 1) / kNaTileH);
@@ -208,11 +213,15 @@ extern "C" int esi_render_frames_noalloc(int width, int height, const esi_params
     ta.w_begin = 0;
     ta.w_end = (int)m;
     ta.frames = frames;
-        ta.frame_outs = nullptr;
+    ta.frame_outs = nullptr;
     ta.P = (long long)width * height;
     ta.batch = kNaBatch;
     ta.status = st;
-    const bool vec = (width % 4 == 0) && ((reinterpret_cast<uintptr_t>(frames) & 3u) == 0);
+    // the vector tile path moves a lane's four pixels as one float4 of S, two
+    // 16-byte words of T and one 32-bit frame word: it needs S and T 16-byte
+    // aligned and frames 4-byte aligned; otherwise the scalar path runs
+    const bool vec = (width % 4 == 0) && ((reinterpret_cast<uintptr_t>(frames) & 3u) == 0) &&
+                     (((reinterpret_cast<uintptr_t>(S) | reinterpret_cast<uintptr_t>(T)) & 15u) == 0);
     rc = cuda_rc(launch_tile(ta, kNaTileH, kTileW, vec, s));
     if (rc) return rc;
     rc = cuda_rc(cudaMemcpyAsync(&hs, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));

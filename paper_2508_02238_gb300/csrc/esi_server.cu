@@ -120,6 +120,10 @@ struct Stream {
     unsigned long long seq_done = 0;      // frames finished
     std::vector<long long> slot_t;
     std::vector<double> slot_lat;
+    // optional caller buffer that keeps every finished frame (by number)
+    unsigned char *sink = nullptr;
+    unsigned long long sink_n = 0;
+    long long *sink_t = nullptr;
 };
 
 struct TickFrame {
@@ -250,6 +254,11 @@ void poll(esi_server *s)
             st.slot_t[slot] = f.t_frame;
             st.slot_lat[slot] = lat;
             st.seq_done = std::max(st.seq_done, f.seq + 1);
+            if (st.sink && f.seq < st.sink_n) {
+                std::memcpy(st.sink + (size_t)f.seq * (size_t)st.P,
+                            st.slots_host + (size_t)slot * (size_t)st.P, (size_t)st.P);
+                if (st.sink_t) st.sink_t[f.seq] = f.t_frame;
+            }
         }
         delete t;
     }
@@ -865,6 +874,44 @@ int esi_stream_frame(esi_server *s, int id, uint8_t *out, int64_t *t_frame, doub
     return ESI_OK;
 }
 
+int esi_stream_frame_seq(esi_server *s, int id, uint64_t seq, uint8_t *out, int64_t *t_frame)
+{
+    if (!s || id < 0 || id >= (int)s->streams.size() || !s->streams[id].open || !out)
+        return ESI_EINVAL;
+    poll(s);
+    Stream &st = s->streams[id];
+    if (seq >= st.seq_done) return ESI_ESTATE;
+    // slot seq % K is reused by frame seq + K once that one is handed to a tick
+    const unsigned long long K = (unsigned long long)s->opts.frame_slots;
+    if (st.seq_issued > seq + K) return ESI_ERANGE;
+    const int slot = (int)(seq % K);
+    std::memcpy(out, st.slots_host + (size_t)slot * (size_t)st.P, (size_t)st.P);
+    if (t_frame) *t_frame = st.slot_t[slot];
+    return ESI_OK;
+}
+
+int esi_stream_set_frame_sink(esi_server *s, int id, uint8_t *out, uint64_t max_frames,
+                              int64_t *t_frames)
+{
+    if (!s || id < 0 || id >= (int)s->streams.size() || !s->streams[id].open) return ESI_EINVAL;
+    if (max_frames && !out) return ESI_EINVAL;
+    poll(s);
+    Stream &st = s->streams[id];
+    st.sink = max_frames ? out : nullptr;
+    st.sink_n = max_frames;
+    st.sink_t = max_frames ? reinterpret_cast<long long *>(t_frames) : nullptr;
+    return ESI_OK;
+}
+
+int esi_stream_frames_done(esi_server *s, int id, uint64_t *n_done)
+{
+    if (!s || id < 0 || id >= (int)s->streams.size() || !s->streams[id].open || !n_done)
+        return ESI_EINVAL;
+    poll(s);
+    *n_done = s->streams[id].seq_done;
+    return ESI_OK;
+}
+
 int esi_stream_state(esi_server *s, int id, float *S, int64_t *T)
 {
     if (!s || id < 0 || id >= (int)s->streams.size() || !s->streams[id].open || !S || !T)
@@ -1031,6 +1078,9 @@ int esi_server_run(esi_server *s, const esi_packet *pk, size_t n, int64_t tick_u
                     continue;
                 }
                 if (!rc && sp->tile_h) rc = esi_stream_set_tile_h(s, id, sp->tile_h);
+                if (!rc && sp->frame_sink)
+                    rc = esi_stream_set_frame_sink(s, id, sp->frame_sink, sp->sink_frames,
+                                                   sp->sink_t_frames);
                 if (!rc) bind(q.stream, id, sp);
             } else {
                 const int id = sid_of(q.stream);

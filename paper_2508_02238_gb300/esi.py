@@ -81,7 +81,9 @@ class esi_packet(ctypes.Structure):
 
 class esi_stream_spec(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
-                ("tile_h", ctypes.c_int32), ("stream_id", ctypes.c_int32), ("params", esi_params)]
+                ("tile_h", ctypes.c_int32), ("stream_id", ctypes.c_int32), ("params", esi_params),
+                ("frame_sink", ctypes.c_void_p), ("sink_frames", ctypes.c_uint64),
+                ("sink_t_frames", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p
@@ -121,6 +123,12 @@ SIGNATURES = {
     "esi_plain_run": (_i32, [_i32, _P, _P, _P, _P, _sz, _i64, _i64, _i64, _i32,
                              ctypes.POINTER(esi_server_stats)]),
     "esi_stream_frame": (_i32, [_P, _i32, _P, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)]),
+    "esi_stream_frames_done": (_i32, [_P, _i32, ctypes.POINTER(ctypes.c_uint64)]),
+    "esi_stream_set_frame_sink": (_i32, [_P, _i32, _P, ctypes.c_uint64, _P]),
+    "esi_stream_frame_seq": (_i32, [_P, _i32, ctypes.c_uint64, _P, ctypes.POINTER(_i64)]),
+    "esi_bin_events": (_i32, [_i32, _i32, ctypes.POINTER(esi_tuning), _P, ctypes.c_uint64,
+                              ctypes.c_uint64, _sz, _i64, _P, _P,
+                              ctypes.POINTER(ctypes.c_uint64), _P]),
     "esi_stream_state": (_i32, [_P, _i32, _P, _P]),
     "esi_stream_close": (_i32, [_P, _i32]),
     "esi_server_sync": (_i32, [_P]),
@@ -347,6 +355,37 @@ def esi_stream_frame(srv, stream_id: int, out):
     rc = _fn("esi_stream_frame")(srv, int(stream_id), _P(ptr(out) or None), ctypes.byref(t),
                                  ctypes.byref(lat))
     return rc, int(t.value), float(lat.value)
+
+
+def esi_stream_frames_done(srv, stream_id: int):
+    """Returns (rc, number of the stream's finished frames)."""
+    n = ctypes.c_uint64(0)
+    rc = _fn("esi_stream_frames_done")(srv, int(stream_id), ctypes.byref(n))
+    return rc, int(n.value)
+
+
+def esi_stream_set_frame_sink(srv, stream_id: int, out, max_frames: int, t_frames=None) -> int:
+    return _fn("esi_stream_set_frame_sink")(srv, int(stream_id), _P(ptr(out) or None),
+                                            int(max_frames), _P(ptr(t_frames) or None))
+
+
+def esi_stream_frame_seq(srv, stream_id: int, seq: int, out):
+    """Returns (rc, t_frame_us) for frame number seq of the stream."""
+    t = ctypes.c_int64(0)
+    rc = _fn("esi_stream_frame_seq")(srv, int(stream_id), int(seq), _P(ptr(out) or None),
+                                     ctypes.byref(t))
+    return rc, int(t.value)
+
+
+def esi_bin_events(width: int, height: int, shape: esi_tuning, ring, ring_capacity: int,
+                   first: int, n: int, t_base: int, records, runs, cuda_stream=0):
+    """Returns (rc, events dropped)."""
+    d = ctypes.c_uint64(0)
+    rc = _fn("esi_bin_events")(int(width), int(height), ctypes.byref(shape),
+                               _P(ptr(ring) or None), int(ring_capacity), int(first), int(n),
+                               int(t_base), _P(ptr(records) or None), _P(ptr(runs) or None),
+                               ctypes.byref(d), _P(int(cuda_stream) or None))
+    return rc, int(d.value)
 
 
 def esi_stream_state(srv, stream_id: int, S, T) -> int:

@@ -284,3 +284,39 @@ def mixed_serving(duration_s: float = 0.25, seed: int = 1004, counts=(16, 48, 12
         out.append(dict(form=form, W=sc.W, H=sc.H, rate=rate, t_join_us=t_join,
                         t_leave_us=t_leave, scene=sc))
     return out
+
+
+def _arrivals(rng, t0_us: int, t1_us: int, mean_us: float = 1000.0) -> np.ndarray:
+    """Packet arrival times in (t0, t1): Poisson with mean gap mean_us, plus a
+    last one at t1 (the stream is complete up to each arrival)."""
+    gaps = rng.exponential(mean_us, size=int((t1_us - t0_us) / mean_us) * 3 + 10)
+    arr = t0_us + np.cumsum(gaps).astype(np.int64) + 1
+    return np.append(arr[arr < t1_us], t1_us)
+
+
+def serving_streams(n_streams: int = 64, duration_s: float = 0.25, seed: int = 1003):
+    """Batched-serving workload of n_streams sinusoid form 346x260 streams:
+    lognormal rates (median 1 Mev/s) clipped to [0.2, 5] Mev/s and Poisson
+    packet arrivals with a 1 ms mean gap.
+
+    Returns (rates, streams): each stream a dict with W, H, rate, scene and
+    arrivals (int64 us; the last one at the end of the stream).
+    """
+    rates = lognormal_rates(n_streams, seed)
+    rng = np.random.default_rng(seed)
+    D = int(round(duration_s * 1e6))
+    out = []
+    for i in range(n_streams):
+        sc = serving_stream(i, float(rates[i]), duration_s)
+        out.append(dict(W=sc.W, H=sc.H, rate=float(rates[i]), scene=sc,
+                        arrivals=_arrivals(rng, 0, D)))
+    return rates, out
+
+
+def mixed_arrivals(ws, duration_s: float = 0.25, seed: int = 1004):
+    """Poisson packet arrivals (1 ms mean gap) of every stream of a
+    mixed_serving workload, from its join to its leave time (or the end)."""
+    rng = np.random.default_rng(seed + 1)
+    D = int(round(duration_s * 1e6))
+    return [_arrivals(rng, w["t_join_us"], w["t_leave_us"] if w["t_leave_us"] is not None else D)
+            for w in ws]

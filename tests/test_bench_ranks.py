@@ -80,7 +80,7 @@ def test_reference_arm_prints_the_contract_line():
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 1 and line["steps"] == 1
     assert line["metric"] == bench.METRIC and line["unit"] == "events/s"
-    assert line["config"]["workload"] == bench.WORKLOAD
+    assert line["config"]["workload"] == bench.WORKLOADS[bench.HEADLINE][0]
     assert line["higher_is_better"] is True and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["cpu_baseline"]["value"] == line["value"]

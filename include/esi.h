@@ -111,7 +111,15 @@ typedef struct {
  * 8 or 16 with tile_w = 128 or 64, 16 or 32 with tile_w = 32.  chunk_events: events per binning block
  * (power of two, 512..8192).  batch_records: records a tile sorts in shared
  * memory at once (power of two, 1024..8192).  max_batch_events: events per
- * binning pass of a render (>= chunk_events).
+ * binning pass of a render (>= chunk_events).  scan_chain: the tile kernel
+ * applies a row's due events 32 at a time; a group in which one pixel has at
+ * least scan_chain events (1..32) is composed as a segmented scan of the
+ * events' clamped-affine maps (Alg. 2's update with the clamp of Eq. 13 is
+ * such a map, and they compose associatively) in log2 steps instead of event
+ * by event; its rounding then differs from the event-by-event loop by a few
+ * units in the last place.  33 turns the scan off: every group runs event
+ * by event in arrival order, and results are bit-identical across every
+ * launch shape.  Default 8.
  */
 typedef struct {
     int32_t tile_h;
@@ -119,6 +127,7 @@ typedef struct {
     int32_t batch_records;
     int32_t max_batch_events;
     int32_t tile_w;
+    int32_t scan_chain;
 } esi_tuning;
 
 /* Per-kernel device time collected while profiling is on. */
@@ -338,7 +347,8 @@ typedef struct {
     int32_t use_graph;            /* 1 (default): replay a captured graph    */
     int32_t tile_h;               /* rows per 128-pixel tile of new streams: 0 = 8, or 4, 16 */
     int32_t max_stream_pixels;    /* largest W * H accepted; default 1280*720 */
-    int32_t _reserved[3];
+    int32_t scan_chain;           /* as esi_tuning.scan_chain; 0 = default (8) */
+    int32_t _reserved[2];
 } esi_server_opts;
 
 /* Latencies in milliseconds over the frames finished since the last reset:

@@ -100,6 +100,7 @@ int validate_tuning(const esi_tuning &t)
     if (!pow2(t.chunk_events) || t.chunk_events < 512 || t.chunk_events > 8192) return ESI_EINVAL;
     if (!pow2(t.batch_records) || t.batch_records < 1024 || t.batch_records > 8192) return ESI_EINVAL;
     if (t.max_batch_events < t.chunk_events) return ESI_EINVAL;
+    if (t.scan_chain < 1 || t.scan_chain > kScanNever) return ESI_EINVAL;
     return ESI_OK;
 }
 
@@ -116,6 +117,7 @@ esi_tuning default_tuning(int W, int H)
     t.chunk_events = large ? 4096 : 2048;
     t.batch_records = large ? 2048 : 4096;
     t.max_batch_events = 1 << 22;
+    t.scan_chain = kScanChainDefault;
     return t;
 }
 
@@ -759,6 +761,7 @@ int esi_set_tuning(esi_handle *h, const esi_tuning *t)
     if (!n.chunk_events) n.chunk_events = d.chunk_events;
     if (!n.batch_records) n.batch_records = d.batch_records;
     if (!n.max_batch_events) n.max_batch_events = d.max_batch_events;
+    if (!n.scan_chain) n.scan_chain = d.scan_chain;
     int rc = validate_tuning(n);
     if (rc) return rc;
     esi_tuning old = h->tun;
@@ -1005,7 +1008,7 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
             ba.tile_bits = index_bits(h->n_tiles);
             ba.rec = h->rec[buf];
             ba.hrow = h->hrow[buf];
-            ba.use_mask = (h->n_tiles <= kBinMaskTiles && bin_mask_fits(chunk, h->n_tiles)) ? 1 : 0;
+            ba.use_mask = bin_mask_fits(chunk, h->n_tiles) ? 1 : 0;
             ba.status = h->dstatus;
             cudaEvent_t ev;
             rc = prof_begin(h, &ev, h->bin_stream);
@@ -1038,6 +1041,7 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
         ta.P = h->P;
         ta.batch = tu.batch_records;
         ta.status = h->dstatus;
+        ta.scan_chain = tu.scan_chain;
         cudaEvent_t ev;
         rc = prof_begin(h, &ev, h->tile_stream);
         if (!rc) rc = cuda_fail(h, launch_tile(ta, tu.tile_h, tu.tile_w, vec, h->tile_stream));

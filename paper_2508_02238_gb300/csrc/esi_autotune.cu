@@ -133,7 +133,7 @@ std::vector<esi_tuning> handle_candidates(int flags)
         for (int chunk : {2048, 4096})
             for (int batch : {2048, 4096})
                 for (int mb : {1 << 21, 1 << 22, 1 << 23}) {
-                    esi_tuning t;
+                    esi_tuning t{};
                     t.tile_w = sh[0];
                     t.tile_h = sh[1];
                     t.chunk_events = chunk;

@@ -33,6 +33,7 @@ extern "C" int esi_bin_events(int width, int height, const esi_tuning *shape,
     if (!t.chunk_events) t.chunk_events = 2048;
     if (!t.batch_records) t.batch_records = 4096;
     if (!t.max_batch_events) t.max_batch_events = t.chunk_events;
+    if (!t.scan_chain) t.scan_chain = kScanChainDefault;
     int rc = validate_tuning(t);
     if (rc) return rc;
     const int tiles_x = (width + t.tile_w - 1) / t.tile_w;
@@ -65,7 +66,7 @@ extern "C" int esi_bin_events(int width, int height, const esi_tuning *shape,
         ba.tile_bits = index_bits(n_tiles);
         ba.rec = reinterpret_cast<unsigned long long *>(records);
         ba.hrow = runs;
-        ba.use_mask = (n_tiles <= kBinMaskTiles && bin_mask_fits(t.chunk_events, n_tiles)) ? 1 : 0;
+        ba.use_mask = bin_mask_fits(t.chunk_events, n_tiles) ? 1 : 0;
         ba.status = st;
         e = launch_bin(ba, n_chunks, s);
     }

@@ -102,7 +102,7 @@ extern "C" int esi_event_states(esi_handle *h, float *out, size_t cap, int out_o
         ba.tile_bits = index_bits(h->n_tiles);
         ba.rec = h->rec[buf];
         ba.hrow = h->hrow[buf];
-        ba.use_mask = (h->n_tiles <= kBinMaskTiles && bin_mask_fits(chunk, h->n_tiles)) ? 1 : 0;
+        ba.use_mask = bin_mask_fits(chunk, h->n_tiles) ? 1 : 0;
         ba.status = h->dstatus;
         ba.rec_idx = h->rec_idx[buf];
         ba.ev_out = dout + sb.i0;
@@ -138,6 +138,7 @@ extern "C" int esi_event_states(esi_handle *h, float *out, size_t cap, int out_o
         ta.status = h->dstatus;
         ta.rec_idx = h->rec_idx[buf];
         ta.ev_out = dout + sb.i0;
+        ta.scan_chain = h->tun.scan_chain;
         rc = prof_begin(h, &ev, h->tile_stream);
         if (!rc) rc = cuda_fail(h, launch_tile_ev(ta, tu.tile_h, tu.tile_w, h->tile_stream));
         if (!rc) rc = prof_end(h, kKindEvState, ev, h->tile_stream);

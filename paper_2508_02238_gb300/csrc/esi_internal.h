@@ -9,6 +9,11 @@
 namespace esi {
 
 constexpr int kTileW = 128;  // a tile row is one warp: lane l owns x = 4l .. 4l + 3
+// Shortest same-pixel chain in a group of 32 records that the tile kernel
+// composes with the segmented scan: the default, and the value that turns
+// the scan off (a group holds at most 32 records).
+constexpr int kScanChainDefault = 8;
+constexpr int kScanNever = 33;
 constexpr int kMaxSmemPerBlock = 227 * 1024;
 
 // Decay of Eq. 4, d(dt) = max(1 - k dt, 0)^b, prepared for the device.
@@ -46,10 +51,12 @@ struct DevStatus {
     int err_where;                // which kernel / wait gave up
 };
 
-// Up to this many tiles the binning finds same-tile lanes through a mask word
-// per tile and warp in shared memory (when it fits); above, through one
-// ballot per tile-index bit.
-constexpr int kBinMaskTiles = 1024;
+// The binning finds same-tile lanes of a warp through kBinMaskSlots mask
+// words per warp in shared memory, indexed by tile mod kBinMaskSlots, and one
+// ballot per higher tile-index bit (or, without the words, one ballot per
+// tile-index bit).
+constexpr int kBinMaskSlotBits = 7;
+constexpr int kBinMaskSlots = 1 << kBinMaskSlotBits;
 
 // Result of a device-checked push: an order violation anywhere, and the time
 // of the push's last event.
@@ -77,7 +84,7 @@ struct BinArgs {
     int tile_bits;                // bits of a tile index (n_tiles <= 2^tile_bits)
     unsigned long long *rec;      // out: records, block c at rec + c * chunk
     unsigned int *hrow;           // out: [tile][chunk] (start << 16 | count)
-    int use_mask;                 // same-tile lanes by shared mask words (up to 1024 tiles)
+    int use_mask;                 // same-tile lanes by shared mask words
     DevStatus *status;
     // per-event output (esi_event_states; both set, or both null for renders):
     unsigned *rec_idx = nullptr;  // out: beside each record, its event's index in the sub-batch
@@ -117,6 +124,10 @@ struct TileArgs {
     // per-event output (esi_event_states' instantiations only; null otherwise)
     const unsigned *rec_idx = nullptr;  // event index (in the sub-batch) beside each record
     float *ev_out = nullptr;            // S right after each event, at its index
+    // a group whose longest same-pixel chain has at least this many records
+    // is composed by the segmented scan; shorter ones event by event
+    // (kScanNever: always event by event, bit-identical across launch shapes)
+    int scan_chain = kScanNever;
 };
 
 // One stream segment of a batched binning launch: the chunks

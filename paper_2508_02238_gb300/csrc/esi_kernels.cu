@@ -33,16 +33,15 @@ constexpr int kWhereBinCopy = 1;
 
 static __host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-// Shared-memory layout of the binning kernel.
+// Shared-memory layout of the binning kernel.  The staged events' 16-byte
+// slots are reused: once phase 1 has read event k, slot k's first half holds
+// its record, and phase 3 sorts the records into the slots' second halves.
 static __host__ __device__ inline size_t bin_layout(int chunk, int n_tiles, bool mask,
-                                                    size_t *off_sort, size_t *off_tstart,
-                                                    size_t *off_cnt)
+                                                    size_t *off_tstart, size_t *off_cnt)
 {
     constexpr int NW = kBinThreads / 32;
     size_t o = 0;
-    o += (size_t)chunk * 16;                       // staged events
-    *off_sort = o;
-    o += (size_t)chunk * 8;                        // sorted records
+    o += (size_t)chunk * 16;                       // staged events, then records
     *off_tstart = o;
     o += (size_t)round_up(n_tiles + 1, 4) * 4;     // tile starts (+ total)
     *off_cnt = o;
@@ -50,19 +49,15 @@ static __host__ __device__ inline size_t bin_layout(int chunk, int n_tiles, bool
     o += (size_t)chunk * 2;                        // event: offset within its warp's tile run
     o += (size_t)chunk * 2;                        // event: tile (0xffff = dropped)
     if (mask)
-        o += (size_t)NW * round_up(n_tiles, 8) * 4; // per-warp lane masks per tile (kept zero)
+        o += (size_t)NW * kBinMaskSlots * 4;       // per-warp lane masks (kept zero)
     return o;
 }
 
-// Shared memory for chunks of `chunk` events over at most n_tiles tiles;
-// with `mask`, jobs of at most kBinMaskTiles tiles use the mask words, so the
-// larger of the two layouts.
+// Shared memory for chunks of `chunk` events over at most n_tiles tiles.
 size_t bin_smem_bytes(int chunk, int n_tiles, bool mask)
 {
-    size_t a, b, c;
-    const size_t plain = bin_layout(chunk, n_tiles, false, &a, &b, &c);
-    if (!mask) return plain;
-    return std::max(plain, bin_layout(chunk, std::min(n_tiles, kBinMaskTiles), true, &a, &b, &c));
+    size_t a, b;
+    return bin_layout(chunk, n_tiles, mask, &a, &b);
 }
 
 // Whether chunks over up to n_tiles tiles can take the mask-word layout.
@@ -86,16 +81,17 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
 
     const int chunk = a.chunk, n_tiles = a.n_tiles;
     const int ntp = round_up(n_tiles, 8);
-    const bool use_mask = a.use_mask && n_tiles <= kBinMaskTiles;
-    size_t off_sort, off_tstart, off_cnt;
-    bin_layout(chunk, n_tiles, use_mask, &off_sort, &off_tstart, &off_cnt);
+    const bool use_mask = a.use_mask != 0;
+    size_t off_tstart, off_cnt;
+    bin_layout(chunk, n_tiles, use_mask, &off_tstart, &off_cnt);
     int4 *sev = reinterpret_cast<int4 *>(smem);
-    unsigned long long *ssort = reinterpret_cast<unsigned long long *>(smem + off_sort);
+    // slot k: record of event k (first half), sorted record k (second half)
+    unsigned long long *srec = reinterpret_cast<unsigned long long *>(smem);
     unsigned *tstart = reinterpret_cast<unsigned *>(smem + off_tstart);
     unsigned short *cnt = reinterpret_cast<unsigned short *>(smem + off_cnt);
     unsigned short *loff = cnt + NW * ntp;
     unsigned short *ltile = loff + chunk;
-    unsigned *tmask = reinterpret_cast<unsigned *>(ltile + chunk);   // [NW][ntp], if use_mask
+    unsigned *tmask = reinterpret_cast<unsigned *>(ltile + chunk);   // [NW][kBinMaskSlots]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long c0 = (long long)cidx * chunk;
@@ -118,7 +114,7 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
     __shared__ int s_copy_ok;
     for (int i = tid; i < NW * ntp; i += NT) cnt[i] = 0;
     if (use_mask)
-        for (int i = tid; i < NW * ntp; i += NT) tmask[i] = 0u;
+        for (int i = tid; i < NW * kBinMaskSlots; i += NT) tmask[i] = 0u;
     if (tid == 0) {
         // one thread waits for the copy; the others sleep at the barrier
         int ok = mbar_wait_bounded(&bar, 0, kWaitLimitNs) ? 1 : 0;
@@ -140,7 +136,9 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
     const int s1 = min(s0 + per, nc);
 
     // phase 1: in arrival order, each warp ranks its slice's events within
-    // their tile (peers by ballot), keeping the offset inside its own run
+    // their tile (peers by mask words and ballots), keeping the offset inside
+    // its own run, and turns each event into its record in place
+    const int th_mask = (1 << thl) - 1;
     unsigned drop = 0;
     for (int base = s0; base < s1; base += 32) {
         const int k = base + lane;
@@ -150,6 +148,10 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
             const int x = e.z & 0xffff, y = (int)((unsigned)e.z >> 16);
             if (x < W && y < H) {
                 tile = (y >> thl) * tiles_x + (x >> twl);
+                const long long t = ((long long)(unsigned)e.y << 32) | (unsigned)e.x;
+                const unsigned pit = ((unsigned)(y & th_mask) << twl) | (unsigned)(x & ((1 << twl) - 1));
+                const bool pos = (signed char)(e.w & 0xff) > 0;
+                srec[2 * k] = make_record((unsigned)(t - a.t_base), pit, pos ? 1u : 0u);
             } else {
                 ++drop;
                 if constexpr (EV) a.ev_out[c0 + k] = __int_as_float(0x7fc00000);
@@ -158,14 +160,21 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
         const bool valid = tile >= 0;
         unsigned peers;
         if (use_mask) {
-            // each lane sets its bit in its tile's mask word, reads the word
-            // and clears it once every lane has read
-            unsigned *mw = tmask + warp * ntp + (valid ? tile : 0);
+            // each lane sets its bit in its tile's mask word (slot tile mod
+            // kBinMaskSlots), reads the word and clears it once every lane
+            // has read; lanes whose tiles share the slot are told apart by
+            // one ballot per higher tile-index bit
+            unsigned *mw = tmask + warp * kBinMaskSlots + (valid ? (tile & (kBinMaskSlots - 1)) : 0);
             if (valid) atomicOr(mw, 1u << lane);
             __syncwarp();
             peers = valid ? *mw : 0u;
             __syncwarp();
             if (valid) *mw = 0u;
+            for (int b = kBinMaskSlotBits; b < tbits; ++b) {
+                const bool bit = (tile >> b) & 1;
+                const unsigned v = __ballot_sync(kFull, bit);
+                peers &= bit ? v : ~v;
+            }
         } else {
             peers = warp_peers((unsigned)tile, tbits, valid);
         }
@@ -203,27 +212,21 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
     for (int j = tid; j < n_tiles; j += NT)
         a.hrow[(size_t)j * n_chunks_all + cidx] = (tstart[j] << 16) | (tstart[j + 1] - tstart[j]);
 
-    // phase 3: scatter every event to its stable place in tile order; each
-    // warp scatters the slice it ranked
-    const int th_mask = (1 << thl) - 1;
+    // phase 3: every record to its stable place in tile order (the second
+    // halves of the slots); each warp scatters the slice it ranked
     const int w = warp;
     for (int k = warp * per + lane; k < min(nc, (warp + 1) * per); k += 32) {
         const unsigned tile = ltile[k];
         if (tile == 0xffffu) continue;
-        const int4 e = sev[k];
-        const int x = e.z & 0xffff, y = (int)((unsigned)e.z >> 16);
-        const long long t = ((long long)(unsigned)e.y << 32) | (unsigned)e.x;
-        const unsigned pit = ((unsigned)(y & th_mask) << twl) | (unsigned)(x & ((1 << twl) - 1));
-        const bool pos = (signed char)(e.w & 0xff) > 0;
         const unsigned q = tstart[tile] + cnt[w * ntp + tile] + loff[k];
-        ssort[q] = make_record((unsigned)(t - a.t_base), pit, pos ? 1u : 0u);
+        srec[2 * q + 1] = srec[2 * k];
         if constexpr (EV) a.rec_idx[c0 + q] = (unsigned)(c0 + k);
     }
     __syncthreads();
 
     // phase 4: the chunk's records, tile-sorted, to global memory
     unsigned long long *dst = a.rec + c0;
-    for (unsigned i = tid; i < total; i += NT) dst[i] = ssort[i];
+    for (unsigned i = tid; i < total; i += NT) dst[i] = srec[2 * i + 1];
     if (tid == 0 && s_drop) atomicAdd(&a.status->dropped, (unsigned long long)s_drop);
 }
 
@@ -272,10 +275,10 @@ size_t tile_smem_bytes_ev(int batch, int n_chunks)
 
 size_t tile_static_smem_bytes(int tile_h, int tile_w)
 {
-    // pixel state (S, F, O and a peer mask per pixel), staged frames and the
-    // sort scratch
-    return (size_t)tile_h * tile_w * 20 + (size_t)kStageFrames * sizeof(WinInfo) +
-           (size_t)tile_h * tile_h * 2 + 1024;
+    // pixel state (S, F, O and a peer mask per pixel), the scan's event maps
+    // (32 per row), staged frames and the sort scratch
+    return (size_t)tile_h * tile_w * 20 + (size_t)tile_h * 32 * 16 +
+           (size_t)kStageFrames * sizeof(WinInfo) + (size_t)tile_h * tile_h * 2 + 1024;
 }
 
 int decay_kind_of(const DecayParams &dp)

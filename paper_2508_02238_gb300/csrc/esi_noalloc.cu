@@ -217,6 +217,7 @@ extern "C" int esi_render_frames_noalloc(int width, int height, const esi_params
     ta.P = (long long)width * height;
     ta.batch = kNaBatch;
     ta.status = st;
+    ta.scan_chain = kScanChainDefault;
     // the vector tile path moves a lane's four pixels as one float4 of S, two
     // 16-byte words of T and one 32-bit frame word: it needs S and T 16-byte
     // aligned and frames 4-byte aligned; otherwise the scalar path runs

@@ -182,7 +182,7 @@ struct esi_server {
     // capacities of one tick
     int cap_jobs = 0, cap_chunks = 0, cap_items = 0, cap_frames = 0, max_tiles = 0;
     int tile_grid = 0;  // persistent grid of the batched tile kernel
-    bool bin_mask = false;  // binning jobs of up to 1024 tiles use mask words
+    bool bin_mask = false;  // binning finds same-tile lanes by mask words
     long long cap_events = 0;
     size_t off_binjob = 0, off_chunkjob = 0, off_tilejob = 0, off_items = 0, off_win = 0,
            off_fout = 0, off_events = 0, tab_bytes = 0;
@@ -356,11 +356,13 @@ int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts, vo
     if (!o.frame_slots) o.frame_slots = 4;
     if (!o.tile_h) o.tile_h = 8;
     if (!o.max_stream_pixels) o.max_stream_pixels = 1280 * 720;
+    if (!o.scan_chain) o.scan_chain = kScanChainDefault;
     if (!opts) o.use_graph = 1;
     if (o.frame_period_us < 1 || o.max_events_per_tick < kChunk || o.max_streams < 1 ||
         o.max_streams > 4096 || o.frame_slots < 2 || o.frame_slots > 64 ||
         (o.tile_h != 4 && o.tile_h != 8 && o.tile_h != 16) ||
-        o.max_stream_pixels < 1 || state_budget_bytes == 0)
+        o.max_stream_pixels < 1 || o.scan_chain < 1 || o.scan_chain > kScanNever ||
+        state_budget_bytes == 0)
         return ESI_EINVAL;
     esi_server *s = new (std::nothrow) esi_server();
     if (!s) return ESI_ENOMEM;
@@ -756,6 +758,7 @@ int esi_server_tick(esi_server *s, int64_t now_us)
         A.status = s->dstatus;
         A.rec_idx = nullptr;
         A.ev_out = nullptr;
+        A.scan_chain = s->opts.scan_chain;
         for (size_t w = 0; w < fr.size(); ++w) {
             const long long d = fr[w] - t_base;
             win[n_frames + w].lim = std::min(std::max(d, -1ll), 0xffffffffll);

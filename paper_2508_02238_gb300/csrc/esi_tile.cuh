@@ -56,6 +56,75 @@ __device__ __forceinline__ int run_of(const unsigned *pre, int n, unsigned g)
     return lo;
 }
 
+// A group of due records with a long same-pixel chain, as a segmented scan.
+// Each event is a monotone map of its pixel's state, f(S) = clamp(a S + b,
+// lo, hi): Alg. 2 gives (d, d c, S_min, S_max) from S <- clamp((S + c) d),
+// Alg. 1 the same without the clamp, Eq. 3 (exp) (d, c) from S <- S d + c.
+// Such maps compose into maps of the same form (a >= 0 commutes with the
+// clamp): g o f = (a_g a_f, a_g b_f + b_g, clamp(a_g lo_f + b_g, lo_g, hi_g),
+// clamp(a_g hi_f + b_g, lo_g, hi_g)), and composition is associative.  The
+// group's lanes are permuted so that each pixel's events sit in contiguous
+// lanes in arrival order, an inclusive segmented scan composes each lane's
+// prefix in log2(chain) shuffle steps, and every lane applies its prefix to
+// the state its pixel had when the group started.  The rounding differs from
+// the event-by-event loop by a few units in the last place.
+// sc: this warp's 32 slots; peers / rank: the lane's same-pixel lanes and
+// its place among them; maxr: the longest chain minus one.
+template <int DK>
+__device__ __forceinline__ float scan_group(float4 *sc, bool valid, unsigned peers, unsigned rank,
+                                            float c, float d, float s_mem, unsigned maxr,
+                                            const DecayParams &dp, const MapParams &mp)
+{
+    const int lane = threadIdx.x & 31;
+    const bool clamped = mp.s_min > -INFINITY;   // Alg. 2 only
+    const bool after = DK == kDecayGeneral && dp.b_mode == kBModeExp;
+    // position of each event: its pixel's first position (an exclusive scan
+    // of the chain lengths over the pixels' first lanes) plus its rank
+    const bool lead = valid && rank == 0u;
+    const unsigned len = lead ? (unsigned)__popc(peers) : 0u;
+    const unsigned first_pos = warp_inclusive_scan(len) - len;
+    const unsigned seg0 = __shfl_sync(kFull, first_pos, valid ? __ffs(peers) - 1 : lane);
+    const unsigned starts = __reduce_or_sync(kFull, lead ? (1u << seg0) : 0u);
+    const int nv = __popc(__ballot_sync(kFull, valid));
+    if (valid) sc[seg0 + rank] = make_float4(d, after ? c : d * c, mp.s_min, mp.s_max);
+    __syncwarp();
+    float4 q = sc[lane];
+    __syncwarp();
+    const unsigned le = lane == 31 ? kFull : (2u << lane) - 1u;
+    const int seg = lane < nv ? 31 - __clz(starts & le) : lane;   // start of this position's pixel
+    for (int o = 1; o <= (int)maxr; o <<= 1) {
+        const float pa = __shfl_up_sync(kFull, q.x, o);
+        const float pb = __shfl_up_sync(kFull, q.y, o);
+        float pl = 0.0f, ph = 0.0f;
+        if (clamped) {
+            pl = __shfl_up_sync(kFull, q.z, o);
+            ph = __shfl_up_sync(kFull, q.w, o);
+        }
+        if (lane - o >= seg) {
+            if (clamped) {
+                const float lo = fminf(fmaxf(fmaf(q.x, pl, q.y), q.z), q.w);
+                const float hi = fminf(fmaxf(fmaf(q.x, ph, q.y), q.z), q.w);
+                q.z = lo;
+                q.w = hi;
+            }
+            q.y = fmaf(q.x, pb, q.y);
+            q.x *= pa;
+        }
+    }
+    // back to the lane that holds the event: its prefix applied to the state
+    // its pixel had when the group started
+    const int src = valid ? (int)(seg0 + rank) : lane;
+    const float A = __shfl_sync(kFull, q.x, src);
+    const float B = __shfl_sync(kFull, q.y, src);
+    float v = fmaf(A, s_mem, B);
+    if (clamped) {
+        const float lo = __shfl_sync(kFull, q.z, src);
+        const float hi = __shfl_sync(kFull, q.w, src);
+        v = fminf(fmaxf(v, lo), hi);
+    }
+    return v;
+}
+
 // One block per (32 PPL) x TH tile; warp w owns tile row w, lane l owns the
 // PPL pixels x = PPL l .. PPL l + PPL - 1 of that row for loads, stores and
 // frame codes (PPL = 4: 128-pixel rows; PPL = 2: 64-pixel rows; PPL = 1:
@@ -88,6 +157,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
     __shared__ __align__(16) float sF[TH][TWP];      // (float)(T - t_base)
     __shared__ __align__(16) long long sO[TH][TWP];  // T - t_base
     __shared__ unsigned sPeer[TH][TWP];              // per-pixel lane masks of a group (kept zero)
+    __shared__ __align__(16) float4 sScan[TH][32];   // a group's event maps, pixel by pixel
 
     const int R = a.batch, n_chunks = a.n_chunks;
     size_t off_b, off_runpre, off_runoff, off_lpos;
@@ -197,11 +267,15 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
         const float c = ((r >> 32) & 1u) ? mp.C : -mp.C;
         const unsigned maxr = __reduce_max_sync(kFull, valid ? rank : 0u);
         float s_out = 0.0f;
-        for (unsigned k = 0;; ++k) {
-            if (valid && rank == k) s_out = event_step<DK>(s_in, c, d, dp, mp);
-            if (k == maxr) break;
-            const float got = __shfl_sync(kFull, s_out, prev);
-            if (valid && rank == k + 1) s_in = got;
+        if ((int)maxr + 1 < a.scan_chain) {
+            for (unsigned k = 0;; ++k) {
+                if (valid && rank == k) s_out = event_step<DK>(s_in, c, d, dp, mp);
+                if (k == maxr) break;
+                const float got = __shfl_sync(kFull, s_out, prev);
+                if (valid && rank == k + 1) s_in = got;
+            }
+        } else {
+            s_out = scan_group<DK>(sScan[warp], valid, peers, rank, c, d, s_mem, maxr, dp, mp);
         }
         if constexpr (EV) {
             if (valid) a.ev_out[ev_idx] = s_out;

@@ -44,7 +44,7 @@ class esi_stats(ctypes.Structure):
 class esi_tuning(ctypes.Structure):
     _fields_ = [("tile_h", ctypes.c_int32), ("chunk_events", ctypes.c_int32),
                 ("batch_records", ctypes.c_int32), ("max_batch_events", ctypes.c_int32),
-                ("tile_w", ctypes.c_int32)]
+                ("tile_w", ctypes.c_int32), ("scan_chain", ctypes.c_int32)]
 
 
 class esi_kernel_time(ctypes.Structure):
@@ -56,7 +56,8 @@ class esi_server_opts(ctypes.Structure):
     _fields_ = [("frame_period_us", ctypes.c_int64), ("max_events_per_tick", ctypes.c_int64),
                 ("max_streams", ctypes.c_int32), ("frame_slots", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("tile_h", ctypes.c_int32),
-                ("max_stream_pixels", ctypes.c_int32), ("_reserved", ctypes.c_int32 * 3)]
+                ("max_stream_pixels", ctypes.c_int32), ("scan_chain", ctypes.c_int32),
+                ("_reserved", ctypes.c_int32 * 2)]
 
 
 class esi_server_stats(ctypes.Structure):

@@ -87,3 +87,28 @@ def test_method_constants_match_the_header():
     for name in ("ESI_METHOD_ALG2", "ESI_METHOD_ALG1", "ESI_METHOD_EQ3_EXP"):
         m = re.search(r"#define\s+%s\s+(\d+)" % name, hdr)
         assert m and int(m.group(1)) == getattr(esi, name), name
+
+
+def test_bin_events_checks_its_arguments_before_touching_cuda():
+    # every refusal happens on the host; without a CUDA device a valid call
+    # gets as far as the runtime and fails there (never ESI_EINVAL)
+    import torch
+    sh = esi.esi_tuning()
+    good = dict(width=346, height=260, ring_capacity=1 << 12, first=0, n=100)
+
+    def call(ring=16 * 4096, **kw):
+        a = dict(good, **kw)
+        return esi.esi_bin_events(a["width"], a["height"], sh, ring, a["ring_capacity"],
+                                  a["first"], a["n"], 0, 1 << 20, 1 << 21)[0]
+
+    assert call(width=0) == esi.ESI_EINVAL
+    assert call(height=70000) == esi.ESI_EINVAL
+    assert call(ring_capacity=3000) == esi.ESI_EINVAL
+    assert call(n=5000) == esi.ESI_EINVAL              # more than the ring holds
+    assert call(ring=16 * 4096 + 8) == esi.ESI_EINVAL  # not 16-byte aligned
+    sh.tile_h = 5
+    assert call() == esi.ESI_EINVAL
+    sh.tile_h = 0
+    assert esi.esi_bin_events(346, 260, sh, 0, 1 << 12, 0, 0, 0, 0, 0)[0] == esi.ESI_OK  # n = 0
+    if not torch.cuda.is_available():
+        assert call() == esi.ESI_ECUDA

@@ -6,7 +6,7 @@ runs each method's own loop.  Tolerances are those of esi_harness.
 import numpy as np
 import pytest
 
-from esi_harness import compare, random_events, run_gpu, run_oracle
+from esi_harness import EXACT, compare, random_events, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -62,10 +62,10 @@ def test_method_launch_shapes_bit_identical(method, b):
     ev = random_events(rng, W, H, 80_000, 0, 800_000, hot=(33, 40, 0.1))
     p = P(method=method, b=b, k_per_s=40.0, render_decay=1)
     tf = np.arange(10_000, 800_001, 10_000)
-    ref = run_gpu(ev, W, H, p, tf)
+    ref = run_gpu(ev, W, H, p, tf, tuning=EXACT)
     compare(ref, run_oracle(ev, W, H, p, tf), p["C"])
     for t in TUNINGS:
-        g = run_gpu(ev, W, H, p, tf, tuning=t)
+        g = run_gpu(ev, W, H, p, tf, tuning={**t, **EXACT})
         assert np.array_equal(g["S"], ref["S"]), t
         assert np.array_equal(g["T"], ref["T"]), t
         assert np.array_equal(g["frames"], ref["frames"]), t

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import synth
-from esi_harness import GpuStream, compare, oracle_params, random_events, run_oracle
+from esi_harness import EXACT, GpuStream, compare, oracle_params, random_events, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -82,12 +82,14 @@ def drive(esi, srv, ids, events, dims, t_end, tick_us=1000, start=0, on_tick=Non
     return frames
 
 
-def serve(stream_specs, t_end, use_graph=1, budget=256 << 20, tile_hs=None, retile=None):
+def serve(stream_specs, t_end, use_graph=1, budget=256 << 20, tile_hs=None, retile=None,
+          scan_chain=0):
     """tile_hs: {spec index: tile height} set at open; retile: (time, {index: tile height})
-    applied before that tick."""
+    applied before that tick; scan_chain: the server's segmented-scan knob (33: off)."""
     esi = _esi()
     opts = esi.esi_server_opts()
     opts.use_graph = use_graph
+    opts.scan_chain = scan_chain
     rc, srv = esi.esi_server_create(budget, opts, 0)
     assert rc == 0
     try:
@@ -159,13 +161,14 @@ def test_each_stream_is_the_same_alone_and_in_the_mix():
 
 def test_served_stream_equals_single_sensor_handle():
     # the server and esi_render_frames run the same kernels on the same events
+    # (with the scan off on both: ticks and one render group records apart)
     W, H, p, kind = STREAMS[1]
     t_end = 100_000
-    res, _ = serve([(1, STREAMS[1])], t_end)
+    res, _ = serve([(1, STREAMS[1])], t_end, scan_chain=33)
     frames, (S, T), ev = res[1]
     tf = sorted(frames)
     used = ev[ev["t"] <= t_end]
-    with GpuStream(W, H, {**dict(t_origin_us=0), **p}) as g:
+    with GpuStream(W, H, {**dict(t_origin_us=0), **p}, EXACT) as g:
         assert g.push(used) == 0
         rc, fr = g.render_frames(tf)
         assert rc == 0
@@ -260,13 +263,14 @@ def test_push_validation():
 
 def test_per_stream_tile_heights_are_bit_identical():
     # tiles only organise the work: every pixel applies its events in the same
-    # order with the same arithmetic at any tile height, and the height may
-    # change between ticks
+    # order with the same arithmetic at any tile height (scan off), and the
+    # height may change between ticks
     t_end = 60_000
     specs = list(enumerate(STREAMS))
-    base, _ = serve(specs, t_end)
-    mixed, st = serve(specs, t_end, tile_hs={0: 4, 1: 16, 2: 4, 3: 16})
-    moved, _ = serve(specs, t_end, tile_hs={1: 4}, retile=(25_000, {0: 16, 1: 8, 2: 16, 3: 4}))
+    base, _ = serve(specs, t_end, scan_chain=33)
+    mixed, st = serve(specs, t_end, tile_hs={0: 4, 1: 16, 2: 4, 3: 16}, scan_chain=33)
+    moved, _ = serve(specs, t_end, tile_hs={1: 4}, retile=(25_000, {0: 16, 1: 8, 2: 16, 3: 4}),
+                     scan_chain=33)
     for other in (mixed, moved):
         for i in range(len(STREAMS)):
             fa, (Sa, Ta), _ = base[i]

@@ -119,7 +119,15 @@ typedef struct {
  * by event; its rounding then differs from the event-by-event loop by a few
  * units in the last place.  33 turns the scan off: every group runs event
  * by event in arrival order, and results are bit-identical across every
- * launch shape.  Default 8.
+ * launch shape.  Default 8.  split_rows (128-pixel rows only): 1 = a tile's
+ * rows are sorted as a whole and divided among its warps by work, a busy row
+ * split at record boundaries, the state at each split obtained by composing
+ * the events before it (the same clamped-affine maps); rounding then differs
+ * from the event-by-event loop by a few units in the last place at split
+ * rows.  2 = one warp per row, walking the tile's records batch by batch.
+ * 3 = rows sorted as a whole, one warp per row, no split (results as with
+ * 2).  Default 2: on the synthetic workloads of this library the split-row
+ * kernel runs about 1.4 times longer than the batch walk.
  */
 typedef struct {
     int32_t tile_h;
@@ -128,6 +136,7 @@ typedef struct {
     int32_t max_batch_events;
     int32_t tile_w;
     int32_t scan_chain;
+    int32_t split_rows;
 } esi_tuning;
 
 /* Per-kernel device time collected while profiling is on. */

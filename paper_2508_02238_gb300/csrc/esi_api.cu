@@ -101,6 +101,7 @@ int validate_tuning(const esi_tuning &t)
     if (!pow2(t.batch_records) || t.batch_records < 1024 || t.batch_records > 8192) return ESI_EINVAL;
     if (t.max_batch_events < t.chunk_events) return ESI_EINVAL;
     if (t.scan_chain < 1 || t.scan_chain > kScanNever) return ESI_EINVAL;
+    if (t.split_rows < 1 || t.split_rows > 3) return ESI_EINVAL;
     return ESI_OK;
 }
 
@@ -118,6 +119,10 @@ esi_tuning default_tuning(int W, int H)
     t.batch_records = large ? 2048 : 4096;
     t.max_batch_events = 1 << 22;
     t.scan_chain = kScanChainDefault;
+    // one warp per row, batch by batch: the split-row kernel is measured
+    // slower on the synthetic workloads (it executes about half as many
+    // instructions again as the batch walk per record)
+    t.split_rows = 2;
     return t;
 }
 
@@ -140,6 +145,10 @@ static int apply_tuning(esi_handle *h, const esi_tuning &t)
     if (tile_smem_bytes(t.tile_h, t.batch_records, max_chunks) + tile_static_smem_bytes(t.tile_h, t.tile_w) >
         (size_t)kMaxSmemPerBlock)
         return ESI_ERANGE;
+    // the split-row kernel keeps more per row and per batch in shared memory
+    h->split = t.tile_w == 128 && t.split_rows != 2 &&
+               tile_smem_bytes(t.tile_h, t.batch_records, max_chunks) +
+                       tile_split_static_smem_bytes(t.tile_h) <= (size_t)kMaxSmemPerBlock;
     return ESI_OK;
 }
 
@@ -518,6 +527,8 @@ void esi_destroy(esi_handle *h)
     cudaFree(h->diag);
     cudaFree(h->rec_idx[0]);
     cudaFree(h->rec_idx[1]);
+    cudaFree(h->srt);
+    cudaFree(h->srt_top);
     cudaFree(h->dstatus);
     cudaFreeHost(h->hstatus);
     cudaFreeHost(h->hwin);
@@ -762,6 +773,7 @@ int esi_set_tuning(esi_handle *h, const esi_tuning *t)
     if (!n.batch_records) n.batch_records = d.batch_records;
     if (!n.max_batch_events) n.max_batch_events = d.max_batch_events;
     if (!n.scan_chain) n.scan_chain = d.scan_chain;
+    if (!n.split_rows) n.split_rows = d.split_rows;
     int rc = validate_tuning(n);
     if (rc) return rc;
     esi_tuning old = h->tun;
@@ -964,6 +976,12 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
         if (!rc) rc = ensure_device(h, &h->hrow[b], &h->hrow_cap[b], max_chunks * (size_t)h->n_tiles);
         if (rc) return rc;
     }
+    if (h->split) {
+        // each tile's region has room for all its records in every row's part
+        rc = ensure_device(h, &h->srt, &h->srt_cap, (size_t)maxb * (size_t)tu.tile_h);
+        if (!rc) rc = ensure_device(h, &h->srt_top, &h->srt_top_cap, 1);
+        if (rc) return rc;
+    }
     // binning reads only the ring and its own scratch half: it may start
     // during the previous render's last tile kernel (the halves alternate
     // across renders), after device pushes queued on the handle's stream
@@ -1042,9 +1060,19 @@ int esi::render_impl(esi_handle *h, const int64_t *tf, int m, uint8_t *out, int 
         ta.batch = tu.batch_records;
         ta.status = h->dstatus;
         ta.scan_chain = tu.scan_chain;
+        if (h->split) {
+            // the split-row kernel hands every tile a region of the scratch
+            ta.srt = h->srt;
+            ta.srt_cap = h->srt_cap;
+            ta.srt_top = h->srt_top;
+            ta.max_splits = tu.split_rows == 1 ? kTileW : 0;
+            e = cudaMemsetAsync(h->srt_top, 0, sizeof(unsigned long long), h->tile_stream);
+            if (e != cudaSuccess) return cuda_fail(h, e);
+        }
         cudaEvent_t ev;
         rc = prof_begin(h, &ev, h->tile_stream);
-        if (!rc) rc = cuda_fail(h, launch_tile(ta, tu.tile_h, tu.tile_w, vec, h->tile_stream));
+        if (!rc) rc = cuda_fail(h, h->split ? launch_tile_split(ta, tu.tile_h, vec, h->tile_stream)
+                                            : launch_tile(ta, tu.tile_h, tu.tile_w, vec, h->tile_stream));
         if (!rc) rc = prof_end(h, kKindTile, ev, h->tile_stream);
         if (!rc) rc = cuda_fail(h, cudaEventRecord(h->ev_tile[buf], h->tile_stream));
         if (rc) return rc;

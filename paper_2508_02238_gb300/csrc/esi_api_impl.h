@@ -94,6 +94,14 @@ struct esi_handle {
     unsigned long long *rec[2] = {nullptr, nullptr};   // binned records of a sub-batch
     size_t rec_cap[2] = {0, 0};
     unsigned int *hrow[2] = {nullptr, nullptr};        // [chunk][tile] run table
+    // split-row tile kernel: whether it runs, the scratch of the tiles'
+    // row-sorted records (tile launches run one after another) and the
+    // counter handing out the tiles' regions
+    bool split = false;
+    unsigned long long *srt = nullptr;
+    size_t srt_cap = 0;
+    unsigned long long *srt_top = nullptr;
+    size_t srt_top_cap = 0;
     size_t hrow_cap[2] = {0, 0};
     esi::WinInfo *dwin = nullptr;        // per-frame constants of a render
     size_t dwin_cap = 0;

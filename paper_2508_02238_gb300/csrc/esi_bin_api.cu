@@ -34,6 +34,7 @@ extern "C" int esi_bin_events(int width, int height, const esi_tuning *shape,
     if (!t.batch_records) t.batch_records = 4096;
     if (!t.max_batch_events) t.max_batch_events = t.chunk_events;
     if (!t.scan_chain) t.scan_chain = kScanChainDefault;
+    if (!t.split_rows) t.split_rows = 2;
     int rc = validate_tuning(t);
     if (rc) return rc;
     const int tiles_x = (width + t.tile_w - 1) / t.tile_w;

@@ -93,6 +93,24 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// Close the thread's outstanding cp.async copies into one group; wait until
+// none of its groups is pending.
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_none()
+{
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Wait until at most one of the thread's groups is pending.
+__device__ __forceinline__ void cp_async_wait_one()
+{
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
 // Wait for phase `phase` of `bar` for at most limit_ns; false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase,
                                                   unsigned long long limit_ns)

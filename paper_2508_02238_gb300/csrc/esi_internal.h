@@ -128,6 +128,14 @@ struct TileArgs {
     // is composed by the segmented scan; shorter ones event by event
     // (kScanNever: always event by event, bit-identical across launch shapes)
     int scan_chain = kScanNever;
+    // split-row tile kernel (esi_tile_split.cuh): scratch for every tile's
+    // row-sorted records (srt_cap records; srt_top, zeroed before each
+    // launch, hands out the tiles' regions) and the most splits of a round
+    // (0: rows are walked whole, one warp each)
+    unsigned long long *srt = nullptr;
+    unsigned long long srt_cap = 0;
+    unsigned long long *srt_top = nullptr;
+    int max_splits = 0;
 };
 
 // One stream segment of a batched binning launch: the chunks
@@ -182,6 +190,10 @@ cudaError_t launch_tile(const TileArgs &a, int tile_h, int tile_w, bool vec, cud
 // renders no frame (a.w_begin == a.w_end).
 cudaError_t launch_tile_ev(const TileArgs &a, int tile_h, int tile_w, cudaStream_t s);
 cudaError_t launch_tile_w128(const TileArgs &a, int tile_h, bool vec, cudaStream_t s);
+// Split-row tile kernel (128-pixel rows; a.srt, a.srt_top set).
+cudaError_t launch_tile_split(const TileArgs &a, int tile_h, bool vec, cudaStream_t s);
+size_t tile_split_static_smem_bytes(int tile_h);
+cudaError_t set_tile_split_attributes();
 cudaError_t launch_tile_w32(const TileArgs &a, int tile_h, cudaStream_t s);
 cudaError_t launch_tile_w64(const TileArgs &a, int tile_h, bool vec, cudaStream_t s);
 cudaError_t launch_tile_ev_w128(const TileArgs &a, int tile_h, cudaStream_t s);

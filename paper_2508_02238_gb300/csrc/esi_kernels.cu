@@ -296,6 +296,7 @@ cudaError_t set_kernel_attributes()
     if (e == cudaSuccess) e = set_tile_attributes_w128();
     if (e == cudaSuccess) e = set_tile_attributes_w32();
     if (e == cudaSuccess) e = set_tile_attributes_w64();
+    if (e == cudaSuccess) e = set_tile_split_attributes();
     return e;
 }
 

@@ -125,6 +125,130 @@ __device__ __forceinline__ float scan_group(float4 *sc, bool valid, unsigned pee
     return v;
 }
 
+// A row's pixel state in shared memory as one warp walks it: S, F = (float)O
+// (for the decay view), O = T - t_base, and a lane mask word per pixel (kept
+// zero between groups).
+struct RowState {
+    float *S;
+    float *F;
+    long long *O;
+    unsigned *P;
+};
+
+// Alg. 2 for a group of due records (one per valid lane, time order):
+// S += p C; dt = t - T; S *= d(dt); T = t; clamp (Eq. 13).  Alg. 1 and Eq. 3
+// run the same loop with infinite clamp bounds, Eq. 3 adding p C after the
+// decay.  A record's dt needs only times (the previous record of its pixel in
+// the group, or T), so every decay of the group is evaluated at once; only
+// S = clamp((S + p C) d) runs in rank order per pixel, S passing from lane to
+// lane by shuffle: the same operations in the same order as the sequential
+// loop, so the result is bit-identical to it.  A group whose longest
+// same-pixel chain has scan_chain records or more is composed by the
+// segmented scan instead (scan_group).  Returns S after the lane's event;
+// the last record of each pixel writes the pixel's state back.
+template <int TWP, int RD, int DK>
+__device__ __forceinline__ float apply_group(const RowState &rs, float4 *sc, unsigned long long r,
+                                             bool valid, const DecayParams &dp,
+                                             const MapParams &mp, int scan_chain)
+{
+    const int lane = threadIdx.x & 31;
+    const int x = (int)((r >> 33) & (unsigned)(TWP - 1));
+    const unsigned toff = (unsigned)r;
+    // the pixel's state as the group starts (no lane writes it before the
+    // write-back below): loaded by every lane while the peers are found
+    const float s_mem = rs.S[x];
+    const long long o_mem = rs.O[x];
+    // lanes holding the same pixel: each sets its bit in the pixel's mask
+    // word, reads the word, and clears it for the next group
+    if (valid) atomicOr(&rs.P[x], 1u << lane);
+    __syncwarp();
+    const unsigned peers = valid ? rs.P[x] : 0u;
+    __syncwarp();
+    if (valid) rs.P[x] = 0u;
+    const unsigned below = peers & lanemask_lt();
+    const unsigned rank = __popc(below);
+    const int prev = below ? 31 - __clz(below) : lane;
+    const unsigned t_prev_rec = __shfl_sync(kFull, toff, prev);
+    const bool first = valid && rank == 0;
+    float s_in = first ? s_mem : 0.0f;
+    const long long t_prev = first ? o_mem : (long long)t_prev_rec;
+    const float d = valid ? decay_state_k<DK>((long long)toff - t_prev, dp) : 0.0f;
+    const float c = ((r >> 32) & 1u) ? mp.C : -mp.C;
+    const unsigned maxr = __reduce_max_sync(kFull, valid ? rank : 0u);
+    float s_out = 0.0f;
+    if ((int)maxr + 1 < scan_chain) {
+        for (unsigned k = 0;; ++k) {
+            if (valid && rank == k) s_out = event_step<DK>(s_in, c, d, dp, mp);
+            if (k == maxr) break;
+            const float got = __shfl_sync(kFull, s_out, prev);
+            if (valid && rank == k + 1) s_in = got;
+        }
+    } else {
+        s_out = scan_group<DK>(sc, valid, peers, rank, c, d, s_mem, maxr, dp, mp);
+    }
+    // the last record of each pixel writes its state back
+    if (valid && (peers >> lane) == 1u) {
+        rs.S[x] = s_out;
+        rs.O[x] = (long long)toff;
+        if (RD) rs.F[x] = __uint2float_rn(toff);
+    }
+    __syncwarp();
+    return s_out;
+}
+
+// Eq. 14 codes of the lane's PPL pixels at a frame (the decay view to the
+// frame time when RD): one 32-bit word (PPL = 4), one 16-bit word (PPL = 2)
+// when VEC, else byte by byte.  fr: the frame at the lane's first pixel.
+template <int PPL, int RD, int DK, bool VEC>
+__device__ __forceinline__ void emit_codes(const RowState &rs, unsigned char *fr, int nval, float tf_f,
+                                           const DecayParams &dp, const MapParams &mp)
+{
+    const int lane = threadIdx.x & 31;
+    if constexpr (PPL == 4) {
+        const float4 s4 = *reinterpret_cast<const float4 *>(rs.S + 4 * lane);
+        float v[4] = {s4.x, s4.y, s4.z, s4.w};
+        if (RD) {
+            const float4 f4 = *reinterpret_cast<const float4 *>(rs.F + 4 * lane);
+            v[0] *= decay_view_k<DK>(tf_f - f4.x, dp);
+            v[1] *= decay_view_k<DK>(tf_f - f4.y, dp);
+            v[2] *= decay_view_k<DK>(tf_f - f4.z, dp);
+            v[3] *= decay_view_k<DK>(tf_f - f4.w, dp);
+        }
+        unsigned code[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) code[q] = quantize_u8(fmaf(v[q], mp.scale, mp.offs));
+        if (VEC) {
+            if (nval == 4)
+                *reinterpret_cast<unsigned *>(fr) =
+                    code[0] | (code[1] << 8) | (code[2] << 16) | (code[3] << 24);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < nval) fr[q] = (unsigned char)code[q];
+        }
+    } else if constexpr (PPL == 2) {
+        const float2 s2 = *reinterpret_cast<const float2 *>(rs.S + 2 * lane);
+        float v0 = s2.x, v1 = s2.y;
+        if (RD) {
+            const float2 f2 = *reinterpret_cast<const float2 *>(rs.F + 2 * lane);
+            v0 *= decay_view_k<DK>(tf_f - f2.x, dp);
+            v1 *= decay_view_k<DK>(tf_f - f2.y, dp);
+        }
+        const unsigned c0 = quantize_u8(fmaf(v0, mp.scale, mp.offs));
+        const unsigned c1 = quantize_u8(fmaf(v1, mp.scale, mp.offs));
+        if (VEC) {
+            if (nval == 2) *reinterpret_cast<unsigned short *>(fr) = (unsigned short)(c0 | (c1 << 8));
+        } else {
+            if (nval > 0) fr[0] = (unsigned char)c0;
+            if (nval > 1) fr[1] = (unsigned char)c1;
+        }
+    } else {
+        float v = rs.S[lane];
+        if (RD) v *= decay_view_k<DK>(tf_f - rs.F[lane], dp);
+        if (nval) fr[0] = (unsigned char)quantize_u8(fmaf(v, mp.scale, mp.offs));
+    }
+}
+
 // One block per (32 PPL) x TH tile; warp w owns tile row w, lane l owns the
 // PPL pixels x = PPL l .. PPL l + PPL - 1 of that row for loads, stores and
 // frame codes (PPL = 4: 128-pixel rows; PPL = 2: 64-pixel rows; PPL = 1:
@@ -233,60 +357,12 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
     }
 
 
-    // Alg. 2 for a group of due records (one per valid lane, time order):
-    // S += p C; dt = t - T; S *= d(dt); T = t; clamp (Eq. 13).  Alg. 1 and
-    // Eq. 3 run the same loop with infinite clamp bounds, Eq. 3 adding p C
-    // after the decay.  A record's dt
-    // needs only times (the previous record of its pixel in the group, or T),
-    // so every decay of the group is evaluated at once; only
-    // S = clamp((S + p C) d) runs in rank order per pixel, S passing from
-    // lane to lane by shuffle.  Same operations in the same order as the
-    // sequential loop, so the result is bit-identical to it.
-    auto apply_group = [&](unsigned long long r, bool valid, unsigned ev_idx) {
-        const int x = (int)((r >> 33) & (unsigned)(TWP - 1));
-        const unsigned toff = (unsigned)r;
-        // the pixel's state as the group starts (no lane writes it before the
-        // write-back below): loaded by every lane while the peers are found
-        const float s_mem = rS[x];
-        const long long o_mem = rO[x];
-        // lanes holding the same pixel: each sets its bit in the pixel's
-        // mask word, reads the word, and clears it for the next group
-        if (valid) atomicOr(&rP[x], 1u << lane);
-        __syncwarp();
-        const unsigned peers = valid ? rP[x] : 0u;
-        __syncwarp();
-        if (valid) rP[x] = 0u;
-        const unsigned below = peers & lanemask_lt();
-        const unsigned rank = __popc(below);
-        const int prev = below ? 31 - __clz(below) : lane;
-        const unsigned t_prev_rec = __shfl_sync(kFull, toff, prev);
-        const bool first = valid && rank == 0;
-        float s_in = first ? s_mem : 0.0f;
-        const long long t_prev = first ? o_mem : (long long)t_prev_rec;
-        const float d = valid ? decay_state_k<DK>((long long)toff - t_prev, dp) : 0.0f;
-        const float c = ((r >> 32) & 1u) ? mp.C : -mp.C;
-        const unsigned maxr = __reduce_max_sync(kFull, valid ? rank : 0u);
-        float s_out = 0.0f;
-        if ((int)maxr + 1 < a.scan_chain) {
-            for (unsigned k = 0;; ++k) {
-                if (valid && rank == k) s_out = event_step<DK>(s_in, c, d, dp, mp);
-                if (k == maxr) break;
-                const float got = __shfl_sync(kFull, s_out, prev);
-                if (valid && rank == k + 1) s_in = got;
-            }
-        } else {
-            s_out = scan_group<DK>(sScan[warp], valid, peers, rank, c, d, s_mem, maxr, dp, mp);
-        }
+    const RowState rs{rS, rF, rO, rP};
+    auto apply = [&](unsigned long long r, bool valid, unsigned ev_idx) {
+        const float s_out = apply_group<TWP, RD, DK>(rs, sScan[warp], r, valid, dp, mp, a.scan_chain);
         if constexpr (EV) {
             if (valid) a.ev_out[ev_idx] = s_out;
         }
-        // the last record of each pixel writes its state back
-        if (valid && (peers >> lane) == 1u) {
-            rS[x] = s_out;
-            rO[x] = (long long)toff;
-            if (RD) rF[x] = __uint2float_rn(toff);
-        }
-        __syncwarp();
     };
 
     int wi = a.w_begin;
@@ -377,7 +453,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
                 }
                 const unsigned vm = __ballot_sync(kFull, valid);
                 if (vm == 0u) break;
-                apply_group(r, valid, EV && valid ? IB[k] : 0u);
+                apply(r, valid, EV && valid ? IB[k] : 0u);
                 const int nv = __popc(vm);
                 cur += nv;
                 if (nv < 32) break;
@@ -385,56 +461,14 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
             // Eq. 14 codes of the lane's pixels at this frame
             unsigned char *fr =
                 (a.frame_outs ? a.frame_outs[wi] : a.frames + (long long)wi * a.P) + pix0;
-            if constexpr (PPL == 4) {
-                const float4 s4 = *reinterpret_cast<const float4 *>(rS + 4 * lane);
-                float v[4] = {s4.x, s4.y, s4.z, s4.w};
-                if (RD) {
-                    const float4 f4 = *reinterpret_cast<const float4 *>(rF + 4 * lane);
-                    v[0] *= decay_view_k<DK>(wv.tf_f - f4.x, dp);
-                    v[1] *= decay_view_k<DK>(wv.tf_f - f4.y, dp);
-                    v[2] *= decay_view_k<DK>(wv.tf_f - f4.z, dp);
-                    v[3] *= decay_view_k<DK>(wv.tf_f - f4.w, dp);
-                }
-                unsigned code[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) code[q] = quantize_u8(fmaf(v[q], mp.scale, mp.offs));
-                if (VEC) {
-                    if (nval == 4)
-                        *reinterpret_cast<unsigned *>(fr) =
-                            code[0] | (code[1] << 8) | (code[2] << 16) | (code[3] << 24);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (q < nval) fr[q] = (unsigned char)code[q];
-                }
-            } else if constexpr (PPL == 2) {
-                const float2 s2 = *reinterpret_cast<const float2 *>(rS + 2 * lane);
-                float v0 = s2.x, v1 = s2.y;
-                if (RD) {
-                    const float2 f2 = *reinterpret_cast<const float2 *>(rF + 2 * lane);
-                    v0 *= decay_view_k<DK>(wv.tf_f - f2.x, dp);
-                    v1 *= decay_view_k<DK>(wv.tf_f - f2.y, dp);
-                }
-                const unsigned c0 = quantize_u8(fmaf(v0, mp.scale, mp.offs));
-                const unsigned c1 = quantize_u8(fmaf(v1, mp.scale, mp.offs));
-                if (VEC) {
-                    if (nval == 2) *reinterpret_cast<unsigned short *>(fr) = (unsigned short)(c0 | (c1 << 8));
-                } else {
-                    if (nval > 0) fr[0] = (unsigned char)c0;
-                    if (nval > 1) fr[1] = (unsigned char)c1;
-                }
-            } else {
-                float v = rS[lane];
-                if (RD) v *= decay_view_k<DK>(wv.tf_f - rF[lane], dp);
-                if (nval) fr[0] = (unsigned char)quantize_u8(fmaf(v, mp.scale, mp.offs));
-            }
+            emit_codes<PPL, RD, DK, VEC>(rs, fr, nval, wv.tf_f, dp, mp);
             ++wi;
         }
         // the rest of this batch's row precedes the next batch's records
         for (; cur < re; cur += 32) {
             const int k = cur + lane;
             const bool valid = k < re;
-            apply_group(valid ? B[k] : 0ull, valid, EV && valid ? IB[k] : 0u);
+            apply(valid ? B[k] : 0ull, valid, EV && valid ? IB[k] : 0u);
         }
         if (last) break;
         __syncthreads();  // A, B, rcnt are rewritten by the next batch

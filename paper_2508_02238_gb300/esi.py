@@ -44,7 +44,8 @@ class esi_stats(ctypes.Structure):
 class esi_tuning(ctypes.Structure):
     _fields_ = [("tile_h", ctypes.c_int32), ("chunk_events", ctypes.c_int32),
                 ("batch_records", ctypes.c_int32), ("max_batch_events", ctypes.c_int32),
-                ("tile_w", ctypes.c_int32), ("scan_chain", ctypes.c_int32)]
+                ("tile_w", ctypes.c_int32), ("scan_chain", ctypes.c_int32),
+                ("split_rows", ctypes.c_int32)]
 
 
 class esi_kernel_time(ctypes.Structure):

@@ -11,9 +11,9 @@ Tolerances (written here, used by every parity test):
   FP64 in the oracle; a value within rounding of a .5 boundary may differ).
 
 Results are bit-identical across launch shapes only with the segmented scan
-off (tuning scan_chain = 33, EXACT below): the scan composes a group's events
-in another order of rounding, and which records form a group depends on the
-shape.
+off and rows walked whole (tuning scan_chain = 33, split_rows = 3: EXACT
+below): the scan and the row splits compose events in another order of
+rounding, and which records they compose depends on the shape.
 """
 from __future__ import annotations
 
@@ -23,8 +23,8 @@ import oracle
 from synth import EVENT_DTYPE
 
 STATE_TOL = 1e-5
-# launch-shape knob that keeps every group on the event-by-event loop
-EXACT = {"scan_chain": 33}
+# launch-shape knobs that keep every event on the event-by-event loop
+EXACT = {"scan_chain": 33, "split_rows": 3}
 
 
 def oracle_params(p) -> oracle.OracleParams:
@@ -84,6 +84,7 @@ class GpuStream:
             t.max_batch_events = tuning.get("max_batch_events", 0)
             t.tile_w = tuning.get("tile_w", 0)
             t.scan_chain = tuning.get("scan_chain", 0)
+            t.split_rows = tuning.get("split_rows", 0)
             esi.check(esi.esi_set_tuning(self.h, t), "esi_set_tuning")
 
     def push(self, events, on_device=False):

@@ -523,29 +523,51 @@ MIXED_SECONDS = 5.0
 SERVING_PARAMS = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1)
 
 
-def _packets(esi, items):
-    items.sort(key=lambda x: (x[0], x[1], x[2]))
-    pk = (esi.esi_packet * len(items))()
-    for j, (a, _, k, p_, n, kind) in enumerate(items):
-        pk[j].stream, pk[j].kind, pk[j].arrival_us, pk[j].ev, pk[j].n = k, kind, a, p_, n
-    return pk
+# esi_packet as numpy sees it (same layout as the C struct)
+PACKET_DTYPE = np.dtype([("stream", "<i4"), ("kind", "<i4"), ("arrival_us", "<i8"),
+                         ("ev", "<u8"), ("n", "<u8")])
+SCENE_SECONDS = 0.5   # serving scenes are generated this long and repeated in time
 
 
-def _event_items(esi, k, ev, arr):
-    items, lo = [], 0
+def _packets(esi, parts):
+    """parts: arrays of PACKET_DTYPE plus an 'order' key (0 open, 1 events,
+    2 close) for packets of one arrival time; sorted by (arrival, order,
+    stream) into one esi_packet array."""
+    allp = np.concatenate([p[0] for p in parts])
+    order = np.concatenate([p[1] for p in parts])
+    idx = np.lexsort((allp["stream"], order, allp["arrival_us"]))
+    allp = np.ascontiguousarray(allp[idx])
+    import ctypes
+    assert PACKET_DTYPE.itemsize == ctypes.sizeof(esi.esi_packet)
+    pk = (esi.esi_packet * len(allp))()
+    np.frombuffer(pk, dtype=PACKET_DTYPE)[:] = allp
+    return pk, len(allp)
+
+
+def _event_part(esi, k, ev, arr):
+    """One stream's event packets: each arrival carries the events since
+    the previous one."""
     cuts = np.searchsorted(ev["t"], arr, side="right")
-    for a, hi in zip(arr.tolist(), cuts.tolist()):
-        items.append((a, 1, k, ev.ctypes.data + lo * 16, hi - lo, esi.ESI_PACKET_EVENTS))
-        lo = hi
-    return items
+    lo = np.concatenate([[0], cuts[:-1]])
+    p = np.zeros(len(arr), dtype=PACKET_DTYPE)
+    p["stream"], p["kind"], p["arrival_us"] = k, esi.ESI_PACKET_EVENTS, arr
+    p["ev"] = ev.ctypes.data + lo.astype(np.uint64) * 16
+    p["n"] = (cuts - lo).astype(np.uint64)
+    return p, np.ones(len(arr), dtype=np.int8)
 
 
-def serving_64(seconds):
+def _one_packet(esi, k, kind, t, ptr=0):
+    p = np.zeros(1, dtype=PACKET_DTYPE)
+    p["stream"], p["kind"], p["arrival_us"], p["ev"] = k, kind, t, ptr
+    return p, np.array([0 if kind == esi.ESI_PACKET_OPEN else 2], dtype=np.int8)
+
+
+def serving_64(seconds, scene_s=None):
     """The 64-stream workload: (rates, streams with generated events)."""
     import synth
-    rates, streams = synth.serving_streams(64, seconds)
+    rates, streams = synth.serving_streams(64, seconds, scene_s=scene_s)
     for s in streams:
-        s["events"] = synth.generate(s["scene"])
+        s["events"] = synth.stream_events(s)
     return rates, streams
 
 
@@ -556,6 +578,8 @@ def _stats(st, dt, realtime, n_ev, expected=None):
          "packet_to_frame_p50_ms": st.packet_latency_p50_ms,
          "packet_to_frame_p99_ms": st.packet_latency_p99_ms,
          "gpu_ms_per_tick": st.gpu_ms_per_tick,
+         "gpu_tick_p99_ms": st.gpu_tick_p99_ms,
+         "host_tick_p50_ms": st.host_tick_p50_ms, "host_tick_p99_ms": st.host_tick_p99_ms,
          "kernel_launches_per_tick": int(st.kernel_launches_per_tick),
          "wall_s": dt, "events_per_s": n_ev / dt if not realtime else None,
          "frames_per_s": st.frames / dt}
@@ -566,8 +590,9 @@ def _stats(st, dt, realtime, n_ev, expected=None):
 
 def serving_leg(esi, seconds=SERVING_SECONDS):
     """Batched (one graph per tick) vs plain (per-stream launches), paced by
-    the wall clock, and batched as fast as possible: 64 streams of 346x260."""
-    rates, streams = serving_64(seconds)
+    the wall clock, and batched as fast as possible: 64 streams of 346x260
+    (each stream's scene generated for SCENE_SECONDS and repeated)."""
+    rates, streams = serving_64(seconds, SCENE_SECONDS)
     t_end = int(round(seconds * 1e6))
     n_ev = int(sum(len(s["events"]) for s in streams))
     params = esi.make_params(**SERVING_PARAMS)
@@ -579,44 +604,43 @@ def serving_leg(esi, seconds=SERVING_SECONDS):
     for mode in ("batched", "batched_throughput"):
         rc, srv = esi.esi_server_create(1 << 30, None, 0)
         esi.check(rc, "server")
-        items = []
+        parts = []
         for k, s in enumerate(streams):
             rc, sid = esi.esi_stream_open(srv, s["W"], s["H"], params)
             esi.check(rc, "open")
-            items += _event_items(esi, sid, s["events"], s["arrivals"])
-        pk = _packets(esi, items)
+            parts.append(_event_part(esi, sid, s["events"], s["arrivals"]))
+        pk, npk = _packets(esi, parts)
         realtime = 1 if mode == "batched" else 0
         t0 = time.perf_counter()
-        esi.check(esi.esi_server_run(srv, pk, len(items), 1000, t_end, realtime), "run")
+        esi.check(esi.esi_server_run(srv, pk, npk, 1000, t_end, realtime), "run")
         dt = time.perf_counter() - t0
         rc, st = esi.esi_server_get_stats(srv)
         esi.esi_server_destroy(srv)
         out[mode] = _stats(st, dt, realtime, n_ev, expected)
-    items = []
-    for k, s in enumerate(streams):
-        items += _event_items(esi, k, s["events"], s["arrivals"])
-    pk = _packets(esi, items)
+    pk, npk = _packets(esi, [_event_part(esi, k, s["events"], s["arrivals"])
+                             for k, s in enumerate(streams)])
     t0 = time.perf_counter()
     rc, st = esi.esi_plain_run([s["W"] for s in streams], [s["H"] for s in streams],
-                               [params] * len(streams), pk, len(items), 1000, t_end, WINDOW_US, 1)
+                               [params] * len(streams), pk, npk, 1000, t_end, WINDOW_US, 1)
     esi.check(rc, "plain")
     out["plain"] = _stats(st, time.perf_counter() - t0, 1, n_ev, expected)
     return out
 
 
-def mixed_workload(esi, seconds, sinks=False):
+def mixed_workload(esi, seconds, sinks=False, scene_s=None):
     """Mixed resolutions with join/leave: 16 x 1280x720 (checkerboard form),
     48 x 640x480 (blob form), 128 x 346x260 (sinusoid form) streams, lognormal
     rates in [0.1, 20] Mev/s, Poisson packets (1 ms mean), a quarter joining
-    in the first half and a fifth leaving in the second.  Returns the
-    workload, its packets, specs and per-stream events (and frame sinks)."""
+    in the first half and a fifth leaving in the second (scenes generated
+    for at most scene_s and repeated).  Returns the workload, its packets,
+    specs and per-stream events (and frame sinks)."""
     import ctypes
     import synth
-    ws = synth.mixed_serving(duration_s=seconds)
+    ws = synth.mixed_serving(duration_s=seconds, scene_s=scene_s)
     arrs = synth.mixed_arrivals(ws, duration_s=seconds)
     t_end = int(round(seconds * 1e6))
-    evs = [synth.generate(w["scene"]) for w in ws]
-    specs, items, sink = [], [], []
+    evs = [synth.stream_events(w) for w in ws]
+    specs, parts, sink = [], [], []
     tile_h = {2: 16, 1: 8, 0: 8}
     for k, (w, arr) in enumerate(zip(ws, arrs)):
         sp = esi.esi_stream_spec()
@@ -631,18 +655,19 @@ def mixed_workload(esi, seconds, sinks=False):
             sp.frame_sink, sp.sink_frames, sp.sink_t_frames = buf.ctypes.data, nf, tfs.ctypes.data
             sink.append((buf, tfs, nf))
         specs.append(sp)
-        items.append((w["t_join_us"], 0, k, ctypes.addressof(sp), 0, esi.ESI_PACKET_OPEN))
-        items += _event_items(esi, k, evs[k], arr)
+        parts.append(_one_packet(esi, k, esi.ESI_PACKET_OPEN, w["t_join_us"], ctypes.addressof(sp)))
+        parts.append(_event_part(esi, k, evs[k], arr))
         if w["t_leave_us"] is not None:
-            items.append((t1, 2, k, 0, 0, esi.ESI_PACKET_CLOSE))
-    return ws, _packets(esi, items), len(items), specs, evs, sink
+            parts.append(_one_packet(esi, k, esi.ESI_PACKET_CLOSE, t1))
+    pk, npk = _packets(esi, parts)
+    return ws, pk, npk, specs, evs, sink
 
 
 def mixed_serving_leg(esi, seconds=SERVING_SECONDS):
     """Mixed-resolution serving: batched, paced by the wall clock, and as
     fast as possible; 100 frames/s per stream, admission by state memory."""
     t_end = int(round(seconds * 1e6))
-    ws, pk, npk, specs, evs, _ = mixed_workload(esi, seconds)
+    ws, pk, npk, specs, evs, _ = mixed_workload(esi, seconds, scene_s=SCENE_SECONDS)
     budget = 768 << 20
     opts = esi.esi_server_opts()
     opts.use_graph, opts.max_streams = 1, 256
@@ -886,7 +911,7 @@ def _parity_serving_64(esi, oracle, seconds=0.25):
     params = esi.make_params(**SERVING_PARAMS)
     rc, srv = esi.esi_server_create(1 << 30, None, 0)
     esi.check(rc, "server")
-    items, sinks, ids = [], [], []
+    parts, sinks, ids = [], [], []
     for s in streams:
         rc, sid = esi.esi_stream_open(srv, s["W"], s["H"], params)
         esi.check(rc, "open")
@@ -895,9 +920,9 @@ def _parity_serving_64(esi, oracle, seconds=0.25):
         esi.check(esi.esi_stream_set_frame_sink(srv, sid, buf, nf, tfs), "sink")
         sinks.append((buf, tfs))
         ids.append(sid)
-        items += _event_items(esi, sid, s["events"], s["arrivals"])
-    pk = _packets(esi, items)
-    esi.check(esi.esi_server_run(srv, pk, len(items), 1000, t_end, 0), "run")
+        parts.append(_event_part(esi, sid, s["events"], s["arrivals"]))
+    pk, npk = _packets(esi, parts)
+    esi.check(esi.esi_server_run(srv, pk, npk, 1000, t_end, 0), "run")
     acc = ParityAcc()
     for s, sid, (buf, tfs) in zip(streams, ids, sinks):
         S = np.empty(s["W"] * s["H"], dtype=np.float32)

@@ -381,6 +381,9 @@ typedef struct {
     uint64_t streams_admitted;    /* esi_stream_open calls that succeeded     */
     uint64_t streams_refused;     /* ESI_EBUSY answers (admission refused)    */
     uint64_t events_refused;      /* executor events of refused streams      */
+    double host_tick_p50_ms;      /* host time of a tick call with work: packing */
+    double host_tick_p99_ms;      /*   the events and tables, queueing the work  */
+    double gpu_tick_p99_ms;       /* device time of a tick's kernels, 99th pct  */
 } esi_server_stats;
 
 typedef struct esi_server esi_server;

@@ -55,7 +55,7 @@ struct DevStatus {
 // words per warp in shared memory, indexed by tile mod kBinMaskSlots, and one
 // ballot per higher tile-index bit (or, without the words, one ballot per
 // tile-index bit).
-constexpr int kBinMaskSlotBits = 7;
+constexpr int kBinMaskSlotBits = 8;
 constexpr int kBinMaskSlots = 1 << kBinMaskSlotBits;
 
 // Result of a device-checked push: an order violation anywhere, and the time
@@ -206,6 +206,8 @@ cudaError_t set_tile_attributes_w32();
 cudaError_t set_tile_attributes_w64();
 cudaError_t launch_bin_batch_tab(const unsigned char *tab, int grid, int chunk, int max_tiles,
                                  bool mask, cudaStream_t s);
+// Resident blocks per SM of the batched binning kernel (its persistent grid).
+int bin_tab_blocks_per_sm(int chunk, int max_tiles, bool mask);
 cudaError_t launch_tile_batch_tab(const unsigned char *tab, int group, int grid, int tile_h, int rd,
                                   int dk, bool vec, int batch, int max_chunks, cudaStream_t s);
 int decay_kind_of(const DecayParams &dp);

@@ -112,9 +112,12 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
         if (n1 < nc) bulk_g2s_stream(sev + n1, a.ring, (unsigned)(nc - n1) * 16u, &bar);
     }
     __shared__ int s_copy_ok;
-    for (int i = tid; i < NW * ntp; i += NT) cnt[i] = 0;
+    // counters (NW * ntp u16, a multiple of 8, 16-byte aligned) and mask
+    // words to zero, 16 bytes at a time
+    for (int i = tid; i < NW * ntp / 8; i += NT) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (use_mask)
-        for (int i = tid; i < NW * kBinMaskSlots; i += NT) tmask[i] = 0u;
+        for (int i = tid; i < NW * kBinMaskSlots / 4; i += NT)
+            reinterpret_cast<uint4 *>(tmask)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
         // one thread waits for the copy; the others sleep at the barrier
         int ok = mbar_wait_bounded(&bar, 0, kWaitLimitNs) ? 1 : 0;
@@ -193,15 +196,20 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
     if (lane == 0 && drop) atomicAdd(&s_drop, drop);
     __syncthreads();
 
-    // phase 2: warp offsets within each tile, tile starts within the chunk
-    for (int j = tid; j < n_tiles; j += NT) {
-        unsigned run = 0;
+    // phase 2: warp offsets within each tile, tile starts within the chunk;
+    // two tiles per 32-bit word of counters (counts stay below 2^16)
+    for (int j2 = tid; j2 < ntp / 2; j2 += NT) {
+        unsigned run_lo = 0, run_hi = 0;
         for (int w = 0; w < NW; ++w) {
-            const unsigned v = cnt[w * ntp + j];
-            cnt[w * ntp + j] = (unsigned short)run;
-            run += v;
+            unsigned *p2 = reinterpret_cast<unsigned *>(cnt + w * ntp) + j2;
+            const unsigned v = *p2;
+            *p2 = run_lo | (run_hi << 16);
+            run_lo += v & 0xffffu;
+            run_hi += v >> 16;
         }
-        tstart[j] = run;
+        const int j = 2 * j2;
+        if (j < n_tiles) tstart[j] = run_lo;
+        if (j + 1 < n_tiles) tstart[j + 1] = run_hi;
     }
     __syncthreads();
     const unsigned total = block_exclusive_scan<NT>(tstart, n_tiles, scan_tmp);
@@ -234,18 +242,20 @@ __global__ void __launch_bounds__(kBinThreads) esi_bin_kernel(BinArgs a) { bin_c
 
 __global__ void __launch_bounds__(kBinThreads) esi_bin_ev_kernel(BinArgs a) { bin_chunk<true>(a, blockIdx.x); }
 
-// Batched binning of a serving tick: block c bins chunk c of the tick; the
-// tick directory names the stream segment (job) each chunk belongs to.  The
-// grid is sized for the capacity; blocks past the tick's chunks return.
+// Batched binning of a serving tick: a persistent grid walks the tick's
+// chunks; the tick directory names the stream segment (job) each chunk
+// belongs to.
 __global__ void __launch_bounds__(kBinThreads) esi_bin_tab_kernel(const unsigned char *tab)
 {
     const TickDir *d = reinterpret_cast<const TickDir *>(tab);
-    const int c = blockIdx.x;
-    if (c >= d->n_chunks) return;
+    const int n = d->n_chunks;
     const BinJob *jobs = reinterpret_cast<const BinJob *>(tab + d->off_binjob);
     const int *cj = reinterpret_cast<const int *>(tab + d->off_chunkjob);
-    const BinJob &j = jobs[cj[c]];
-    bin_chunk(j.args, c - j.first_chunk);
+    for (int c = blockIdx.x; c < n; c += gridDim.x) {
+        const BinJob &j = jobs[cj[c]];
+        bin_chunk(j.args, c - j.first_chunk);
+        __syncthreads();  // shared memory (and the copy barrier) serve the next chunk
+    }
 }
 
 // Dynamic shared memory a kernel may ask for: the 227 KB per block minus its
@@ -308,6 +318,17 @@ cudaError_t launch_bin(const BinArgs &a, int n_chunks, cudaStream_t s)
     else
         esi_bin_kernel<<<n_chunks, kBinThreads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+int bin_tab_blocks_per_sm(int chunk, int max_tiles, bool mask)
+{
+    int nb = 0;
+    const size_t smem = bin_smem_bytes(chunk, max_tiles, mask);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, esi_bin_tab_kernel, kBinThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
 }
 
 cudaError_t launch_bin_batch_tab(const unsigned char *tab, int grid, int chunk, int max_tiles,

@@ -182,6 +182,7 @@ struct esi_server {
     // capacities of one tick
     int cap_jobs = 0, cap_chunks = 0, cap_items = 0, cap_frames = 0, max_tiles = 0;
     int tile_grid = 0;  // persistent grid of the batched tile kernel
+    int bin_grid = 0;   // persistent grid of the batched binning kernel
     bool bin_mask = false;  // binning finds same-tile lanes by mask words
     long long cap_events = 0;
     size_t off_binjob = 0, off_chunkjob = 0, off_tilejob = 0, off_items = 0, off_win = 0,
@@ -204,7 +205,7 @@ struct esi_server {
     std::vector<cudaEvent_t> ev_pool;
 
     // statistics since the last reset
-    std::vector<double> frame_lat, pkt_lat;
+    std::vector<double> frame_lat, pkt_lat, host_tick, gpu_tick;
     unsigned long long n_ticks = 0, n_frames = 0, n_events = 0, n_packets = 0;
     unsigned long long n_admitted = 0, n_refused = 0, n_events_refused = 0;
     double gpu_ms = 0.0;
@@ -240,6 +241,7 @@ void poll(esi_server *s)
         if (cudaEventElapsedTime(&ms, t->ev0, t->ev1) == cudaSuccess) {
             s->gpu_ms += ms;
             s->gpu_n += 1;
+            s->gpu_tick.push_back(ms);
         }
         s->ev_pool.push_back(t->ev0);
         s->ev_pool.push_back(t->ev1);
@@ -301,7 +303,7 @@ int build_graph(esi_server *s, unsigned long long groups)
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess)
-        e = launch_bin_batch_tab(s->dtab, s->cap_chunks, kChunk, s->max_tiles, s->bin_mask, cs);
+        e = launch_bin_batch_tab(s->dtab, s->bin_grid, kChunk, s->max_tiles, s->bin_mask, cs);
     for (int gi = 0; gi < kGroups && e == cudaSuccess; ++gi)
         if (groups & (1ull << gi)) e = launch_group(s, gi, cs);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(cs, on_tick_done, s->comp);
@@ -418,6 +420,8 @@ int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts, vo
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
         s->tile_grid = std::max(1, sms) * 2;
+        s->bin_grid = std::min(s->cap_chunks,
+                               std::max(1, sms) * bin_tab_blocks_per_sm(kChunk, s->max_tiles, s->bin_mask));
     }
     if (e == cudaSuccess) {
         if (cuda_stream) {
@@ -843,7 +847,7 @@ int esi_server_tick(esi_server *s, int64_t now_us)
             for (int g = 0; g < kGroups; ++g) ng += (int)((s->graph_groups >> g) & 1ull);
             s->launches_per_tick = 1 + ng;
         } else {
-            e = launch_bin_batch_tab(s->dtab, s->cap_chunks, kChunk, s->max_tiles, s->bin_mask, s->stream);
+            e = launch_bin_batch_tab(s->dtab, s->bin_grid, kChunk, s->max_tiles, s->bin_mask, s->stream);
             for (int g = 0; g < kGroups && e == cudaSuccess; ++g)
                 if (groups & (1ull << g)) e = launch_group(s, g, s->stream);
             if (e == cudaSuccess) e = cudaLaunchHostFunc(s->stream, on_tick_done, s->comp);
@@ -859,6 +863,7 @@ int esi_server_tick(esi_server *s, int64_t now_us)
     s->inflight.push_back(rec);
     s->n_ticks += 1;
     s->n_events += (unsigned long long)n_ev;
+    s->host_tick.push_back((double)(wall_ns() - call_ns) * 1e-6);
     return ESI_OK;
 }
 
@@ -968,6 +973,9 @@ int esi_server_get_stats(esi_server *s, esi_server_stats *out)
     out->streams_admitted = s->n_admitted;
     out->streams_refused = s->n_refused;
     out->events_refused = s->n_events_refused;
+    out->host_tick_p50_ms = percentile(s->host_tick, 0.50);
+    out->host_tick_p99_ms = percentile(s->host_tick, 0.99);
+    out->gpu_tick_p99_ms = percentile(s->gpu_tick, 0.99);
     return ESI_OK;
 }
 
@@ -977,6 +985,8 @@ int esi_server_reset_stats(esi_server *s)
     poll(s);
     s->frame_lat.clear();
     s->pkt_lat.clear();
+    s->host_tick.clear();
+    s->gpu_tick.clear();
     s->n_ticks = s->n_frames = s->n_events = s->n_packets = 0;
     s->n_admitted = s->n_refused = s->n_events_refused = 0;
     s->gpu_ms = 0.0;

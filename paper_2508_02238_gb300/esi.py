@@ -70,7 +70,8 @@ class esi_server_stats(ctypes.Structure):
                 ("state_budget_bytes", ctypes.c_uint64), ("streams_open", ctypes.c_int32),
                 ("kernel_launches_per_tick", ctypes.c_int32),
                 ("streams_admitted", ctypes.c_uint64), ("streams_refused", ctypes.c_uint64),
-                ("events_refused", ctypes.c_uint64)]
+                ("events_refused", ctypes.c_uint64), ("host_tick_p50_ms", ctypes.c_double),
+                ("host_tick_p99_ms", ctypes.c_double), ("gpu_tick_p99_ms", ctypes.c_double)]
 
 
 ESI_PACKET_EVENTS, ESI_PACKET_OPEN, ESI_PACKET_CLOSE = 0, 1, 2

@@ -247,7 +247,8 @@ C0_MAX_RATE = 8.0e6
 
 def mixed_serving(duration_s: float = 0.25, seed: int = 1004, counts=(16, 48, 128),
                   median: float = 1.0e6, sigma: float = 1.0, lo: float = 0.1e6,
-                  hi: float = 20.0e6, late_join: float = 0.25, leave: float = 0.2):
+                  hi: float = 20.0e6, late_join: float = 0.25, leave: float = 0.2,
+                  scene_s: float | None = None):
     """Mixed-resolution serving workload: counts[0] 1280x720 checkerboard form,
     counts[1] 640x480 blob form and counts[2] 346x260 sinusoid form
     streams.  Rates are lognormal(median, sigma) clipped to [lo, hi] and to
@@ -256,8 +257,11 @@ def mixed_serving(duration_s: float = 0.25, seed: int = 1004, counts=(16, 48, 12
     a seeded time in the second half.  Each stream's scene starts at its join
     time and ends at its leave time (or duration_s).
 
+    scene_s: generate at most this much of each scene and repeat it in time
+    (stream_events).
+
     Returns a list of dicts: form, W, H, rate, t_join_us, t_leave_us (None if
-    it stays), scene.
+    it stays), t_end_us (its leave time or the end), scene.
     """
     rng = np.random.default_rng(seed)
     forms = [2] * counts[0] + [1] * counts[1] + [0] * counts[2]
@@ -268,6 +272,8 @@ def mixed_serving(duration_s: float = 0.25, seed: int = 1004, counts=(16, 48, 12
         t_join = int(rng.integers(1, D // 2000)) * 1000 if rng.random() < late_join else 0
         t_leave = int(rng.integers(D // 2000, D // 1000)) * 1000 if rng.random() < leave else None
         dur = ((t_leave if t_leave is not None else D) - t_join) / 1e6
+        if scene_s:
+            dur = min(dur, scene_s)
         sd = seed * 1000 + i
         if form == 0:
             rate = float(min(rates[i], C0_MAX_RATE))
@@ -282,7 +288,8 @@ def mixed_serving(duration_s: float = 0.25, seed: int = 1004, counts=(16, 48, 12
             sc = checkerboard_1280x720(duration_s=dur, seed=sd, t0_us=t_join)
             sc.keep_prob = rate / CHECKER_NATURAL_RATE
         out.append(dict(form=form, W=sc.W, H=sc.H, rate=rate, t_join_us=t_join,
-                        t_leave_us=t_leave, scene=sc))
+                        t_leave_us=t_leave, t_end_us=t_leave if t_leave is not None else D,
+                        scene=sc))
     return out
 
 
@@ -294,23 +301,40 @@ def _arrivals(rng, t0_us: int, t1_us: int, mean_us: float = 1000.0) -> np.ndarra
     return np.append(arr[arr < t1_us], t1_us)
 
 
-def serving_streams(n_streams: int = 64, duration_s: float = 0.25, seed: int = 1003):
+def serving_streams(n_streams: int = 64, duration_s: float = 0.25, seed: int = 1003,
+                    scene_s: float | None = None):
     """Batched-serving workload of n_streams sinusoid form 346x260 streams:
     lognormal rates (median 1 Mev/s) clipped to [0.2, 5] Mev/s and Poisson
-    packet arrivals with a 1 ms mean gap.
+    packet arrivals with a 1 ms mean gap.  scene_s: generate at most this
+    much of each stream's scene and repeat it in time (stream_events).
 
-    Returns (rates, streams): each stream a dict with W, H, rate, scene and
-    arrivals (int64 us; the last one at the end of the stream).
+    Returns (rates, streams): each stream a dict with W, H, rate, scene,
+    t_join_us, t_end_us and arrivals (int64 us; the last one at the end).
     """
     rates = lognormal_rates(n_streams, seed)
     rng = np.random.default_rng(seed)
     D = int(round(duration_s * 1e6))
     out = []
     for i in range(n_streams):
-        sc = serving_stream(i, float(rates[i]), duration_s)
-        out.append(dict(W=sc.W, H=sc.H, rate=float(rates[i]), scene=sc,
+        sc = serving_stream(i, float(rates[i]), min(duration_s, scene_s or duration_s))
+        out.append(dict(W=sc.W, H=sc.H, rate=float(rates[i]), scene=sc, t_join_us=0, t_end_us=D,
                         arrivals=_arrivals(rng, 0, D)))
     return rates, out
+
+
+def stream_events(w: dict, t_end_us: int | None = None) -> np.ndarray:
+    """A serving stream's events: its scene generated once and repeated in
+    time (each copy shifted by the scene's length) up to its end time."""
+    ev = generate(w["scene"])
+    t0 = int(w.get("t_join_us", 0))
+    t1 = int(t_end_us if t_end_us is not None else w["t_end_us"])
+    period = int(round(w["scene"].duration_s * 1e6))
+    if period <= 0 or t0 + period >= t1:
+        return ev
+    reps = -(-(t1 - t0) // period)
+    out = np.concatenate([ev] * reps)
+    out["t"] += np.repeat(np.arange(reps, dtype=np.int64) * period, len(ev))
+    return out[out["t"] < t1]
 
 
 def mixed_arrivals(ws, duration_s: float = 0.25, seed: int = 1004):

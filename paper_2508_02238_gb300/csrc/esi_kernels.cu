@@ -285,10 +285,10 @@ size_t tile_smem_bytes_ev(int batch, int n_chunks)
 
 size_t tile_static_smem_bytes(int tile_h, int tile_w)
 {
-    // pixel state (S, F, O and a peer mask per pixel), the scan's event maps
-    // (32 per row), staged frames and the sort scratch
-    return (size_t)tile_h * tile_w * 20 + (size_t)tile_h * 32 * 16 +
-           (size_t)kStageFrames * sizeof(WinInfo) + (size_t)tile_h * tile_h * 2 + 1024;
+    // pixel state (S, F, O and a peer mask per pixel), staged frames and the
+    // sort scratch
+    return (size_t)tile_h * tile_w * 20 + (size_t)kStageFrames * sizeof(WinInfo) +
+           (size_t)tile_h * tile_h * 2 + 1024;
 }
 
 int decay_kind_of(const DecayParams &dp)

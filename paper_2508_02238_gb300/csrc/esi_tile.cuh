@@ -20,7 +20,11 @@ static __host__ __device__ inline size_t tile_layout(int batch, int n_chunks, si
                                                      size_t *off_runpre, size_t *off_runoff,
                                                      size_t *off_lpos)
 {
-    size_t o = (size_t)(batch + 2) * 8;   // batch + the next batch's first record
+    // batch + the next batch's first record; while the warps walk the
+    // sorted copy, the same bytes hold the segmented scan's 32 event maps
+    // (16 bytes each) per warp, up to 32 warps
+    size_t o = (size_t)(batch + 2) * 8;
+    if (o < (size_t)32 * 32 * 16) o = (size_t)32 * 32 * 16;
     *off_b = o;
     o += (size_t)batch * 8;
     *off_runpre = o;
@@ -281,7 +285,6 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
     __shared__ __align__(16) float sF[TH][TWP];      // (float)(T - t_base)
     __shared__ __align__(16) long long sO[TH][TWP];  // T - t_base
     __shared__ unsigned sPeer[TH][TWP];              // per-pixel lane masks of a group (kept zero)
-    __shared__ __align__(16) float4 sScan[TH][32];   // a group's event maps, pixel by pixel
 
     const int R = a.batch, n_chunks = a.n_chunks;
     size_t off_b, off_runpre, off_runoff, off_lpos;
@@ -358,8 +361,11 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
 
 
     const RowState rs{rS, rF, rO, rP};
+    // the segmented scan's 32 slots per warp live in the gathered-batch
+    // buffer A, which nothing reads while the warps walk the sorted copy B
+    float4 *sScan = reinterpret_cast<float4 *>(A) + warp * 32;
     auto apply = [&](unsigned long long r, bool valid, unsigned ev_idx) {
-        const float s_out = apply_group<TWP, RD, DK>(rs, sScan[warp], r, valid, dp, mp, a.scan_chain);
+        const float s_out = apply_group<TWP, RD, DK>(rs, sScan, r, valid, dp, mp, a.scan_chain);
         if constexpr (EV) {
             if (valid) a.ev_out[ev_idx] = s_out;
         }

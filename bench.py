@@ -81,6 +81,8 @@ def parse_args():
                     help="skip every leg but the headline measurement")
     ap.add_argument("--serving-only", action="store_true",
                     help="run only the two serving legs and print their JSON")
+    ap.add_argument("--serving-apply", type=int, choices=[0, 1, 2], default=0,
+                    help="esi_server_opts.apply_mode of the serving legs (0: default)")
     ap.add_argument("--serving-seconds", type=float, default=None,
                     help="stream time of the serving legs (default 5 s)")
     ap.add_argument("--ncu-case", action="store_true",
@@ -375,8 +377,13 @@ def bench_esi(args):
     legs = {}
 
     def leg(key, fn, *a):
+        # a leg that fails is reported in its key; the headline line still prints
         t0 = time.perf_counter()
-        line[key] = fn(*a)
+        try:
+            line[key] = fn(*a)
+        except Exception as ex:
+            line[key] = {"error": f"{type(ex).__name__}: {ex}"}
+            print(f"bench: leg {key} failed: {ex!r}", file=sys.stderr, flush=True)
         legs[key] = round(time.perf_counter() - t0, 1)
 
     if extras:
@@ -519,6 +526,7 @@ def other_workloads_leg(esi, torch, K=6):
 
 
 SERVING_SECONDS = 5.0
+SERVING_APPLY = 0   # esi_server_opts.apply_mode of the serving legs (0: the server's default)
 MIXED_SECONDS = 5.0
 SERVING_PARAMS = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1)
 
@@ -571,6 +579,12 @@ def serving_64(seconds, scene_s=None):
     return rates, streams
 
 
+def _server_run(esi, srv, pk, npk, t_end, realtime, tick_us=1000):
+    rc = esi.esi_server_run(srv, pk, npk, tick_us, t_end, realtime)
+    if rc:
+        raise RuntimeError(f"esi_server_run: {esi.esi_strerror(rc)}: {esi.esi_server_last_error(srv)}")
+
+
 def _stats(st, dt, realtime, n_ev, expected=None):
     d = {"frames": int(st.frames),
          "frame_latency_p50_ms": st.frame_latency_p50_ms,
@@ -581,6 +595,8 @@ def _stats(st, dt, realtime, n_ev, expected=None):
          "gpu_tick_p99_ms": st.gpu_tick_p99_ms,
          "host_tick_p50_ms": st.host_tick_p50_ms, "host_tick_p99_ms": st.host_tick_p99_ms,
          "kernel_launches_per_tick": int(st.kernel_launches_per_tick),
+         "host_pool_peak_mb": round(st.host_pool_peak_bytes / 2**20, 1),
+         "ring_grows": int(st.ring_grows),
          "wall_s": dt, "events_per_s": n_ev / dt if not realtime else None,
          "frames_per_s": st.frames / dt}
     if expected is not None:
@@ -601,8 +617,10 @@ def serving_leg(esi, seconds=SERVING_SECONDS):
                        f"{np.median(rates) / 1e6:.2f}), Poisson packets 1 ms, 100 frames/s, "
                        f"{seconds} s", "events": n_ev}
     expected = len(streams) * (t_end // WINDOW_US)
+    opts = esi.esi_server_opts()
+    opts.use_graph, opts.apply_mode = 1, SERVING_APPLY
     for mode in ("batched", "batched_throughput"):
-        rc, srv = esi.esi_server_create(1 << 30, None, 0)
+        rc, srv = esi.esi_server_create(1 << 30, opts, 0)
         esi.check(rc, "server")
         parts = []
         for k, s in enumerate(streams):
@@ -612,7 +630,7 @@ def serving_leg(esi, seconds=SERVING_SECONDS):
         pk, npk = _packets(esi, parts)
         realtime = 1 if mode == "batched" else 0
         t0 = time.perf_counter()
-        esi.check(esi.esi_server_run(srv, pk, npk, 1000, t_end, realtime), "run")
+        _server_run(esi, srv, pk, npk, t_end, realtime)
         dt = time.perf_counter() - t0
         rc, st = esi.esi_server_get_stats(srv)
         esi.esi_server_destroy(srv)
@@ -670,7 +688,8 @@ def mixed_serving_leg(esi, seconds=SERVING_SECONDS):
     ws, pk, npk, specs, evs, _ = mixed_workload(esi, seconds, scene_s=SCENE_SECONDS)
     budget = 768 << 20
     opts = esi.esi_server_opts()
-    opts.use_graph, opts.max_streams = 1, 256
+    opts.use_graph, opts.max_streams, opts.apply_mode = 1, 256, SERVING_APPLY
+    opts.host_pool_bytes = 1 << 30
     n_ev = int(sum(len(e) for e in evs))
     expected = sum(((w["t_leave_us"] if w["t_leave_us"] is not None else t_end) - w["t_join_us"])
                    // WINDOW_US for w in ws)
@@ -690,7 +709,7 @@ def mixed_serving_leg(esi, seconds=SERVING_SECONDS):
         esi.check(rc, "server")
         realtime = 1 if mode == "batched" else 0
         t0 = time.perf_counter()
-        esi.check(esi.esi_server_run(srv, pk, npk, 1000, t_end, realtime), "run")
+        _server_run(esi, srv, pk, npk, t_end, realtime)
         dt = time.perf_counter() - t0
         rc, st = esi.esi_server_get_stats(srv)
         esi.esi_server_destroy(srv)
@@ -922,7 +941,7 @@ def _parity_serving_64(esi, oracle, seconds=0.25):
         ids.append(sid)
         parts.append(_event_part(esi, sid, s["events"], s["arrivals"]))
     pk, npk = _packets(esi, parts)
-    esi.check(esi.esi_server_run(srv, pk, npk, 1000, t_end, 0), "run")
+    _server_run(esi, srv, pk, npk, t_end, 0)
     acc = ParityAcc()
     for s, sid, (buf, tfs) in zip(streams, ids, sinks):
         S = np.empty(s["W"] * s["H"], dtype=np.float32)
@@ -948,9 +967,10 @@ def _parity_mixed(esi, oracle, seconds=0.25):
     ws, pk, npk, specs, evs, sinks = mixed_workload(esi, seconds, sinks=True)
     opts = esi.esi_server_opts()
     opts.use_graph, opts.max_streams = 1, 256
+    opts.host_pool_bytes = 1 << 30
     rc, srv = esi.esi_server_create(768 << 20, opts, 0)
     esi.check(rc, "server")
-    esi.check(esi.esi_server_run(srv, pk, npk, 1000, t_end, 0), "run")
+    _server_run(esi, srv, pk, npk, t_end, 0)
     acc = ParityAcc()
     for w, sp, ev, (buf, tfs, nf) in zip(ws, specs, evs, sinks):
         t0 = w["t_join_us"]
@@ -984,8 +1004,11 @@ def summary(line):
     s = {"Gev_s": {HEADLINE: g(line["value"])},
          "tile_frac": {HEADLINE: round(line["roofline"]["frac"], 4) if line.get("roofline") else None},
          "step_frac": {HEADLINE: round(line["step_roofline"]["frac"], 4)},
-         "e2e_Gev_s": g(line["e2e"]["value"]) if line.get("e2e") else None}
-    for name, r in (line.get("other_workloads") or {}).items():
+         "e2e_Gev_s": g(line["e2e"]["value"]) if (line.get("e2e") or {}).get("value") else None}
+
+    def ok(d):
+        return isinstance(d, dict) and "error" not in d
+    for name, r in (line.get("other_workloads") if ok(line.get("other_workloads")) else {}).items():
         s["Gev_s"][name] = g(r["default"]["events_per_s"])
         s["step_frac"][name] = round(r["default"]["step_hbm_frac"], 4)
         if r["default"].get("dominant"):
@@ -995,6 +1018,9 @@ def summary(line):
         d = line.get(key)
         if not d:
             continue
+        if not ok(d):
+            sv[tag] = d
+            continue
         e = {"lat_ms(f50,f99,p50,p99)": {m: lat(d[m]) for m in ("batched", "plain") if m in d},
              "frames": f"{d['batched']['frames']}/{d['batched'].get('expected_frames')}",
              "max_Gev_s": g(d["batched_throughput"]["events_per_s"])}
@@ -1003,7 +1029,7 @@ def summary(line):
     s["parity(err,err1e-3C,lsb,off,frames)"] = {
         k: [float(f"{v['state_err']:.2e}"), float(f"{v['state_err_floor_1e-3C']:.2e}"),
             v["frame_max_lsb"], v["frame_off_by_one"], v["frames"]]
-        for k, v in (line.get("parity") or {}).items()}
+        for k, v in (line.get("parity") if ok(line.get("parity")) else {}).items()}
     return s
 
 
@@ -1032,7 +1058,9 @@ def ncu_case():
 
 
 def main():
+    global SERVING_APPLY
     args = parse_args()
+    SERVING_APPLY = args.serving_apply
     if args.ncu_case:
         ncu_case()
         return
@@ -1045,8 +1073,15 @@ def main():
             print(json.dumps({"diagnostics": diagnostics_leg(esi, torch)}), flush=True)
         elif args.serving_only:
             sec = args.serving_seconds or SERVING_SECONDS
-            print(json.dumps({"serving": serving_leg(esi, sec),
-                              "serving_mixed": mixed_serving_leg(esi, sec)}), flush=True)
+            out = {}
+            for key, fn in (("serving", serving_leg), ("serving_mixed", mixed_serving_leg)):
+                try:
+                    out[key] = fn(esi, sec)
+                except Exception as ex:
+                    out[key] = {"error": f"{type(ex).__name__}: {ex}"}
+            print(json.dumps(out), flush=True)
+            if any("error" in v for v in out.values()):
+                sys.exit(1)
         else:
             print(json.dumps({"parity": parity_leg(esi, torch)}), flush=True)
         return

@@ -335,8 +335,9 @@ const char *esi_strerror(int code);
  * Time: streams share the caller's clock now_us (int64 us).  Stream frames
  * fall at t_origin + k * frame_period_us, k >= 1.  The caller pushes each
  * stream's events as its packets arrive; esi_server_tick(now_us) promises
- * that every event with t <= now_us has been pushed.  The tick applies each
- * stream's pushed events with t <= now_us, renders every frame with
+ * that every event with t <= now_us has been pushed.  The tick applies
+ * pushed events with t <= now_us (every stream's, or only those of streams
+ * with a frame due: esi_server_opts.apply_mode), renders every frame with
  * t_frame <= now_us (at most frame_slots - 1 per stream per tick; the rest
  * follow in the next ticks) and returns once the work is queued.  Frames land
  * in host memory the GPU writes directly; esi_stream_frame returns the newest
@@ -357,8 +358,27 @@ typedef struct {
     int32_t tile_h;               /* rows per 128-pixel tile of new streams: 0 = 8, or 4, 16 */
     int32_t max_stream_pixels;    /* largest W * H accepted; default 1280*720 */
     int32_t scan_chain;           /* as esi_tuning.scan_chain; 0 = default (8) */
-    int32_t _reserved[2];
+    int32_t apply_mode;           /* when a stream's events are applied: 0 = default
+                                   * (ESI_APPLY_EVERY_TICK), ESI_APPLY_EVERY_TICK or
+                                   * ESI_APPLY_AT_FRAMES */
+    int32_t copy_threads;         /* host threads that copy a large push into its
+                                   * ring, the caller's included: 0 = default (4),
+                                   * 1 .. 16                                   */
+    int64_t host_pool_bytes;      /* pinned host memory holding the streams'
+                                   * pending events (a ring per stream, grown on
+                                   * demand); 0 = default (256 MB)             */
 } esi_server_opts;
+
+/* esi_server_opts.apply_mode.  EVERY_TICK: each tick applies every stream's
+ * pushed events up to the tick's time, so a frame's tick has only the newest
+ * events left; each tick then reads and writes the state of every tile that
+ * received an event.  AT_FRAMES: a stream's events wait on the host until the
+ * tick that renders its next frame (or until 65536 events are pending), so
+ * each tile's state is read and written about once per frame.  Both give the
+ * same results; EVERY_TICK keeps frame ticks short (lower p99 latency),
+ * AT_FRAMES does less device work per event. */
+#define ESI_APPLY_EVERY_TICK 1
+#define ESI_APPLY_AT_FRAMES 2
 
 /* Latencies in milliseconds over the frames finished since the last reset:
  * frame latency = frame ready - the tick call that rendered it;
@@ -384,6 +404,10 @@ typedef struct {
     double host_tick_p50_ms;      /* host time of a tick call with work: packing */
     double host_tick_p99_ms;      /*   the events and tables, queueing the work  */
     double gpu_tick_p99_ms;       /* device time of a tick's kernels, 99th pct  */
+    uint64_t host_pool_bytes;     /* pinned host pool of the event rings        */
+    uint64_t host_pool_used_bytes;  /* held by rings now (retired ones included) */
+    uint64_t host_pool_peak_bytes;  /* the most held since the last reset        */
+    uint64_t ring_grows;          /* rings moved into larger ones              */
 } esi_server_stats;
 
 typedef struct esi_server esi_server;
@@ -449,7 +473,9 @@ int esi_stream_set_tile_h(esi_server *srv, int stream_id, int tile_h);
 int esi_stream_autotune(esi_server *srv, int stream_id, const esi_event *sample, size_t n,
                         int flags, int *tile_h);
 
-/* Copy a stream's state (as esi_get_state with host buffers); waits. */
+/* Copy a stream's state (as esi_get_state with host buffers) after every
+ * pushed event with t <= the latest tick's time has been applied (events the
+ * apply mode held back are applied first); waits. */
 int esi_stream_state(esi_server *srv, int stream_id, float *S, int64_t *T);
 
 /* Close a stream: waits for its work, returns its state memory. */
@@ -459,6 +485,36 @@ int esi_stream_close(esi_server *srv, int stream_id);
 int esi_server_sync(esi_server *srv);
 
 int esi_server_get_stats(esi_server *srv, esi_server_stats *out);
+
+/* What the server's last failed call ran into (a CUDA error, the host pool
+ * being full, the executor's packet), or "" when no call has failed.  The
+ * string stays valid until the next call on the server. */
+const char *esi_server_last_error(esi_server *srv);
+
+/* One finished tick that had work, as the server saw it.  Host times are in
+ * nanoseconds since the server's creation (steady clock); device times come
+ * from CUDA events on the server's stream. */
+typedef struct {
+    int64_t call_ns;      /* esi_server_tick called                               */
+    int64_t issued_ns;    /* its copies and kernels queued (the call returns)     */
+    int64_t ready_ns;     /* its completion stamp: its frames readable (may come
+                           * before issued_ns: a small tick can finish on the
+                           * device before its call returns)                    */
+    float copy_ms;        /* device: the tick's table copy                         */
+    float kernels_ms;     /* device: the tick's kernels and completion stamp       */
+    float gap_ms;         /* device: from the previous traced tick's end to this
+                           * tick's start; near 0 when it queued behind it; -1 for
+                           * the first                                              */
+    int32_t frames;       /* frames it rendered                                    */
+    int64_t events;       /* events it applied                                     */
+    int32_t streams;      /* streams with work                                     */
+    int32_t items;        /* (stream, tile) work items                             */
+} esi_tick_trace;
+
+/* Copy the trace of the last finished ticks (at most 65536 are kept, since
+ * the last esi_server_reset_stats), oldest first: up to cap records into out,
+ * the number copied into *n.  out may be NULL with cap 0 to ask for *n. */
+int esi_server_trace(esi_server *srv, esi_tick_trace *out, size_t cap, size_t *n);
 int esi_server_reset_stats(esi_server *srv);
 void esi_server_destroy(esi_server *srv);
 

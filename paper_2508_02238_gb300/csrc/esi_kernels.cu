@@ -69,8 +69,10 @@ bool bin_mask_fits(int chunk, int n_tiles)
 // One chunk of events: block-level body shared by the single-sensor and the
 // batched binning kernels.  cidx is the chunk's index within a.n's events.
 // EV: also write each record's event index (a.rec_idx) and NaN for events
-// outside the sensor (a.ev_out), for esi_event_states.
-template <bool EV = false>
+// outside the sensor (a.ev_out), for esi_event_states.  PLAIN: the block
+// reads the chunk with 16-byte loads instead of a bulk copy (the serving
+// tick's events stay in mapped host memory).
+template <bool EV = false, bool PLAIN = false>
 __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
 {
     constexpr int NT = kBinThreads, NW = NT / 32;
@@ -98,11 +100,17 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
     const int nc = (int)min((long long)chunk, (long long)a.n - c0);
 
     if (tid == 0) {
-        mbar_init(&bar, 1);
+        if (!PLAIN) mbar_init(&bar, 1);
         s_drop = 0;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (PLAIN) {
+        const int4 *src = reinterpret_cast<const int4 *>(a.ring);
+        const unsigned long long f0 = a.first + (unsigned long long)c0;
+#pragma unroll 4
+        for (int i = tid; i < nc; i += NT) sev[i] = src[(f0 + (unsigned long long)i) & a.ring_mask];
+    }
+    if (!PLAIN && tid == 0) {
         // the chunk's ring range may wrap around the end of the ring
         const unsigned long long cap = a.ring_mask + 1ull;
         const unsigned long long r0 = (a.first + (unsigned long long)c0) & a.ring_mask;
@@ -118,7 +126,8 @@ __device__ __forceinline__ void bin_chunk(const BinArgs &a, int cidx)
     if (use_mask)
         for (int i = tid; i < NW * kBinMaskSlots / 4; i += NT)
             reinterpret_cast<uint4 *>(tmask)[i] = make_uint4(0u, 0u, 0u, 0u);
-    if (tid == 0) {
+    if (PLAIN && tid == 0) s_copy_ok = 1;
+    if (!PLAIN && tid == 0) {
         // one thread waits for the copy; the others sleep at the barrier
         int ok = mbar_wait_bounded(&bar, 0, kWaitLimitNs) ? 1 : 0;
         if (!ok) {
@@ -253,7 +262,7 @@ __global__ void __launch_bounds__(kBinThreads) esi_bin_tab_kernel(const unsigned
     const int *cj = reinterpret_cast<const int *>(tab + d->off_chunkjob);
     for (int c = blockIdx.x; c < n; c += gridDim.x) {
         const BinJob &j = jobs[cj[c]];
-        bin_chunk(j.args, c - j.first_chunk);
+        bin_chunk<false, true>(j.args, c - j.first_chunk);
         __syncthreads();  // shared memory (and the copy barrier) serve the next chunk
     }
 }

@@ -1,10 +1,13 @@
 // Batched serving of many sensors (esi_server_* in esi.h).
 //
-// A tick gathers, for every stream with a frame due, its pushed events up to
-// the tick's time and its due frame times, packs them with per-stream
-// descriptors into one pinned staging buffer, copies that to a fixed device
-// table, and runs one batched binning launch plus one batched tile launch per
-// parameter variant (render mode x decay kind x row alignment).  The kernels
+// Each stream's pushed events wait in a ring in pinned, mapped host memory
+// (one copy, split over worker threads when large).  A tick takes, for every
+// stream with work, its pending events up to the tick's time and its due
+// frame times, writes per-stream descriptors (ring position, sizes, frames)
+// into one pinned staging table, copies that table to the device, and runs
+// one batched binning launch (which reads the events from the rings) and,
+// after it, one batched tile launch per parameter variant (tile height x
+// render mode x decay kind x row alignment) as parallel graph branches.  The kernels
 // read their sizes and per-stream descriptors from the device table, so one
 // captured CUDA graph serves every tick; frames are written straight into
 // mapped host memory.  A host-function node stamps each tick's completion.
@@ -16,8 +19,13 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <condition_variable>
+#include <cstdio>
 #include <map>
+#include <mutex>
 #include <new>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "esi_api_impl.h"
@@ -48,9 +56,11 @@ class Arena {
     void init(size_t size)
     {
         size_ = size;
+        used_ = 0;
         free_.clear();
         if (size) free_[0] = size;
     }
+    size_t used() const { return used_; }
     // offset of a block of n bytes, or SIZE_MAX when nothing fits
     size_t alloc(size_t n)
     {
@@ -60,6 +70,7 @@ class Arena {
             const size_t off = it->first, len = it->second;
             free_.erase(it);
             if (len > n) free_[off + n] = len - n;
+            used_ += n;
             return off;
         }
         return SIZE_MAX;
@@ -67,6 +78,7 @@ class Arena {
     void release(size_t off, size_t n)
     {
         n = align_up(n, 256);
+        used_ -= n;
         auto it = free_.emplace(off, n).first;
         auto nx = std::next(it);
         if (nx != free_.end() && it->first + it->second == nx->first) {
@@ -83,14 +95,102 @@ class Arena {
     }
 
   private:
-    size_t size_ = 0;
+    size_t size_ = 0, used_ = 0;
     std::map<size_t, size_t> free_;
 };
+
+// Worker threads that split a large copy with the calling thread.
+class CopyPool {
+  public:
+    ~CopyPool() { stop(); }
+    bool start(int workers)
+    {
+        try {
+            for (int k = 0; k < workers; ++k) th_.emplace_back([this, k] { run(k); });
+        } catch (...) {
+            stop();
+            return false;
+        }
+        return true;
+    }
+    void stop()
+    {
+        {
+            std::lock_guard<std::mutex> g(m_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (std::thread &t : th_) t.join();
+        th_.clear();
+    }
+    // bytes split into workers + 1 parts; the caller copies the last one
+    void copy(void *dst, const void *src, size_t bytes)
+    {
+        const int parts = (int)th_.size() + 1;
+        const size_t part = (bytes / (size_t)parts + 63) & ~(size_t)63;  // 64-byte multiples
+        {
+            std::lock_guard<std::mutex> g(m_);
+            dst_ = static_cast<unsigned char *>(dst);
+            src_ = static_cast<const unsigned char *>(src);
+            bytes_ = bytes;
+            part_ = part;
+            pending_ = (int)th_.size();
+            gen_ += 1;
+        }
+        cv_.notify_all();
+        const size_t a = std::min(bytes, part * (size_t)(parts - 1));
+        std::memcpy(static_cast<unsigned char *>(dst) + a, static_cast<const unsigned char *>(src) + a,
+                    bytes - a);
+        std::unique_lock<std::mutex> l(m_);
+        done_cv_.wait(l, [this] { return pending_ == 0; });
+    }
+    int workers() const { return (int)th_.size(); }
+
+  private:
+    void run(int k)
+    {
+        unsigned long long seen = 0;
+        for (;;) {
+            unsigned char *d;
+            const unsigned char *s;
+            size_t a, b;
+            {
+                std::unique_lock<std::mutex> l(m_);
+                cv_.wait(l, [&] { return stop_ || gen_ != seen; });
+                if (stop_) return;
+                seen = gen_;
+                d = dst_;
+                s = src_;
+                a = std::min(bytes_, part_ * (size_t)k);
+                b = std::min(bytes_, part_ * (size_t)(k + 1));
+            }
+            if (b > a) std::memcpy(d + a, s + a, b - a);
+            {
+                std::lock_guard<std::mutex> g(m_);
+                pending_ -= 1;
+            }
+            done_cv_.notify_one();
+        }
+    }
+    std::vector<std::thread> th_;
+    std::mutex m_;
+    std::condition_variable cv_, done_cv_;
+    unsigned long long gen_ = 0;
+    int pending_ = 0;
+    bool stop_ = false;
+    unsigned char *dst_ = nullptr;
+    const unsigned char *src_ = nullptr;
+    size_t bytes_ = 0, part_ = 0;
+};
+
+constexpr size_t kParallelCopyBytes = 1 << 20;  // smaller pushes copy on the caller's thread
 
 constexpr int kGroups = kTickGroups;
 constexpr int kChunk = 2048;
 constexpr int kBatch = 2048;
 constexpr int kMaxChunksPerStream = 64;
+constexpr long long kDeferCap = 65536;  // AT_FRAMES: pending events applied without a frame
+constexpr unsigned long long kRingInit = 16384;  // events of a new stream's ring
 constexpr int kTickSlots = 64;  // completion stamps kept for ticks in flight
 constexpr int kMaxSlots = 1 << 20;  // caller stream slots of one esi_server_run
 
@@ -107,8 +207,14 @@ struct Stream {
     size_t arena_off = 0, arena_bytes = 0;
     float *S = nullptr;
     long long *T = nullptr;
-    std::vector<esi_event> pend;
-    size_t pend_head = 0;
+    // pending events: a ring in the pinned host pool, read by the device
+    // through its mapped address; absolute indices done <= head <= tail:
+    // [head, tail) pending, [done, head) read by ticks still in flight
+    esi_event *ring_h = nullptr;
+    const esi_event *ring_d = nullptr;
+    size_t ring_off = 0, ring_bytes = 0;
+    unsigned long long ring_cap = 0;  // events, a power of two
+    unsigned long long head = 0, tail = 0, done = 0;
     long long last_event_t = 0;
     long long push_floor = 0;
     long long next_frame_t = 0;
@@ -135,11 +241,36 @@ struct TickFrame {
 
 struct TickRec {
     unsigned long long id = 0;
-    long long call_ns = 0;
+    std::vector<std::pair<int, unsigned long long>> used;  // (stream, ring index it read up to)
+    long long call_ns = 0, issued_ns = 0;
     std::vector<TickFrame> frames;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t evc = nullptr;             // before the copies
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the kernels
+    long long n_events = 0;
+    int n_streams = 0, n_items = 0;
     int stage = 0;
 };
+
+constexpr size_t kTraceCap = 65536;  // tick trace records kept
+
+// The pending event at absolute ring index i.
+inline const esi_event &ring_at(const Stream &st, unsigned long long i)
+{
+    return st.ring_h[i & (st.ring_cap - 1)];
+}
+
+// How many of the n pending events from the ring's head have t <= t_lim
+// (times are non-decreasing).
+size_t ring_count_upto(const Stream &st, size_t n, long long t_lim)
+{
+    size_t lo = 0, hi = n;
+    while (lo < hi) {
+        const size_t mid = lo + (hi - lo) / 2;
+        if (ring_at(st, st.head + mid).t_us <= t_lim) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
 
 // Completion stamps written by the host-function node of each tick.
 struct Completion {
@@ -186,7 +317,7 @@ struct esi_server {
     bool bin_mask = false;  // binning finds same-tile lanes by mask words
     long long cap_events = 0;
     size_t off_binjob = 0, off_chunkjob = 0, off_tilejob = 0, off_items = 0, off_win = 0,
-           off_fout = 0, off_events = 0, tab_bytes = 0;
+           off_fout = 0, tab_bytes = 0;
     unsigned char *stage[2] = {nullptr, nullptr};  // pinned
     cudaEvent_t stage_ev[2] = {nullptr, nullptr};
     bool stage_busy[2] = {false, false};
@@ -206,6 +337,26 @@ struct esi_server {
 
     // statistics since the last reset
     std::vector<double> frame_lat, pkt_lat, host_tick, gpu_tick;
+    long long last_now = LLONG_MIN;  // the latest tick time
+    long long t0_ns = 0;             // creation (trace times are relative to it)
+    std::vector<esi_tick_trace> trace;  // ring of kTraceCap records
+    size_t trace_n = 0;                  // records written since the reset
+    cudaEvent_t prev_end = nullptr;      // the last traced tick's end
+    std::string err;  // the last failure, for esi_server_last_error
+    // pinned host pool of the streams' event rings, and rings replaced by
+    // larger ones that ticks in flight may still read: freed once the tick
+    // count reaches the tag
+    unsigned char *hpool = nullptr;
+    unsigned char *hpool_d = nullptr;
+    Arena harena;
+    struct Retired {
+        unsigned long long tag;
+        size_t off, bytes;
+    };
+    std::vector<Retired> retired;
+    size_t hpool_peak = 0;
+    unsigned long long ring_grows = 0;
+    CopyPool copiers;
     unsigned long long n_ticks = 0, n_frames = 0, n_events = 0, n_packets = 0;
     unsigned long long n_admitted = 0, n_refused = 0, n_events_refused = 0;
     double gpu_ms = 0.0;
@@ -214,6 +365,13 @@ struct esi_server {
 };
 
 namespace {
+
+// rc_of, keeping what failed for esi_server_last_error
+int cuda_note(esi_server *s, const char *where, cudaError_t e)
+{
+    if (e != cudaSuccess) s->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return rc_of(e);
+}
 
 cudaEvent_t take_event(esi_server *s)
 {
@@ -242,9 +400,33 @@ void poll(esi_server *s)
             s->gpu_ms += ms;
             s->gpu_n += 1;
             s->gpu_tick.push_back(ms);
+        } else {
+            ms = -1.0f;
         }
+        esi_tick_trace tr{};
+        tr.call_ns = t->call_ns - s->t0_ns;
+        tr.issued_ns = t->issued_ns - s->t0_ns;
+        tr.ready_ns = ready - s->t0_ns;
+        tr.kernels_ms = ms;
+        if (cudaEventElapsedTime(&tr.copy_ms, t->evc, t->ev0) != cudaSuccess) tr.copy_ms = -1.0f;
+        tr.gap_ms = -1.0f;
+        if (s->prev_end && cudaEventElapsedTime(&tr.gap_ms, s->prev_end, t->evc) != cudaSuccess)
+            tr.gap_ms = -1.0f;
+        tr.frames = (int)t->frames.size();
+        tr.events = t->n_events;
+        tr.streams = t->n_streams;
+        tr.items = t->n_items;
+        if (s->trace.size() < kTraceCap) s->trace.push_back(tr);
+        else s->trace[s->trace_n % kTraceCap] = tr;
+        s->trace_n += 1;
+        if (s->prev_end) s->ev_pool.push_back(s->prev_end);
+        s->prev_end = t->ev1;
+        s->ev_pool.push_back(t->evc);
         s->ev_pool.push_back(t->ev0);
-        s->ev_pool.push_back(t->ev1);
+        for (const auto &u : t->used) {
+            Stream &st = s->streams[u.first];
+            if (st.open) st.done = std::max(st.done, u.second);
+        }
         for (const TickFrame &f : t->frames) {
             Stream &st = s->streams[f.stream];
             const double lat = (double)(ready - t->call_ns) * 1e-6;
@@ -265,16 +447,91 @@ void poll(esi_server *s)
         delete t;
     }
     s->inflight.erase(s->inflight.begin(), s->inflight.begin() + k);
+    // rings replaced while ticks that read them were in flight
+    const unsigned long long finished = s->comp->done.load(std::memory_order_acquire);
+    size_t w = 0;
+    for (size_t i = 0; i < s->retired.size(); ++i) {
+        if (s->retired[i].tag <= finished) s->harena.release(s->retired[i].off, s->retired[i].bytes);
+        else s->retired[w++] = s->retired[i];
+    }
+    s->retired.resize(w);
+}
+
+// Room for n more events in stream id's ring: frees the slots of finished
+// ticks, waits for ticks in flight that still read slots it needs, or moves
+// the pending events into a larger ring (the old one is freed once the ticks
+// in flight are done).  ESI_ENOMEM when the host pool is full.
+int ring_reserve(esi_server *s, int id, size_t n)
+{
+    Stream &st = s->streams[id];
+    auto fits = [&] { return st.tail - st.done + n <= st.ring_cap; };
+    if (fits()) return ESI_OK;
+    poll(s);
+    if (fits()) return ESI_OK;
+    if (st.tail - st.head + n <= st.ring_cap) {
+        // the pending events fit: wait for the ticks reading older slots
+        while (!fits() && !s->inflight.empty()) {
+            cudaError_t e = cudaEventSynchronize(s->inflight.front()->ev1);
+            if (e != cudaSuccess) return cuda_note(s, "waiting for a tick", e);
+            const unsigned long long before = s->inflight.front()->id;
+            poll(s);
+            if (!s->inflight.empty() && s->inflight.front()->id == before) {
+                // its completion stamp is still being written (bounded)
+                const long long t_give_up = wall_ns() + 2000000000ll;
+                while (s->comp->done.load(std::memory_order_acquire) <= before) {
+                    if (wall_ns() > t_give_up) return ESI_ETIMEOUT;
+                }
+                poll(s);
+            }
+        }
+        if (!fits()) st.done = st.head;  // no tick in flight reads this ring any more
+        return ESI_OK;
+    }
+    unsigned long long cap = st.ring_cap;
+    while (cap < 2 * (st.tail - st.head + n)) cap *= 2;
+    const size_t bytes = (size_t)cap * sizeof(esi_event);
+    const size_t off = s->harena.alloc(bytes);
+    if (off == SIZE_MAX) {
+        char m[200];
+        std::snprintf(m, sizeof(m),
+                      "host pool full: stream %d needs a ring of %llu events (%zu MB); %zu of %zu MB held",
+                      id, cap, bytes >> 20, s->harena.used() >> 20, (size_t)s->opts.host_pool_bytes >> 20);
+        s->err = m;
+        return ESI_ENOMEM;
+    }
+    s->hpool_peak = std::max(s->hpool_peak, s->harena.used());
+    s->ring_grows += 1;
+    esi_event *nh = reinterpret_cast<esi_event *>(s->hpool + off);
+    for (unsigned long long i = st.head; i < st.tail; ++i) nh[i & (cap - 1)] = ring_at(st, i);
+    if (s->inflight.empty()) s->harena.release(st.ring_off, st.ring_bytes);
+    else s->retired.push_back({s->ticks_issued, st.ring_off, st.ring_bytes});
+    st.ring_h = nh;
+    st.ring_d = reinterpret_cast<const esi_event *>(s->hpool_d + off);
+    st.ring_off = off;
+    st.ring_bytes = bytes;
+    st.ring_cap = cap;
+    st.done = st.head;
+    return ESI_OK;
+}
+
+// Copy n events into a ring: large copies are split over the copy threads.
+void copy_events(esi_server *s, esi_event *dst, const esi_event *src, size_t n)
+{
+    const size_t bytes = n * sizeof(esi_event);
+    if (bytes >= kParallelCopyBytes && s->copiers.workers() > 0) s->copiers.copy(dst, src, bytes);
+    else std::memcpy(dst, src, bytes);
 }
 
 int wait_all(esi_server *s)
 {
     cudaError_t e = cudaStreamSynchronize(s->stream);
-    // the host-function node may still be finishing its store
+    // the host-function node may still be finishing its store (bounded: 2 s)
+    const long long t_give_up = wall_ns() + 2000000000ll;
     while (e == cudaSuccess && s->comp->done.load(std::memory_order_acquire) < s->ticks_issued) {
+        if (wall_ns() > t_give_up) return ESI_ETIMEOUT;
     }
     poll(s);
-    return rc_of(e);
+    return cuda_note(s, "waiting for ticks", e);
 }
 
 // Variant group g: tile height index g / 12 (4, 8, 16 rows), then render
@@ -290,31 +547,55 @@ cudaError_t launch_group(esi_server *s, int g, cudaStream_t cs)
                                  group_dk(g), group_vec(g), kBatch, kMaxChunksPerStream, cs);
 }
 
-// Capture the per-tick graph for the variant groups in `groups`.
+// Capture the per-tick graph for the variant groups in `groups`: binning,
+// then the groups' tile launches as parallel branches (they touch disjoint
+// streams), joined before the completion stamp.
 int build_graph(esi_server *s, unsigned long long groups)
 {
     if (s->gexec) {
         cudaGraphExecDestroy(s->gexec);
         s->gexec = nullptr;
     }
-    cudaStream_t cs = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return rc_of(e);
+    std::vector<int> gl;
+    for (int gi = 0; gi < kGroups; ++gi)
+        if (groups & (1ull << gi)) gl.push_back(gi);
+    std::vector<cudaStream_t> br(std::max<size_t>(gl.size(), 1), nullptr);
+    std::vector<cudaEvent_t> ev(gl.size() + 1, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < br.size() && e == cudaSuccess; ++i)
+        e = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
+    for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    cudaStream_t cs = br[0];
     cudaGraph_t g = nullptr;
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    bool capturing = false;
+    if (e == cudaSuccess) {
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        capturing = e == cudaSuccess;
+    }
     if (e == cudaSuccess)
         e = launch_bin_batch_tab(s->dtab, s->bin_grid, kChunk, s->max_tiles, s->bin_mask, cs);
-    for (int gi = 0; gi < kGroups && e == cudaSuccess; ++gi)
-        if (groups & (1ull << gi)) e = launch_group(s, gi, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], cs);  // fork after binning
+    for (size_t i = 1; i < gl.size() && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(br[i], ev[0], 0);
+    for (size_t i = 0; i < gl.size() && e == cudaSuccess; ++i) e = launch_group(s, gl[i], br[i]);
+    for (size_t i = 1; i < gl.size() && e == cudaSuccess; ++i) {  // join
+        e = cudaEventRecord(ev[i], br[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[i], 0);
+    }
     if (e == cudaSuccess) e = cudaLaunchHostFunc(cs, on_tick_done, s->comp);
-    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
-    if (e == cudaSuccess) e = e2;
+    if (capturing) {
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e2;
+    }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&s->gexec, g, 0);
     if (g) cudaGraphDestroy(g);
-    cudaStreamDestroy(cs);
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    for (cudaStream_t x : br)
+        if (x) cudaStreamDestroy(x);
     if (e != cudaSuccess) {
         s->gexec = nullptr;
-        return rc_of(e);
+        return cuda_note(s, "tick graph", e);
     }
     s->graph_groups = groups;
     return ESI_OK;
@@ -359,16 +640,23 @@ int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts, vo
     if (!o.tile_h) o.tile_h = 8;
     if (!o.max_stream_pixels) o.max_stream_pixels = 1280 * 720;
     if (!o.scan_chain) o.scan_chain = kScanChainDefault;
+    if (!o.apply_mode) o.apply_mode = ESI_APPLY_EVERY_TICK;
+    if (!o.host_pool_bytes) o.host_pool_bytes = 256ll << 20;
+    if (!o.copy_threads) o.copy_threads = 4;
     if (!opts) o.use_graph = 1;
     if (o.frame_period_us < 1 || o.max_events_per_tick < kChunk || o.max_streams < 1 ||
         o.max_streams > 4096 || o.frame_slots < 2 || o.frame_slots > 64 ||
         (o.tile_h != 4 && o.tile_h != 8 && o.tile_h != 16) ||
         o.max_stream_pixels < 1 || o.scan_chain < 1 || o.scan_chain > kScanNever ||
+        (o.apply_mode != ESI_APPLY_EVERY_TICK && o.apply_mode != ESI_APPLY_AT_FRAMES) ||
+        o.copy_threads < 1 || o.copy_threads > 16 ||
+        o.host_pool_bytes < (long long)(kRingInit * sizeof(esi_event)) ||
         state_budget_bytes == 0)
         return ESI_EINVAL;
     esi_server *s = new (std::nothrow) esi_server();
     if (!s) return ESI_ENOMEM;
     s->opts = o;
+    s->t0_ns = wall_ns();
     s->budget = state_budget_bytes;
     s->tile_h = o.tile_h;
     s->streams.resize((size_t)o.max_streams);
@@ -408,8 +696,6 @@ int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts, vo
     off = align_up(off + sizeof(void *) * (size_t)s->cap_frames, 256);
     s->off_items = off;
     off = align_up(off + sizeof(int2) * (size_t)s->cap_items, 256);
-    s->off_events = off;
-    off = align_up(off + sizeof(esi_event) * (size_t)s->cap_events, 256);
     s->tab_bytes = off;
     s->hrow_cap = (size_t)s->cap_chunks * (size_t)s->max_tiles;
     s->bin_mask = bin_mask_fits(kChunk, s->max_tiles);
@@ -436,6 +722,8 @@ int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts, vo
     if (e == cudaSuccess) e = cudaMalloc((void **)&s->rec, (size_t)s->cap_chunks * kChunk * 8);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s->hrow, s->hrow_cap * 4);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s->dstatus, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->hpool, (size_t)o.host_pool_bytes, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&s->hpool_d, s->hpool, 0);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->dstatus, 0, sizeof(DevStatus), s->stream);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
         e = cudaMallocHost((void **)&s->stage[b], s->tab_bytes);
@@ -452,6 +740,11 @@ int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts, vo
         return rc;
     }
     s->arena.init(state_budget_bytes);
+    s->harena.init((size_t)o.host_pool_bytes);
+    if (o.copy_threads > 1 && !s->copiers.start(o.copy_threads - 1)) {
+        esi_server_destroy(s);
+        return ESI_ENOMEM;
+    }
     *out = s;
     return ESI_OK;
 }
@@ -459,16 +752,23 @@ int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts, vo
 void esi_server_destroy(esi_server *s)
 {
     if (!s) return;
-    if (s->stream) cudaStreamSynchronize(s->stream);
+    cudaError_t e = cudaSuccess;
+    if (s->stream) e = cudaStreamSynchronize(s->stream);
+    bool comp_idle = true;
     if (s->comp) {
-        while (s->comp->done.load(std::memory_order_acquire) < s->ticks_issued) {
+        const long long t_give_up = wall_ns() + 2000000000ll;
+        while (e == cudaSuccess && s->comp->done.load(std::memory_order_acquire) < s->ticks_issued &&
+               wall_ns() < t_give_up) {
         }
+        comp_idle = e == cudaSuccess && s->comp->done.load(std::memory_order_acquire) >= s->ticks_issued;
     }
     for (TickRec *t : s->inflight) {
+        cudaEventDestroy(t->evc);
         cudaEventDestroy(t->ev0);
         cudaEventDestroy(t->ev1);
         delete t;
     }
+    if (s->prev_end) cudaEventDestroy(s->prev_end);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     for (Stream &st : s->streams)
         if (st.slots_host) cudaFreeHost(st.slots_host);
@@ -477,12 +777,14 @@ void esi_server_destroy(esi_server *s)
         if (s->stage[b]) cudaFreeHost(s->stage[b]);
         if (s->stage_ev[b]) cudaEventDestroy(s->stage_ev[b]);
     }
+    if (s->hpool) cudaFreeHost(s->hpool);
     cudaFree(s->arena_base);
     cudaFree(s->dtab);
     cudaFree(s->rec);
     cudaFree(s->hrow);
     cudaFree(s->dstatus);
-    delete s->comp;
+    // a completion stamp that may still run keeps its target (leaked)
+    if (comp_idle) delete s->comp;
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -531,6 +833,20 @@ int esi_stream_open(esi_server *s, int width, int height, const esi_params *para
     st.next_frame_t = params->t_origin_us + s->opts.frame_period_us;
     st.slot_t.assign((size_t)s->opts.frame_slots, 0);
     st.slot_lat.assign((size_t)s->opts.frame_slots, 0.0);
+    const size_t rbytes = kRingInit * sizeof(esi_event);
+    const size_t roff = s->harena.alloc(rbytes);
+    if (roff == SIZE_MAX) {  // no room for its events: refused like a full budget
+        s->arena.release(off, sbytes);
+        st = Stream();
+        s->n_refused += 1;
+        return ESI_EBUSY;
+    }
+    s->hpool_peak = std::max(s->hpool_peak, s->harena.used());
+    st.ring_off = roff;
+    st.ring_bytes = rbytes;
+    st.ring_cap = kRingInit;
+    st.ring_h = reinterpret_cast<esi_event *>(s->hpool + roff);
+    st.ring_d = reinterpret_cast<const esi_event *>(s->hpool_d + roff);
     cudaError_t e = cudaHostAlloc((void **)&st.slots_host, (size_t)s->opts.frame_slots * (size_t)P,
                                   cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&st.slots_dev, st.slots_host, 0);
@@ -539,9 +855,10 @@ int esi_stream_open(esi_server *s, int width, int height, const esi_params *para
     if (e == cudaSuccess) e = launch_fill_i64(st.T, P, params->t_origin_us, s->stream);
     if (e != cudaSuccess) {
         if (st.slots_host) cudaFreeHost(st.slots_host);
-        st.slots_host = nullptr;
         s->arena.release(off, sbytes);
-        return rc_of(e);
+        s->harena.release(roff, rbytes);
+        st = Stream();
+        return cuda_note(s, "stream open", e);
     }
     st.open = true;
     s->used += sbytes;
@@ -562,11 +879,15 @@ int esi_stream_push(esi_server *s, int id, const esi_event *ev, size_t n)
         if (ev[i].t_us < prev) return ESI_ETIMEORDER;
         prev = ev[i].t_us;
     }
-    if (st.pend_head > 0 && st.pend_head * 2 > st.pend.size()) {
-        st.pend.erase(st.pend.begin(), st.pend.begin() + (long)st.pend_head);
-        st.pend_head = 0;
-    }
-    st.pend.insert(st.pend.end(), ev, ev + n);
+    int rc = ring_reserve(s, id, n);
+    if (rc) return rc;
+    // copy into the ring (two pieces where it wraps)
+    const unsigned long long mask = st.ring_cap - 1;
+    const size_t i0 = (size_t)(st.tail & mask);
+    const size_t n1 = std::min(n, (size_t)(st.ring_cap - i0));
+    copy_events(s, st.ring_h + i0, ev, n1);
+    if (n1 < n) copy_events(s, st.ring_h, ev + n1, n - n1);
+    st.tail += n;
     st.last_event_t = prev;
     st.last_push_ns = wall_ns();
     s->n_packets += 1;
@@ -629,10 +950,17 @@ int esi_stream_autotune(esi_server *s, int id, const esi_event *sample, size_t n
     return rc;
 }
 
-int esi_server_tick(esi_server *s, int64_t now_us)
+namespace {
+
+constexpr int kFlushNone = -1;  // tick_impl: apply as apply_mode says
+constexpr int kFlushAll = -2;   // tick_impl: apply every stream's events
+
+// One tick (esi_server_tick).  flush: kFlushNone, kFlushAll or a stream id
+// whose events are applied whatever apply_mode says.
+int tick_impl(esi_server *s, long long now_us, int flush)
 {
-    if (!s) return ESI_EINVAL;
     const long long call_ns = wall_ns();
+    s->last_now = std::max(s->last_now, now_us);
     poll(s);
     const int b = s->stage_next;
     if (s->stage_busy[b]) {
@@ -648,7 +976,6 @@ int esi_server_tick(esi_server *s, int64_t now_us)
     TileArgs *tj = reinterpret_cast<TileArgs *>(stg + s->off_tilejob);
     WinInfo *win = reinterpret_cast<WinInfo *>(stg + s->off_win);
     unsigned char **fout = reinterpret_cast<unsigned char **>(stg + s->off_fout);
-    esi_event *evs = reinterpret_cast<esi_event *>(stg + s->off_events);
 
     TickRec *rec = new (std::nothrow) TickRec();
     if (!rec) return ESI_ENOMEM;
@@ -674,33 +1001,33 @@ int esi_server_tick(esi_server *s, int64_t now_us)
             fr.push_back(tf);
             tf += s->opts.frame_period_us;
         }
-        // every tick applies what has arrived, so a frame's tick only has the
-        // newest events left to do
-        const size_t avail = st.pend.size() - st.pend_head;
+        // every tick applies what has arrived (EVERY_TICK), so a frame's tick
+        // only has the newest events left to do; or the events wait for the
+        // frame's tick (AT_FRAMES), unless so many are pending that the
+        // frame's tick could not take them all
+        const size_t avail = (size_t)(st.tail - st.head);
         if (fr.empty() && avail == 0) continue;
+        if (fr.empty() && s->opts.apply_mode == ESI_APPLY_AT_FRAMES && avail < (size_t)kDeferCap &&
+            flush != kFlushAll && flush != id)
+            continue;
         // events: t <= now, or <= the last frame when frames wait for the next tick
         long long lim_t = upto;
         if (tf <= upto) lim_t = fr.empty() ? st.push_floor : fr.back();
-        const esi_event *pb = st.pend.data() + st.pend_head;
-        size_t take = (size_t)(std::upper_bound(pb, pb + avail, lim_t,
-                                                [](long long v, const esi_event &e) { return v < e.t_us; }) -
-                               pb);
+        size_t take = ring_count_upto(st, avail, lim_t);
         take = std::min(take, (size_t)ev_cap_stream);
         if (n_ev + (long long)take > s->cap_events) take = (size_t)std::max<long long>(0, s->cap_events - n_ev);
         if (take > 0 && take < avail) {
             // frames after an event left for later must wait too
-            const long long t_left = pb[take].t_us;
+            const long long t_left = ring_at(st, st.head + take).t_us;
             while (!fr.empty() && fr.back() >= t_left) fr.pop_back();
         }
         if (take > 0) {
             // record times are 32-bit offsets from the first event
-            const long long lim = pb[0].t_us + 0xffffffffll;
-            size_t ok = (size_t)(std::upper_bound(pb, pb + take, lim,
-                                                  [](long long v, const esi_event &e) { return v < e.t_us; }) -
-                                 pb);
+            const long long lim = ring_at(st, st.head).t_us + 0xffffffffll;
+            const size_t ok = ring_count_upto(st, take, lim);
             if (ok < take) {
                 take = ok;
-                const long long t_left = pb[take].t_us;
+                const long long t_left = ring_at(st, st.head + take).t_us;
                 while (!fr.empty() && fr.back() >= t_left) fr.pop_back();
             }
         }
@@ -712,13 +1039,12 @@ int esi_server_tick(esi_server *s, int64_t now_us)
             n_items_total + st.n_tiles > s->cap_items)
             break;  // the tick is full: the rest waits for the next one
         const int j = n_jobs++;
-        const long long t_base = take ? pb[0].t_us : fr.front();
-        std::memcpy(evs + n_ev, pb, take * sizeof(esi_event));
-        // binning job
+        const long long t_base = take ? ring_at(st, st.head).t_us : fr.front();
+        // binning job: the device reads the events from the stream's ring
         BinJob &B = bj[j];
-        B.args.ring = reinterpret_cast<const esi_event *>(s->dtab + s->off_events) + n_ev;
-        B.args.ring_mask = ~0ull >> 1;
-        B.args.first = 0;
+        B.args.ring = st.ring_d;
+        B.args.ring_mask = st.ring_cap - 1;
+        B.args.first = st.head;
         B.args.n = (int)take;
         B.args.chunk = kChunk;
         B.args.t_base = t_base;
@@ -775,7 +1101,8 @@ int esi_server_tick(esi_server *s, int64_t now_us)
         job_stream.push_back({j, id});
         st.seq_issued += fr.size();
         if (!fr.empty()) st.next_frame_t = fr.back() + s->opts.frame_period_us;
-        st.pend_head += take;
+        st.head += take;
+        if (take) rec->used.push_back({id, st.head});
         if (!fr.empty()) st.push_floor = std::max(st.push_floor, fr.back());
         n_ev += (long long)take;
         n_chunks += chunks;
@@ -814,17 +1141,22 @@ int esi_server_tick(esi_server *s, int64_t now_us)
     dir->off_chunkjob = (long long)s->off_chunkjob;
     dir->off_tilejob = (long long)s->off_tilejob;
 
-    // tables and events to the device; tick kernels; completion stamp
-    cudaError_t e = cudaMemcpyAsync(s->dtab, stg, s->off_items + (size_t)item_off * sizeof(int2),
-                                    cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess && n_ev)
-        e = cudaMemcpyAsync(s->dtab + s->off_events, stg + s->off_events,
-                            (size_t)n_ev * sizeof(esi_event), cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(s->stage_ev[b], s->stream);
-    if (e != cudaSuccess) {
+    // a tick that fails to queue returns its events to the pool
+    auto drop = [&](int rc) {
+        for (cudaEvent_t ev : {rec->evc, rec->ev0, rec->ev1})
+            if (ev) s->ev_pool.push_back(ev);
         delete rec;
-        return rc_of(e);
-    }
+        return rc;
+    };
+    // the table to the device (the kernels read the events from the
+    // streams' rings); tick kernels; completion stamp
+    rec->evc = take_event(s);
+    cudaError_t e = cudaEventRecord(rec->evc, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->dtab, stg, s->off_items + (size_t)item_off * sizeof(int2),
+                            cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s->stage_ev[b], s->stream);
+    if (e != cudaSuccess) return drop(cuda_note(s, "tick", e));
     s->stage_busy[b] = true;
     s->stage_next = 1 - b;
     rec->ev0 = take_event(s);
@@ -837,10 +1169,7 @@ int esi_server_tick(esi_server *s, int64_t now_us)
         if (s->opts.use_graph) {
             if (!s->gexec || (groups & ~s->graph_groups)) {
                 int rc = build_graph(s, groups | s->graph_groups);
-                if (rc) {
-                    delete rec;
-                    return rc;
-                }
+                if (rc) return drop(rc);
             }
             e = cudaGraphLaunch(s->gexec, s->stream);
             int ng = 0;
@@ -855,16 +1184,49 @@ int esi_server_tick(esi_server *s, int64_t now_us)
         }
     }
     if (e == cudaSuccess) e = cudaEventRecord(rec->ev1, s->stream);
-    if (e != cudaSuccess) {
-        delete rec;
-        return rc_of(e);
-    }
+    if (e != cudaSuccess) return drop(cuda_note(s, "tick", e));
     s->ticks_issued += 1;
+    rec->n_events = n_ev;
+    rec->n_streams = n_jobs;
+    rec->n_items = (int)item_off;
+    rec->issued_ns = wall_ns();
     s->inflight.push_back(rec);
     s->n_ticks += 1;
     s->n_events += (unsigned long long)n_ev;
-    s->host_tick.push_back((double)(wall_ns() - call_ns) * 1e-6);
+    s->host_tick.push_back((double)(rec->issued_ns - call_ns) * 1e-6);
     return ESI_OK;
+}
+
+// Apply the pending events of stream `which` (kFlushAll: every stream) up
+// to the last tick's time, then wait for every queued tick.  Bounded: a tick
+// may be full and leave events for the next one.
+int flush_events(esi_server *s, int which)
+{
+    for (int guard = 0; guard < 4096; ++guard) {
+        bool left = false;
+        for (int id = 0; id < (int)s->streams.size() && !left; ++id) {
+            const Stream &st = s->streams[id];
+            if (!st.open || (which != kFlushAll && id != which) || st.head == st.tail) continue;
+            const long long upto = std::min(s->last_now, st.watermark);
+            left = ring_at(st, st.head).t_us <= upto;
+        }
+        if (!left) return wait_all(s);
+        if (!s->inflight.empty()) {
+            cudaError_t e = cudaEventSynchronize(s->inflight.front()->ev1);
+            if (e != cudaSuccess) return rc_of(e);
+        }
+        int rc = tick_impl(s, s->last_now, which);
+        if (rc) return rc;
+    }
+    return ESI_ERANGE;
+}
+
+}  // namespace
+
+int esi_server_tick(esi_server *s, int64_t now_us)
+{
+    if (!s) return ESI_EINVAL;
+    return tick_impl(s, now_us, kFlushNone);
 }
 
 int esi_stream_frame(esi_server *s, int id, uint8_t *out, int64_t *t_frame, double *latency_ms)
@@ -924,7 +1286,7 @@ int esi_stream_state(esi_server *s, int id, float *S, int64_t *T)
 {
     if (!s || id < 0 || id >= (int)s->streams.size() || !s->streams[id].open || !S || !T)
         return ESI_EINVAL;
-    int rc = wait_all(s);
+    int rc = flush_events(s, id);
     if (rc) return rc;
     Stream &st = s->streams[id];
     cudaError_t e = cudaMemcpy(S, st.S, (size_t)st.P * 4, cudaMemcpyDeviceToHost);
@@ -940,6 +1302,7 @@ int esi_stream_close(esi_server *s, int id)
     Stream &st = s->streams[id];
     s->arena.release(st.arena_off, st.arena_bytes);
     s->used -= st.arena_bytes;
+    if (st.ring_h) s->harena.release(st.ring_off, st.ring_bytes);
     if (st.slots_host) cudaFreeHost(st.slots_host);
     st = Stream();
     s->n_open -= 1;
@@ -976,7 +1339,29 @@ int esi_server_get_stats(esi_server *s, esi_server_stats *out)
     out->host_tick_p50_ms = percentile(s->host_tick, 0.50);
     out->host_tick_p99_ms = percentile(s->host_tick, 0.99);
     out->gpu_tick_p99_ms = percentile(s->gpu_tick, 0.99);
+    out->host_pool_bytes = (uint64_t)s->opts.host_pool_bytes;
+    out->host_pool_used_bytes = s->harena.used();
+    out->host_pool_peak_bytes = s->hpool_peak;
+    out->ring_grows = s->ring_grows;
     return ESI_OK;
+}
+
+int esi_server_trace(esi_server *s, esi_tick_trace *out, size_t cap, size_t *n)
+{
+    if (!s || !n || (cap && !out)) return ESI_EINVAL;
+    poll(s);
+    const size_t have = s->trace.size();
+    const size_t k = std::min(cap, have);
+    // oldest first: once the ring wrapped, its oldest record sits at trace_n % kTraceCap
+    const size_t first = have < kTraceCap ? 0 : s->trace_n % kTraceCap;
+    for (size_t i = 0; i < k; ++i) out[i] = s->trace[(first + (have - k) + i) % have];
+    *n = cap ? k : have;
+    return ESI_OK;
+}
+
+const char *esi_server_last_error(esi_server *s)
+{
+    return s ? s->err.c_str() : "";
 }
 
 int esi_server_reset_stats(esi_server *s)
@@ -987,10 +1372,14 @@ int esi_server_reset_stats(esi_server *s)
     s->pkt_lat.clear();
     s->host_tick.clear();
     s->gpu_tick.clear();
+    s->trace.clear();
+    s->trace_n = 0;
     s->n_ticks = s->n_frames = s->n_events = s->n_packets = 0;
     s->n_admitted = s->n_refused = s->n_events_refused = 0;
     s->gpu_ms = 0.0;
     s->gpu_n = 0;
+    s->hpool_peak = s->harena.used();
+    s->ring_grows = 0;
     return ESI_OK;
 }
 
@@ -1064,6 +1453,7 @@ int esi_server_run(esi_server *s, const esi_packet *pk, size_t n, int64_t tick_u
         if (spec) slot_spec[slot] = spec;
         if (slot_spec[slot]) slot_spec[slot]->stream_id = id;
     };
+    s->err.clear();
     const long long t0 = wall_ns();
     const long long min_gap = std::max<long long>(1, tick_us / 5);
     size_t i = 0;
@@ -1111,7 +1501,13 @@ int esi_server_run(esi_server *s, const esi_packet *pk, size_t n, int64_t tick_u
                     if (!rc) rc = esi_stream_watermark(s, id, q.arrival_us);
                 }
             }
-            if (rc) return rc;
+            if (rc) {
+                char m[160];
+                std::snprintf(m, sizeof(m), "packet %zu (slot %d, kind %d, %llu events, arrival %lld us, now %lld us): ",
+                              i, q.stream, q.kind, (unsigned long long)q.n, (long long)q.arrival_us, now);
+                s->err = m + (s->err.empty() ? std::string(esi_strerror(rc)) : s->err);
+                return rc;
+            }
         }
         // tick at the tick period, and early when a packet has made a frame due
         bool due = false;

@@ -58,7 +58,8 @@ class esi_server_opts(ctypes.Structure):
                 ("max_streams", ctypes.c_int32), ("frame_slots", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("max_stream_pixels", ctypes.c_int32), ("scan_chain", ctypes.c_int32),
-                ("_reserved", ctypes.c_int32 * 2)]
+                ("apply_mode", ctypes.c_int32), ("copy_threads", ctypes.c_int32),
+                ("host_pool_bytes", ctypes.c_int64)]
 
 
 class esi_server_stats(ctypes.Structure):
@@ -71,10 +72,21 @@ class esi_server_stats(ctypes.Structure):
                 ("kernel_launches_per_tick", ctypes.c_int32),
                 ("streams_admitted", ctypes.c_uint64), ("streams_refused", ctypes.c_uint64),
                 ("events_refused", ctypes.c_uint64), ("host_tick_p50_ms", ctypes.c_double),
-                ("host_tick_p99_ms", ctypes.c_double), ("gpu_tick_p99_ms", ctypes.c_double)]
+                ("host_tick_p99_ms", ctypes.c_double), ("gpu_tick_p99_ms", ctypes.c_double),
+                ("host_pool_bytes", ctypes.c_uint64), ("host_pool_used_bytes", ctypes.c_uint64),
+                ("host_pool_peak_bytes", ctypes.c_uint64), ("ring_grows", ctypes.c_uint64)]
 
 
 ESI_PACKET_EVENTS, ESI_PACKET_OPEN, ESI_PACKET_CLOSE = 0, 1, 2
+ESI_APPLY_EVERY_TICK, ESI_APPLY_AT_FRAMES = 1, 2
+
+
+class esi_tick_trace(ctypes.Structure):
+    _fields_ = [("call_ns", ctypes.c_int64), ("issued_ns", ctypes.c_int64),
+                ("ready_ns", ctypes.c_int64), ("copy_ms", ctypes.c_float),
+                ("kernels_ms", ctypes.c_float), ("gap_ms", ctypes.c_float),
+                ("frames", ctypes.c_int32), ("events", ctypes.c_int64),
+                ("streams", ctypes.c_int32), ("items", ctypes.c_int32)]
 
 
 class esi_packet(ctypes.Structure):
@@ -119,6 +131,8 @@ SIGNATURES = {
     "esi_stream_open": (_i32, [_P, _i32, _i32, ctypes.POINTER(esi_params), ctypes.POINTER(_i32)]),
     "esi_stream_push": (_i32, [_P, _i32, _P, _sz]),
     "esi_server_tick": (_i32, [_P, _i64]),
+    "esi_server_trace": (_i32, [_P, _P, _sz, ctypes.POINTER(_sz)]),
+    "esi_server_last_error": (ctypes.c_char_p, [_P]),
     "esi_stream_watermark": (_i32, [_P, _i32, _i64]),
     "esi_stream_set_tile_h": (_i32, [_P, _i32, _i32]),
     "esi_stream_autotune": (_i32, [_P, _i32, _P, _sz, _i32, ctypes.POINTER(_i32)]),
@@ -397,6 +411,29 @@ def esi_stream_state(srv, stream_id: int, S, T) -> int:
 
 def esi_stream_close(srv, stream_id: int) -> int:
     return _fn("esi_stream_close")(srv, int(stream_id))
+
+
+def esi_server_trace(srv):
+    """(rc, numpy structured array of the kept tick records, oldest first)."""
+    import numpy as np
+    n = _sz(0)
+    rc = _fn("esi_server_trace")(srv, None, 0, ctypes.byref(n))
+    if rc != ESI_OK:
+        return rc, None
+    buf = (esi_tick_trace * max(n.value, 1))()
+    rc = _fn("esi_server_trace")(srv, ctypes.cast(buf, _P), n.value, ctypes.byref(n))
+    if rc != ESI_OK:
+        return rc, None
+    dt = np.dtype([("call_ns", np.int64), ("issued_ns", np.int64), ("ready_ns", np.int64),
+                   ("copy_ms", np.float32), ("kernels_ms", np.float32), ("gap_ms", np.float32),
+                   ("frames", np.int32), ("events", np.int64), ("streams", np.int32),
+                   ("items", np.int32)], align=True)
+    assert dt.itemsize == ctypes.sizeof(esi_tick_trace)
+    return ESI_OK, np.frombuffer(bytes(buf)[:n.value * dt.itemsize], dtype=dt).copy()
+
+
+def esi_server_last_error(srv) -> str:
+    return (_fn("esi_server_last_error")(srv) or b"").decode()
 
 
 def esi_server_sync(srv) -> int:

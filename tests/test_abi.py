@@ -84,9 +84,25 @@ def test_method_constants_match_the_header():
     import os
     import re
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "esi.h")).read()
-    for name in ("ESI_METHOD_ALG2", "ESI_METHOD_ALG1", "ESI_METHOD_EQ3_EXP"):
+    for name in ("ESI_METHOD_ALG2", "ESI_METHOD_ALG1", "ESI_METHOD_EQ3_EXP",
+                 "ESI_APPLY_EVERY_TICK", "ESI_APPLY_AT_FRAMES"):
         m = re.search(r"#define\s+%s\s+(\d+)" % name, hdr)
         assert m and int(m.group(1)) == getattr(esi, name), name
+
+
+def test_server_options_are_checked_before_touching_cuda():
+    for field, bad in (("apply_mode", 3), ("apply_mode", -1), ("copy_threads", 17),
+                       ("copy_threads", -1), ("host_pool_bytes", 4096), ("scan_chain", 34),
+                       ("frame_slots", 1), ("tile_h", 5)):
+        opts = esi.esi_server_opts()
+        setattr(opts, field, bad)
+        rc, srv = esi.esi_server_create(1 << 20, opts, 0)
+        assert rc == esi.ESI_EINVAL and not srv, field
+
+
+def test_server_trace_and_last_error_reject_null_servers():
+    assert esi.esi_server_trace(None)[0] == esi.ESI_EINVAL
+    assert esi.esi_server_last_error(None) == ""
 
 
 def test_bin_events_checks_its_arguments_before_touching_cuda():

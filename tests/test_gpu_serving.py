@@ -11,7 +11,8 @@ import pytest
 
 import oracle
 import synth
-from esi_harness import EXACT, GpuStream, compare, oracle_params, random_events, run_oracle
+from esi_harness import (EXACT, STATE_TOL, GpuStream, compare, oracle_params, random_events,
+                         run_oracle, state_error)
 
 pytestmark = pytest.mark.gpu
 
@@ -83,13 +84,16 @@ def drive(esi, srv, ids, events, dims, t_end, tick_us=1000, start=0, on_tick=Non
 
 
 def serve(stream_specs, t_end, use_graph=1, budget=256 << 20, tile_hs=None, retile=None,
-          scan_chain=0):
+          scan_chain=0, apply_mode=0):
     """tile_hs: {spec index: tile height} set at open; retile: (time, {index: tile height})
-    applied before that tick; scan_chain: the server's segmented-scan knob (33: off)."""
+    applied before that tick; scan_chain: the server's segmented-scan knob (33: off);
+    apply_mode: when the server applies a stream's events (0: default)."""
     esi = _esi()
     opts = esi.esi_server_opts()
     opts.use_graph = use_graph
     opts.scan_chain = scan_chain
+    opts.apply_mode = apply_mode
+    opts.host_pool_bytes = 64 << 20
     rc, srv = esi.esi_server_create(budget, opts, 0)
     assert rc == 0
     try:
@@ -144,6 +148,146 @@ def test_served_streams_match_the_oracle():
         st_ref.integrate(used[n_used:])
         got = {"S": S, "T": T, "frames": np.stack([frames[t] for t in expect_tf])}
         compare(got, {"S": st_ref.S, "T": st_ref.T, "frames": ref_frames}, pp["C"], f"stream {i}")
+
+
+def test_both_apply_modes_match_each_other():
+    # events applied every tick or only in frame ticks: the same frames and
+    # states (with the scan off, bit for bit; the record groups differ)
+    esi = _esi()
+    t_end = 90_000
+    specs = list(enumerate(STREAMS[:4]))
+    every, st_e = serve(specs, t_end, scan_chain=33, apply_mode=esi.ESI_APPLY_EVERY_TICK)
+    frames_only, st_f = serve(specs, t_end, scan_chain=33, apply_mode=esi.ESI_APPLY_AT_FRAMES)
+    for i, _ in specs:
+        fe, (Se, Te), _ = every[i]
+        ff, (Sf, Tf), _ = frames_only[i]
+        assert sorted(fe) == sorted(ff)
+        for t in fe:
+            assert np.array_equal(fe[t], ff[t]), (i, t)
+        assert np.array_equal(Se, Sf) and np.array_equal(Te, Tf)
+    assert st_e.frames == st_f.frames and st_e.events == st_f.events
+
+
+def test_frame_only_mode_holds_events_back_until_a_frame_or_a_state_read():
+    esi = _esi()
+    W, H = 96, 40
+    opts = esi.esi_server_opts()
+    opts.apply_mode = esi.ESI_APPLY_AT_FRAMES
+    opts.host_pool_bytes = 16 << 20
+    rc, srv = esi.esi_server_create(64 << 20, opts, 0)
+    assert rc == 0
+    try:
+        pp = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1, t_origin_us=0)
+        rc, sid = esi.esi_stream_open(srv, W, H, esi.make_params(**pp))
+        assert rc == 0
+        ev = random_events(np.random.default_rng(3), W, H, 3000, 0, 4000)
+        assert esi.esi_stream_push(srv, sid, ev, len(ev)) == 0
+        for now in (1000, 2000, 4000):
+            assert esi.esi_server_tick(srv, now) == 0
+        assert esi.esi_server_sync(srv) == 0
+        rc, st = esi.esi_server_get_stats(srv)
+        assert rc == 0 and st.events == 0 and st.frames == 0   # no frame due before 10 ms
+        S = np.empty(W * H, dtype=np.float32)
+        T = np.empty(W * H, dtype=np.int64)
+        assert esi.esi_stream_state(srv, sid, S, T) == 0       # applies the held events
+        rc, st = esi.esi_server_get_stats(srv)
+        assert st.events == len(ev)
+        ref = oracle.OracleState(W, H, oracle_params(pp))
+        ref.integrate(ev)
+        assert np.array_equal(T, ref.T)
+        assert state_error(S, ref.S, pp["C"]) <= STATE_TOL
+    finally:
+        esi.esi_server_destroy(srv)
+
+
+def test_event_rings_grow_and_refuse_pushes_beyond_the_host_pool():
+    # a stream's ring starts at 16384 events and doubles on demand inside the
+    # pinned host pool; a push that cannot fit is refused whole (ESI_ENOMEM,
+    # with the reason in esi_server_last_error) and the stream carries on with
+    # the events it had
+    esi = _esi()
+    W, H = 200, 150
+    opts = esi.esi_server_opts()
+    opts.host_pool_bytes = 8 << 20            # 524288 events
+    rc, srv = esi.esi_server_create(64 << 20, opts, 0)
+    assert rc == 0
+    try:
+        pp = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1, t_origin_us=0)
+        rc, sid = esi.esi_stream_open(srv, W, H, esi.make_params(**pp))
+        assert rc == 0
+        ev = random_events(np.random.default_rng(11), W, H, 400_000, 0, 40_000)
+        a, b = 100_000, 300_000
+        assert esi.esi_stream_push(srv, sid, ev[:a], a) == 0      # grows to 262144 events
+        assert esi.esi_stream_push(srv, sid, ev[a:b], b - a) == esi.ESI_ENOMEM
+        assert "host pool full" in esi.esi_server_last_error(srv)
+        t_a = int(ev["t"][a - 1])                                  # about 10 ms
+        for now in list(range(1000, t_a, 1000)) + [t_a]:
+            assert esi.esi_server_tick(srv, now) == 0
+        assert esi.esi_server_sync(srv) == 0
+        # the refused push left nothing behind: the rest goes in packet by packet
+        for lo in range(a, len(ev), 20_000):
+            part = ev[lo:lo + 20_000]
+            assert esi.esi_stream_push(srv, sid, part, len(part)) == 0
+            assert esi.esi_server_tick(srv, int(part["t"][-1])) == 0
+        S = np.empty(W * H, dtype=np.float32)
+        T = np.empty(W * H, dtype=np.int64)
+        assert esi.esi_stream_state(srv, sid, S, T) == 0
+        ref = oracle.OracleState(W, H, oracle_params(pp))
+        ref.integrate(ev)
+        assert np.array_equal(T, ref.T)
+        assert state_error(S, ref.S, pp["C"]) <= STATE_TOL
+        rc, n_done = esi.esi_stream_frames_done(srv, sid)
+        assert rc == 0 and n_done == int(ev["t"][-1]) // 10_000    # 10, 20, 30 ms
+        rc, st = esi.esi_server_get_stats(srv)
+        assert st.ring_grows >= 1 and st.host_pool_peak_bytes >= (262144 * 16)
+    finally:
+        esi.esi_server_destroy(srv)
+
+
+def test_tick_trace_records_every_tick_with_work():
+    esi = _esi()
+    W, H = 96, 40
+    rc, srv = esi.esi_server_create(64 << 20, None, 0)
+    assert rc == 0
+    try:
+        pp = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1, t_origin_us=0)
+        rc, sid = esi.esi_stream_open(srv, W, H, esi.make_params(**pp))
+        assert rc == 0
+        ev = random_events(np.random.default_rng(5), W, H, 20_000, 0, 30_000)
+        n_ticks, lo = 0, 0
+        for now in range(1000, 30_001, 1000):
+            hi = int(np.searchsorted(ev["t"], now, side="right"))
+            part = ev[lo:hi]
+            lo = hi
+            assert esi.esi_stream_push(srv, sid, part, len(part)) == 0
+            assert esi.esi_server_tick(srv, now) == 0
+            n_ticks += 1
+        assert esi.esi_server_sync(srv) == 0
+        rc, tr = esi.esi_server_trace(srv)
+        assert rc == 0 and len(tr) == n_ticks
+        assert int(tr["events"].sum()) == len(ev)
+        assert int(tr["frames"].sum()) == 3
+        assert np.all(np.diff(tr["call_ns"]) > 0)
+        # a small tick can finish on the device before its call has returned
+        assert np.all(tr["issued_ns"] >= tr["call_ns"]) and np.all(tr["ready_ns"] >= tr["call_ns"])
+        assert np.all(tr["kernels_ms"] > 0) and tr["gap_ms"][0] == -1.0
+        assert esi.esi_server_reset_stats(srv) == 0
+        rc, tr = esi.esi_server_trace(srv)
+        assert rc == 0 and len(tr) == 0
+    finally:
+        esi.esi_server_destroy(srv)
+
+
+def test_apply_mode_validation():
+    esi = _esi()
+    for mode, threads, ok in ((0, 0, True), (1, 1, True), (2, 16, True), (3, 0, False),
+                              (-1, 0, False), (0, 17, False)):
+        opts = esi.esi_server_opts()
+        opts.apply_mode, opts.copy_threads = mode, threads
+        rc, srv = esi.esi_server_create(1 << 20, opts, 0)
+        assert (rc == 0) == ok, (mode, threads, rc)
+        if rc == 0:
+            esi.esi_server_destroy(srv)
 
 
 def test_each_stream_is_the_same_alone_and_in_the_mix():

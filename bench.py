@@ -65,10 +65,10 @@ WORKLOADS = {
 }
 HEADLINE = "c2"
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel, from one ncu capture of the headline's launch shape
-# (--ncu-case), keyed by kernel; None until a capture of the kernel as built.
-NCU_TRAFFIC_PER_LAUNCH = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture of a full launch of the headline's shape (--ncu-case: its
+# second sub-batch, 4.19 M events and 8 frames), keyed by kernel.
+NCU_TRAFFIC_PER_LAUNCH = {"esi_tile": 48845312, "esi_bin": 70952448}
 
 
 def parse_args():
@@ -364,6 +364,7 @@ def bench_esi(args):
         "frames_per_s": frames_per_s,
         "roofline": roof,
         "roofline_binning": tile_roofline(r["prof"], P, M, args.steps, n_ev, peak, peak_kind,
+                                          traffic=NCU_TRAFFIC_PER_LAUNCH.get("esi_bin"),
                                           name="esi_bin"),
         "step_roofline": {"bytes_per_step": step_bytes,
                           "achieved_gbs": step_bytes / (ms / args.steps / 1e3) / 1e9,
@@ -585,6 +586,18 @@ def _server_run(esi, srv, pk, npk, t_end, realtime, tick_us=1000):
         raise RuntimeError(f"esi_server_run: {esi.esi_strerror(rc)}: {esi.esi_server_last_error(srv)}")
 
 
+def _tick_gaps(esi, srv):
+    """From the server's tick trace: the longest wait between two tick calls
+    with work, and how many exceeded 2 ms (the executor fell behind)."""
+    rc, tr = esi.esi_server_trace(srv)
+    if rc or tr is None or len(tr) < 2:
+        return {}
+    gaps = np.diff(tr["call_ns"]) / 1e6
+    return {"max_tick_gap_ms": round(float(gaps.max()), 3),
+            "tick_gaps_over_2ms": int((gaps > 2.0).sum()),
+            "traced_ticks": int(len(tr))}
+
+
 def _stats(st, dt, realtime, n_ev, expected=None):
     d = {"frames": int(st.frames),
          "frame_latency_p50_ms": st.frame_latency_p50_ms,
@@ -633,8 +646,10 @@ def serving_leg(esi, seconds=SERVING_SECONDS):
         _server_run(esi, srv, pk, npk, t_end, realtime)
         dt = time.perf_counter() - t0
         rc, st = esi.esi_server_get_stats(srv)
+        tick_gaps = _tick_gaps(esi, srv)
         esi.esi_server_destroy(srv)
         out[mode] = _stats(st, dt, realtime, n_ev, expected)
+        out[mode].update(tick_gaps)
     pk, npk = _packets(esi, [_event_part(esi, k, s["events"], s["arrivals"])
                              for k, s in enumerate(streams)])
     t0 = time.perf_counter()
@@ -712,8 +727,10 @@ def mixed_serving_leg(esi, seconds=SERVING_SECONDS):
         _server_run(esi, srv, pk, npk, t_end, realtime)
         dt = time.perf_counter() - t0
         rc, st = esi.esi_server_get_stats(srv)
+        tick_gaps = _tick_gaps(esi, srv)
         esi.esi_server_destroy(srv)
         out[mode] = _stats(st, dt, realtime, n_ev, expected)
+        out[mode].update(tick_gaps)
         out[mode]["streams_admitted"] = int(st.streams_admitted)
         out[mode]["streams_refused"] = int(st.streams_refused)
     return out

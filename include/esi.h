@@ -345,8 +345,9 @@ const char *esi_strerror(int code);
  *
  * Admission: each stream's device state (12 bytes per pixel) comes from an
  * arena of state_budget_bytes reserved at creation; esi_stream_open returns
- * ESI_EBUSY when it does not fit, and esi_stream_close returns the space, so a
- * later open can succeed.  Streams may open and close between ticks; work of
+ * ESI_EBUSY when it does not fit (nor its event ring and frame slots in the
+ * pinned host pool), and esi_stream_close returns the space, so a later open
+ * can succeed.  Streams may open and close between ticks; work of
  * successive ticks overlaps on the device (two host staging buffers).
  */
 typedef struct {
@@ -364,9 +365,11 @@ typedef struct {
     int32_t copy_threads;         /* host threads that copy a large push into its
                                    * ring, the caller's included: 0 = default (4),
                                    * 1 .. 16                                   */
-    int64_t host_pool_bytes;      /* pinned host memory holding the streams'
-                                   * pending events (a ring per stream, grown on
-                                   * demand); 0 = default (256 MB)             */
+    int64_t host_pool_bytes;      /* pinned, mapped host memory holding the
+                                   * streams' pending events (a ring per stream,
+                                   * grown on demand) and frame slots
+                                   * (frame_slots x W x H each); 0 = default
+                                   * (512 MB)                                  */
 } esi_server_opts;
 
 /* esi_server_opts.apply_mode.  EVERY_TICK: each tick applies every stream's
@@ -478,7 +481,11 @@ int esi_stream_autotune(esi_server *srv, int stream_id, const esi_event *sample,
  * apply mode held back are applied first); waits. */
 int esi_stream_state(esi_server *srv, int stream_id, float *S, int64_t *T);
 
-/* Close a stream: waits for its work, returns its state memory. */
+/* Close a stream.  Returns at once: the id may be reused by the next open;
+ * ticks already queued still finish its work and deliver its frames to its
+ * frame sink, and its state, ring and frame slots go back to the budget and
+ * the host pool when they are done (esi_stream_open waits for them when it
+ * needs that memory). */
 int esi_stream_close(esi_server *srv, int stream_id);
 
 /* Wait for all queued ticks. */
@@ -558,7 +565,7 @@ typedef struct {
  * to it; when admission is refused (ESI_EBUSY) the slot's later packets are
  * dropped and counted (streams_refused, events_refused).  A CLOSE packet
  * renders the slot's frames that are due (up to its last packet), then closes
- * the stream (esi_stream_close: it waits for the stream's work); its events
+ * the stream (esi_stream_close); its events
  * after its last frame are discarded.  After the last tick the executor ticks
  * again at t_end_us until every due frame is issued, then waits.
  * A slot that no OPEN packet of this call has bound names a server stream id

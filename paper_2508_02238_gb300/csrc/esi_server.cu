@@ -10,7 +10,8 @@
 // render mode x decay kind x row alignment) as parallel graph branches.  The kernels
 // read their sizes and per-stream descriptors from the device table, so one
 // captured CUDA graph serves every tick; frames are written straight into
-// mapped host memory.  A host-function node stamps each tick's completion.
+// mapped host memory.  A host function queued after each tick stamps its
+// completion.
 #include <time.h>
 
 #include <algorithm>
@@ -220,8 +221,10 @@ struct Stream {
     long long next_frame_t = 0;
     long long watermark = LLONG_MAX;      // events complete up to here
     long long last_push_ns = 0;
-    unsigned char *slots_host = nullptr;  // frame_slots * P bytes, mapped
+    unsigned char *slots_host = nullptr;  // frame_slots * P bytes in the host pool, mapped
     unsigned char *slots_dev = nullptr;
+    size_t slots_off = 0, slots_bytes = 0;
+    unsigned long long gen = 0;           // which opening of this id (ticks name it)
     unsigned long long seq_issued = 0;    // frames handed to ticks
     unsigned long long seq_done = 0;      // frames finished
     std::vector<long long> slot_t;
@@ -234,6 +237,7 @@ struct Stream {
 
 struct TickFrame {
     int stream;
+    unsigned long long gen;
     unsigned long long seq;
     long long t_frame;
     long long ref_push_ns;
@@ -241,7 +245,11 @@ struct TickFrame {
 
 struct TickRec {
     unsigned long long id = 0;
-    std::vector<std::pair<int, unsigned long long>> used;  // (stream, ring index it read up to)
+    struct Use {
+        int stream;
+        unsigned long long gen, upto;  // the ring index it read up to
+    };
+    std::vector<Use> used;
     long long call_ns = 0, issued_ns = 0;
     std::vector<TickFrame> frames;
     cudaEvent_t evc = nullptr;             // before the copies
@@ -354,6 +362,14 @@ struct esi_server {
         size_t off, bytes;
     };
     std::vector<Retired> retired;
+    // closed streams whose ticks are still in flight: their frames are still
+    // delivered (sinks), their memory is freed once the tick count reaches tag
+    struct Zombie {
+        unsigned long long tag;
+        Stream st;
+    };
+    std::vector<Zombie> zombies;
+    unsigned long long gen_next = 1;
     size_t hpool_peak = 0;
     unsigned long long ring_grows = 0;
     CopyPool copiers;
@@ -383,6 +399,15 @@ cudaEvent_t take_event(esi_server *s)
     cudaEvent_t e = nullptr;
     cudaEventCreate(&e);
     return e;
+}
+
+// Return a closed stream's device state, ring and frame slots to their arenas.
+void free_stream_memory(esi_server *s, Stream &st)
+{
+    if (st.arena_bytes) s->arena.release(st.arena_off, st.arena_bytes);
+    if (st.ring_bytes) s->harena.release(st.ring_off, st.ring_bytes);
+    if (st.slots_bytes) s->harena.release(st.slots_off, st.slots_bytes);
+    st.arena_bytes = st.ring_bytes = st.slots_bytes = 0;
 }
 
 // Finish every tick whose completion stamp is in: frames become readable,
@@ -424,16 +449,22 @@ void poll(esi_server *s)
         s->ev_pool.push_back(t->evc);
         s->ev_pool.push_back(t->ev0);
         for (const auto &u : t->used) {
-            Stream &st = s->streams[u.first];
-            if (st.open) st.done = std::max(st.done, u.second);
+            Stream &st = s->streams[u.stream];
+            if (st.open && st.gen == u.gen) st.done = std::max(st.done, u.upto);
         }
         for (const TickFrame &f : t->frames) {
-            Stream &st = s->streams[f.stream];
             const double lat = (double)(ready - t->call_ns) * 1e-6;
             s->frame_lat.push_back(lat);
             if (f.ref_push_ns) s->pkt_lat.push_back((double)(ready - f.ref_push_ns) * 1e-6);
             s->n_frames += 1;
-            if (!st.open) continue;
+            Stream *sp = &s->streams[f.stream];
+            if (!sp->open || sp->gen != f.gen) {  // closed since: its zombie, if any
+                sp = nullptr;
+                for (auto &z : s->zombies)
+                    if (z.st.gen == f.gen) sp = &z.st;
+                if (!sp) continue;
+            }
+            Stream &st = *sp;
             const int slot = (int)(f.seq % (unsigned long long)s->opts.frame_slots);
             st.slot_t[slot] = f.t_frame;
             st.slot_lat[slot] = lat;
@@ -447,7 +478,7 @@ void poll(esi_server *s)
         delete t;
     }
     s->inflight.erase(s->inflight.begin(), s->inflight.begin() + k);
-    // rings replaced while ticks that read them were in flight
+    // rings replaced, and streams closed, while ticks that read them were in flight
     const unsigned long long finished = s->comp->done.load(std::memory_order_acquire);
     size_t w = 0;
     for (size_t i = 0; i < s->retired.size(); ++i) {
@@ -455,7 +486,16 @@ void poll(esi_server *s)
         else s->retired[w++] = s->retired[i];
     }
     s->retired.resize(w);
+    w = 0;
+    for (size_t i = 0; i < s->zombies.size(); ++i) {
+        if (s->zombies[i].tag <= finished) free_stream_memory(s, s->zombies[i].st);
+        else if (w != i) s->zombies[w++] = std::move(s->zombies[i]);
+        else ++w;
+    }
+    s->zombies.resize(w);
 }
+
+void move_ring(esi_server *s, Stream &st, size_t off, unsigned long long cap, unsigned long long tag);
 
 // Room for n more events in stream id's ring: frees the slots of finished
 // ticks, waits for ticks in flight that still read slots it needs, or moves
@@ -487,8 +527,9 @@ int ring_reserve(esi_server *s, int id, size_t n)
         if (!fits()) st.done = st.head;  // no tick in flight reads this ring any more
         return ESI_OK;
     }
+    const unsigned long long need = st.tail - st.head + n;
     unsigned long long cap = st.ring_cap;
-    while (cap < 2 * (st.tail - st.head + n)) cap *= 2;
+    while (cap < need + need / 4) cap *= 2;
     const size_t bytes = (size_t)cap * sizeof(esi_event);
     const size_t off = s->harena.alloc(bytes);
     if (off == SIZE_MAX) {
@@ -501,17 +542,41 @@ int ring_reserve(esi_server *s, int id, size_t n)
     }
     s->hpool_peak = std::max(s->hpool_peak, s->harena.used());
     s->ring_grows += 1;
+    move_ring(s, st, off, cap, s->inflight.empty() ? 0 : s->ticks_issued);
+    return ESI_OK;
+}
+
+// Move stream st's pending events into the ring of cap events at pool
+// offset off; the old ring is freed now (tag 0) or once the tick count
+// reaches tag.
+void move_ring(esi_server *s, Stream &st, size_t off, unsigned long long cap, unsigned long long tag)
+{
     esi_event *nh = reinterpret_cast<esi_event *>(s->hpool + off);
     for (unsigned long long i = st.head; i < st.tail; ++i) nh[i & (cap - 1)] = ring_at(st, i);
-    if (s->inflight.empty()) s->harena.release(st.ring_off, st.ring_bytes);
-    else s->retired.push_back({s->ticks_issued, st.ring_off, st.ring_bytes});
+    if (tag == 0) s->harena.release(st.ring_off, st.ring_bytes);
+    else s->retired.push_back({tag, st.ring_off, st.ring_bytes});
     st.ring_h = nh;
     st.ring_d = reinterpret_cast<const esi_event *>(s->hpool_d + off);
     st.ring_off = off;
-    st.ring_bytes = bytes;
+    st.ring_bytes = (size_t)cap * sizeof(esi_event);
     st.ring_cap = cap;
     st.done = st.head;
-    return ESI_OK;
+}
+
+// After a tick took events: a ring grown large for a burst (16 times the
+// initial size or more) and now mostly empty goes back to a smaller one (the
+// tick being built still reads the old one).  Rings of ordinary size are left
+// alone, so steady traffic does not grow and shrink them tick after tick.
+void shrink_ring(esi_server *s, Stream &st)
+{
+    const unsigned long long pending = st.tail - st.head;
+    if (st.ring_cap < 16 * kRingInit || pending > st.ring_cap / 16) return;
+    unsigned long long cap = 4 * kRingInit;
+    while (cap < 4 * pending) cap *= 2;
+    if (cap >= st.ring_cap) return;
+    const size_t off = s->harena.alloc((size_t)cap * sizeof(esi_event));
+    if (off == SIZE_MAX) return;
+    move_ring(s, st, off, cap, s->ticks_issued + 1);
 }
 
 // Copy n events into a ring: large copies are split over the copy threads.
@@ -549,7 +614,7 @@ cudaError_t launch_group(esi_server *s, int g, cudaStream_t cs)
 
 // Capture the per-tick graph for the variant groups in `groups`: binning,
 // then the groups' tile launches as parallel branches (they touch disjoint
-// streams), joined before the completion stamp.
+// streams), joined at the end.
 int build_graph(esi_server *s, unsigned long long groups)
 {
     if (s->gexec) {
@@ -582,7 +647,6 @@ int build_graph(esi_server *s, unsigned long long groups)
         e = cudaEventRecord(ev[i], br[i]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[i], 0);
     }
-    if (e == cudaSuccess) e = cudaLaunchHostFunc(cs, on_tick_done, s->comp);
     if (capturing) {
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = e2;
@@ -641,7 +705,7 @@ int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts, vo
     if (!o.max_stream_pixels) o.max_stream_pixels = 1280 * 720;
     if (!o.scan_chain) o.scan_chain = kScanChainDefault;
     if (!o.apply_mode) o.apply_mode = ESI_APPLY_EVERY_TICK;
-    if (!o.host_pool_bytes) o.host_pool_bytes = 256ll << 20;
+    if (!o.host_pool_bytes) o.host_pool_bytes = 512ll << 20;
     if (!o.copy_threads) o.copy_threads = 4;
     if (!opts) o.use_graph = 1;
     if (o.frame_period_us < 1 || o.max_events_per_tick < kChunk || o.max_streams < 1 ||
@@ -770,8 +834,6 @@ void esi_server_destroy(esi_server *s)
     }
     if (s->prev_end) cudaEventDestroy(s->prev_end);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
-    for (Stream &st : s->streams)
-        if (st.slots_host) cudaFreeHost(st.slots_host);
     if (s->gexec) cudaGraphExecDestroy(s->gexec);
     for (int b = 0; b < 2; ++b) {
         if (s->stage[b]) cudaFreeHost(s->stage[b]);
@@ -807,6 +869,24 @@ int esi_stream_open(esi_server *s, int width, int height, const esi_params *para
     }
     const long long P = (long long)width * height;
     const size_t sbytes = align_up((size_t)P * 4, 256) + (size_t)P * 8;
+    const size_t rbytes = kRingInit * sizeof(esi_event);
+    const size_t fbytes = (size_t)s->opts.frame_slots * (size_t)P;
+    // memory of closed streams whose ticks are in flight comes back once
+    // they finish: wait for them before refusing
+    auto fits = [&] {
+        const size_t a = s->arena.alloc(sbytes);
+        if (a == SIZE_MAX) return false;
+        s->arena.release(a, sbytes);
+        const size_t r = s->harena.alloc(rbytes), f = s->harena.alloc(fbytes);
+        if (r != SIZE_MAX) s->harena.release(r, rbytes);
+        if (f != SIZE_MAX) s->harena.release(f, fbytes);
+        return r != SIZE_MAX && f != SIZE_MAX;
+    };
+    poll(s);
+    if (!fits() && (!s->zombies.empty() || !s->retired.empty())) {
+        rc = wait_all(s);
+        if (rc) return rc;
+    }
     const size_t off = s->arena.alloc(sbytes);
     if (off == SIZE_MAX) {
         s->n_refused += 1;
@@ -833,10 +913,12 @@ int esi_stream_open(esi_server *s, int width, int height, const esi_params *para
     st.next_frame_t = params->t_origin_us + s->opts.frame_period_us;
     st.slot_t.assign((size_t)s->opts.frame_slots, 0);
     st.slot_lat.assign((size_t)s->opts.frame_slots, 0.0);
-    const size_t rbytes = kRingInit * sizeof(esi_event);
+    // its event ring and frame slots come from the pinned host pool
     const size_t roff = s->harena.alloc(rbytes);
-    if (roff == SIZE_MAX) {  // no room for its events: refused like a full budget
+    const size_t foff = roff == SIZE_MAX ? SIZE_MAX : s->harena.alloc(fbytes);
+    if (foff == SIZE_MAX) {  // no room for its events or frames: refused like a full budget
         s->arena.release(off, sbytes);
+        if (roff != SIZE_MAX) s->harena.release(roff, rbytes);
         st = Stream();
         s->n_refused += 1;
         return ESI_EBUSY;
@@ -847,19 +929,20 @@ int esi_stream_open(esi_server *s, int width, int height, const esi_params *para
     st.ring_cap = kRingInit;
     st.ring_h = reinterpret_cast<esi_event *>(s->hpool + roff);
     st.ring_d = reinterpret_cast<const esi_event *>(s->hpool_d + roff);
-    cudaError_t e = cudaHostAlloc((void **)&st.slots_host, (size_t)s->opts.frame_slots * (size_t)P,
-                                  cudaHostAllocMapped);
-    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&st.slots_dev, st.slots_host, 0);
+    st.slots_off = foff;
+    st.slots_bytes = fbytes;
+    st.slots_host = s->hpool + foff;
+    st.slots_dev = s->hpool_d + foff;
+    std::memset(st.slots_host, 0, fbytes);
     // Alg. 2 initialisation: S = 0, T = t_origin
-    if (e == cudaSuccess) e = cudaMemsetAsync(st.S, 0, (size_t)P * 4, s->stream);
+    cudaError_t e = cudaMemsetAsync(st.S, 0, (size_t)P * 4, s->stream);
     if (e == cudaSuccess) e = launch_fill_i64(st.T, P, params->t_origin_us, s->stream);
     if (e != cudaSuccess) {
-        if (st.slots_host) cudaFreeHost(st.slots_host);
-        s->arena.release(off, sbytes);
-        s->harena.release(roff, rbytes);
+        free_stream_memory(s, st);
         st = Stream();
         return cuda_note(s, "stream open", e);
     }
+    st.gen = s->gen_next++;
     st.open = true;
     s->used += sbytes;
     s->n_open += 1;
@@ -1096,13 +1179,16 @@ int tick_impl(esi_server *s, long long now_us, int flush)
             win[n_frames + w].pad = 0;
             const unsigned long long seq = st.seq_issued + w;
             fout[n_frames + w] = st.slots_dev + (size_t)(seq % (unsigned long long)K) * (size_t)st.P;
-            rec->frames.push_back({id, seq, fr[w], st.last_push_ns});
+            rec->frames.push_back({id, st.gen, seq, fr[w], st.last_push_ns});
         }
         job_stream.push_back({j, id});
         st.seq_issued += fr.size();
         if (!fr.empty()) st.next_frame_t = fr.back() + s->opts.frame_period_us;
         st.head += take;
-        if (take) rec->used.push_back({id, st.head});
+        if (take) {
+            rec->used.push_back({id, st.gen, st.head});
+            shrink_ring(s, st);
+        }
         if (!fr.empty()) st.push_floor = std::max(st.push_floor, fr.back());
         n_ev += (long long)take;
         n_chunks += chunks;
@@ -1179,11 +1265,13 @@ int tick_impl(esi_server *s, long long now_us, int flush)
             e = launch_bin_batch_tab(s->dtab, s->bin_grid, kChunk, s->max_tiles, s->bin_mask, s->stream);
             for (int g = 0; g < kGroups && e == cudaSuccess; ++g)
                 if (groups & (1ull << g)) e = launch_group(s, g, s->stream);
-            if (e == cudaSuccess) e = cudaLaunchHostFunc(s->stream, on_tick_done, s->comp);
             s->launches_per_tick = 1 + ngroups;
         }
     }
+    // the kernels' end, then the completion stamp: when the stamp is in, the
+    // event is complete too
     if (e == cudaSuccess) e = cudaEventRecord(rec->ev1, s->stream);
+    if (e == cudaSuccess) e = cudaLaunchHostFunc(s->stream, on_tick_done, s->comp);
     if (e != cudaSuccess) return drop(cuda_note(s, "tick", e));
     s->ticks_issued += 1;
     rec->n_events = n_ev;
@@ -1297,13 +1385,17 @@ int esi_stream_state(esi_server *s, int id, float *S, int64_t *T)
 int esi_stream_close(esi_server *s, int id)
 {
     if (!s || id < 0 || id >= (int)s->streams.size() || !s->streams[id].open) return ESI_EINVAL;
-    int rc = wait_all(s);
-    if (rc) return rc;
+    poll(s);
     Stream &st = s->streams[id];
-    s->arena.release(st.arena_off, st.arena_bytes);
     s->used -= st.arena_bytes;
-    if (st.ring_h) s->harena.release(st.ring_off, st.ring_bytes);
-    if (st.slots_host) cudaFreeHost(st.slots_host);
+    st.open = false;
+    if (s->inflight.empty()) {
+        free_stream_memory(s, st);
+    } else {
+        // ticks in flight may still touch its state or deliver its frames:
+        // it lives on until they finish, and the id is free meanwhile
+        s->zombies.push_back({s->ticks_issued, std::move(st)});
+    }
     st = Stream();
     s->n_open -= 1;
     return ESI_OK;

@@ -201,10 +201,11 @@ def test_frame_only_mode_holds_events_back_until_a_frame_or_a_state_read():
 
 
 def test_event_rings_grow_and_refuse_pushes_beyond_the_host_pool():
-    # a stream's ring starts at 16384 events and doubles on demand inside the
-    # pinned host pool; a push that cannot fit is refused whole (ESI_ENOMEM,
-    # with the reason in esi_server_last_error) and the stream carries on with
-    # the events it had
+    # a stream's ring starts at 16384 events and grows on demand inside the
+    # pinned host pool (to a power of two with a quarter to spare); a push
+    # that cannot fit is refused whole
+    # (ESI_ENOMEM, with the reason in esi_server_last_error) and the stream
+    # carries on with the events it had
     esi = _esi()
     W, H = 200, 150
     opts = esi.esi_server_opts()
@@ -217,7 +218,7 @@ def test_event_rings_grow_and_refuse_pushes_beyond_the_host_pool():
         assert rc == 0
         ev = random_events(np.random.default_rng(11), W, H, 400_000, 0, 40_000)
         a, b = 100_000, 300_000
-        assert esi.esi_stream_push(srv, sid, ev[:a], a) == 0      # grows to 262144 events
+        assert esi.esi_stream_push(srv, sid, ev[:a], a) == 0      # grows to 131072 events
         assert esi.esi_stream_push(srv, sid, ev[a:b], b - a) == esi.ESI_ENOMEM
         assert "host pool full" in esi.esi_server_last_error(srv)
         t_a = int(ev["t"][a - 1])                                  # about 10 ms
@@ -239,7 +240,46 @@ def test_event_rings_grow_and_refuse_pushes_beyond_the_host_pool():
         rc, n_done = esi.esi_stream_frames_done(srv, sid)
         assert rc == 0 and n_done == int(ev["t"][-1]) // 10_000    # 10, 20, 30 ms
         rc, st = esi.esi_server_get_stats(srv)
-        assert st.ring_grows >= 1 and st.host_pool_peak_bytes >= (262144 * 16)
+        assert st.ring_grows >= 1 and st.host_pool_peak_bytes >= (131072 * 16)
+    finally:
+        esi.esi_server_destroy(srv)
+
+
+def test_a_ring_grown_for_a_burst_shrinks_once_applied():
+    esi = _esi()
+    W, H = 120, 90
+    opts = esi.esi_server_opts()
+    opts.host_pool_bytes = 64 << 20
+    rc, srv = esi.esi_server_create(64 << 20, opts, 0)
+    assert rc == 0
+    try:
+        pp = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1, t_origin_us=0)
+        rc, sid = esi.esi_stream_open(srv, W, H, esi.make_params(**pp))
+        assert rc == 0
+        ev = random_events(np.random.default_rng(21), W, H, 600_000, 0, 25_000)
+        burst = int(np.searchsorted(ev["t"], 5000, side="right"))   # 120 k events
+        assert esi.esi_stream_push(srv, sid, ev[:burst], burst) == 0
+        assert esi.esi_server_tick(srv, 5000) == 0
+        assert esi.esi_server_sync(srv) == 0
+        rc, st = esi.esi_server_get_stats(srv)
+        big = st.host_pool_peak_bytes
+        assert st.ring_grows == 1 and big >= 262144 * 16
+        lo = burst
+        for now in range(6000, 25_001, 1000):                        # 24 k events per ms
+            hi = int(np.searchsorted(ev["t"], now, side="right"))
+            assert esi.esi_stream_push(srv, sid, ev[lo:hi], hi - lo) == 0
+            assert esi.esi_server_tick(srv, now) == 0
+            lo = hi
+        assert esi.esi_server_sync(srv) == 0
+        rc, st = esi.esi_server_get_stats(srv)
+        assert st.host_pool_used_bytes < 262144 * 16                 # back to a small ring
+        S = np.empty(W * H, dtype=np.float32)
+        T = np.empty(W * H, dtype=np.int64)
+        assert esi.esi_stream_state(srv, sid, S, T) == 0
+        ref = oracle.OracleState(W, H, oracle_params(pp))
+        ref.integrate(ev[:lo])
+        assert np.array_equal(T, ref.T)
+        assert state_error(S, ref.S, pp["C"]) <= STATE_TOL
     finally:
         esi.esi_server_destroy(srv)
 

@@ -21,7 +21,7 @@ namespace {
 int ev_batch(const esi_handle *h, int max_chunks)
 {
     for (int b = std::min(h->tun.batch_records, 2048); b >= 1024; b /= 2)
-        if (tile_smem_bytes_ev(b, max_chunks) + tile_static_smem_bytes(h->tun.tile_h, h->tun.tile_w) <=
+        if (tile_smem_bytes_ev(h->tun.tile_h, b, max_chunks) + tile_static_smem_bytes(h->tun.tile_h, h->tun.tile_w) <=
             (size_t)kMaxSmemPerBlock)
             return b;
     return 0;

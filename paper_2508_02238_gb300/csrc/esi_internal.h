@@ -182,7 +182,7 @@ size_t bin_smem_bytes(int chunk, int n_tiles, bool mask);
 bool bin_mask_fits(int chunk, int n_tiles);
 size_t tile_smem_bytes(int tile_h, int batch, int n_chunks);
 // The same for the per-event-output instantiations (index arrays added).
-size_t tile_smem_bytes_ev(int batch, int n_chunks);
+size_t tile_smem_bytes_ev(int tile_h, int batch, int n_chunks);
 size_t tile_static_smem_bytes(int tile_h, int tile_w);
 cudaError_t launch_bin(const BinArgs &a, int n_chunks, cudaStream_t s);
 cudaError_t launch_tile(const TileArgs &a, int tile_h, int tile_w, bool vec, cudaStream_t s);

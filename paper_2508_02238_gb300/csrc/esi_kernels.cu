@@ -280,16 +280,15 @@ cudaError_t allow_dynamic_smem_impl(const void *kernel)
 
 size_t tile_smem_bytes(int tile_h, int batch, int n_chunks)
 {
-    (void)tile_h;
     size_t a, b, c, d;
-    return tile_layout(batch, n_chunks, &a, &b, &c, &d);
+    return tile_layout(batch, n_chunks, tile_h, &a, &b, &c, &d);
 }
 
 
-size_t tile_smem_bytes_ev(int batch, int n_chunks)
+size_t tile_smem_bytes_ev(int tile_h, int batch, int n_chunks)
 {
     size_t a, b;
-    return tile_layout_ev(batch, n_chunks, &a, &b);
+    return tile_layout_ev(batch, n_chunks, tile_h, &a, &b);
 }
 
 size_t tile_static_smem_bytes(int tile_h, int tile_w)

@@ -15,16 +15,16 @@ constexpr int kGatherLanes = ESI_GATHER_LANES;   // lanes copying one run of a b
 
 static __host__ __device__ inline int tile_round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-// Shared-memory layout of the tile kernel (dynamic part).
-static __host__ __device__ inline size_t tile_layout(int batch, int n_chunks, size_t *off_b,
+// Shared-memory layout of the tile kernel (dynamic part) for tiles of th
+// rows: the gathered batch A, its row-sorted copy B, the run table, and the
+// records' offsets within their warp's row runs, whose bytes hold the
+// segmented scan's 32 event maps (16 bytes each) per warp while the warps
+// walk B (A then receives the next batch).
+static __host__ __device__ inline size_t tile_layout(int batch, int n_chunks, int th, size_t *off_b,
                                                      size_t *off_runpre, size_t *off_runoff,
                                                      size_t *off_lpos)
 {
-    // batch + the next batch's first record; while the warps walk the
-    // sorted copy, the same bytes hold the segmented scan's 32 event maps
-    // (16 bytes each) per warp, up to 32 warps
-    size_t o = (size_t)(batch + 2) * 8;
-    if (o < (size_t)32 * 32 * 16) o = (size_t)32 * 32 * 16;
+    size_t o = (size_t)(batch + 2) * 8;   // batch + the next batch's first record
     *off_b = o;
     o += (size_t)batch * 8;
     *off_runpre = o;
@@ -32,16 +32,17 @@ static __host__ __device__ inline size_t tile_layout(int batch, int n_chunks, si
     *off_runoff = o;
     o += (size_t)tile_round_up(n_chunks, 4) * 4;
     *off_lpos = o;                   // record: offset inside its warp's row run
-    o += (size_t)tile_round_up(batch, 8) * 2;
+    const size_t lbytes = (size_t)tile_round_up(batch, 8) * 2, sbytes = (size_t)th * 32 * 16;
+    o += lbytes > sbytes ? lbytes : sbytes;
     return o;
 }
 
 // Per-event output: two u32 index arrays beside A and B, after the layout.
-static __host__ __device__ inline size_t tile_layout_ev(int batch, int n_chunks, size_t *off_ia,
+static __host__ __device__ inline size_t tile_layout_ev(int batch, int n_chunks, int th, size_t *off_ia,
                                                         size_t *off_ib)
 {
     size_t a, b, c, d;
-    size_t o = tile_round_up((int)tile_layout(batch, n_chunks, &a, &b, &c, &d), 16);
+    size_t o = tile_round_up((int)tile_layout(batch, n_chunks, th, &a, &b, &c, &d), 16);
     *off_ia = o;
     o += (size_t)(batch + 2) * 4;
     *off_ib = o;
@@ -288,7 +289,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
 
     const int R = a.batch, n_chunks = a.n_chunks;
     size_t off_b, off_runpre, off_runoff, off_lpos;
-    tile_layout(R, n_chunks, &off_b, &off_runpre, &off_runoff, &off_lpos);
+    tile_layout(R, n_chunks, TH, &off_b, &off_runpre, &off_runoff, &off_lpos);
     unsigned long long *A = reinterpret_cast<unsigned long long *>(smem);
     unsigned long long *B = reinterpret_cast<unsigned long long *>(smem + off_b);
     unsigned *runpre = reinterpret_cast<unsigned *>(smem + off_runpre);
@@ -297,7 +298,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
     unsigned *IA = nullptr, *IB = nullptr;
     if constexpr (EV) {
         size_t off_ia, off_ib;
-        tile_layout_ev(R, n_chunks, &off_ia, &off_ib);
+        tile_layout_ev(R, n_chunks, TH, &off_ia, &off_ib);
         IA = reinterpret_cast<unsigned *>(smem + off_ia);
         IB = reinterpret_cast<unsigned *>(smem + off_ib);
     }
@@ -334,6 +335,33 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
     // a tile with no record and no frame in this launch keeps its state as is
     if (total == 0 && a.w_end == a.w_begin) return;
 
+    // gather a batch (records b0 .. b0 + nb of this tile, arrival order,
+    // plus the next batch's first record) into A with asynchronous copies,
+    // so every record of the batch is in flight; the first batch's copies
+    // fly while the state loads, each later one while the rows walk the
+    // previous batch's sorted copy B
+    auto gather = [&](unsigned b0) {
+        const int nb = (int)min((unsigned)R, total - min(total, b0));
+        const unsigned next = b0 + (unsigned)R >= total ? 0u : 1u;
+        if (nb == 0) return;
+        const unsigned bend = b0 + (unsigned)nb + next;
+        const int cfirst = run_of(runpre, n_chunks, b0);
+        const int clast = run_of(runpre, n_chunks, bend - 1u);
+        // kGatherLanes lanes per run: a warp instruction copies several
+        // runs, each from contiguous addresses
+        const int grp = tid / kGatherLanes, sub = tid % kGatherLanes;
+        for (int c = cfirst + grp; c <= clast; c += NT / kGatherLanes) {
+            const unsigned rs = max(runpre[c], b0), re = min(runpre[c + 1], bend);
+            const unsigned long long *src = a.rec + (size_t)c * a.chunk + runoff[c] + (rs - runpre[c]);
+            for (unsigned i = sub; i + rs < re; i += kGatherLanes) cp_async8(&A[rs - b0 + i], src + i);
+            if constexpr (EV) {
+                const unsigned *isrc = a.rec_idx + (size_t)c * a.chunk + runoff[c] + (rs - runpre[c]);
+                for (unsigned i = sub; i + rs < re; i += kGatherLanes) cp_async4(&IA[rs - b0 + i], isrc + i);
+            }
+        }
+    };
+    gather(0u);
+
     {
         float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         long long o4[4] = {0, 0, 0, 0};
@@ -361,9 +389,9 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
 
 
     const RowState rs{rS, rF, rO, rP};
-    // the segmented scan's 32 slots per warp live in the gathered-batch
-    // buffer A, which nothing reads while the warps walk the sorted copy B
-    float4 *sScan = reinterpret_cast<float4 *>(A) + warp * 32;
+    // the segmented scan's 32 slots per warp (the offsets' bytes, free while
+    // the warps walk)
+    float4 *sScan = reinterpret_cast<float4 *>(smem + off_lpos) + warp * 32;
     auto apply = [&](unsigned long long r, bool valid, unsigned ev_idx) {
         const float s_out = apply_group<TWP, RD, DK>(rs, sScan, r, valid, dp, mp, a.scan_chain);
         if constexpr (EV) {
@@ -375,29 +403,6 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
     for (unsigned b0 = 0;; b0 += (unsigned)R) {
         const int nb = (int)min((unsigned)R, total - min(total, b0));
         const bool last = b0 + (unsigned)R >= total;
-
-        // gather the batch (records b0 .. b0 + nb of this tile, arrival
-        // order, plus the next batch's first record) with asynchronous
-        // copies, so every record of the batch is in flight
-        const unsigned next = last ? 0u : 1u;
-        if (nb > 0) {
-            const unsigned bend = b0 + (unsigned)nb + next;
-            const int cfirst = run_of(runpre, n_chunks, b0);
-            const int clast = run_of(runpre, n_chunks, bend - 1u);
-            // kGatherLanes lanes per run: a warp instruction copies several
-            // runs, each from contiguous addresses
-            const int grp = tid / kGatherLanes, sub = tid % kGatherLanes;
-            for (int c = cfirst + grp; c <= clast; c += NT / kGatherLanes) {
-                const unsigned rs = max(runpre[c], b0), re = min(runpre[c + 1], bend);
-                const unsigned long long *src =
-                    a.rec + (size_t)c * a.chunk + runoff[c] + (rs - runpre[c]);
-                for (unsigned i = sub; i + rs < re; i += kGatherLanes) cp_async8(&A[rs - b0 + i], src + i);
-                if constexpr (EV) {
-                    const unsigned *isrc = a.rec_idx + (size_t)c * a.chunk + runoff[c] + (rs - runpre[c]);
-                    for (unsigned i = sub; i + rs < re; i += kGatherLanes) cp_async4(&IA[rs - b0 + i], isrc + i);
-                }
-            }
-        }
         cp_async_wait_all();
         __syncthreads();
         if (tid == 0) s_tnext = last ? 0x7fffffffffffffffll : (long long)(unsigned)A[nb];
@@ -441,6 +446,8 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
             if constexpr (EV) IB[rcnt[warp][row] + lpos[k]] = IA[k];
         }
         __syncthreads();
+        // A (and the offsets) are free: the next batch's copies start now
+        if (!last) gather(b0 + (unsigned)R);
 
         // walk this warp's row, frame by frame
         int cur = (int)rowstart[warp];
@@ -477,7 +484,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
             apply(valid ? B[k] : 0ull, valid, EV && valid ? IB[k] : 0u);
         }
         if (last) break;
-        __syncthreads();  // A, B, rcnt are rewritten by the next batch
+        __syncthreads();  // B, rcnt and the scan slots are rewritten by the next batch
     }
 
     __syncwarp();

@@ -208,7 +208,7 @@ __device__ __forceinline__ void tile_body_split(const TileArgs &a, int tile)
 
     const int R = a.batch, n_chunks = a.n_chunks;
     size_t off_b, off_runpre, off_runoff, off_lpos;
-    tile_layout(R, n_chunks, &off_b, &off_runpre, &off_runoff, &off_lpos);
+    tile_layout(R, n_chunks, TH, &off_b, &off_runpre, &off_runoff, &off_lpos);
     unsigned long long *A = reinterpret_cast<unsigned long long *>(smem);
     unsigned long long *B = reinterpret_cast<unsigned long long *>(smem + off_b);
     unsigned *runpre = reinterpret_cast<unsigned *>(smem + off_runpre);

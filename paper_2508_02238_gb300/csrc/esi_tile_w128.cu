@@ -63,7 +63,7 @@ cudaError_t launch_tile_tab_w128(const unsigned char *tab, int group, int grid, 
 
 cudaError_t launch_tile_ev_w128(const TileArgs &a, int tile_h, cudaStream_t s)
 {
-    const size_t smem = tile_smem_bytes_ev(a.batch, a.n_chunks);
+    const size_t smem = tile_smem_bytes_ev(tile_h, a.batch, a.n_chunks);
     const int dk = decay_kind_of(a.dp);
 #define Y(TH, DK)                                                                       \
     if (tile_h == TH && dk == DK) {                                                     \

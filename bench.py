@@ -528,6 +528,9 @@ def other_workloads_leg(esi, torch, K=6):
 
 SERVING_SECONDS = 5.0
 SERVING_APPLY = 0   # esi_server_opts.apply_mode of the serving legs (0: the server's default)
+# tile rows of the mixed workload's streams by scene form (2: 1280x720
+# checkerboard, 1: 640x480 blobs, 0: 346x260 sinusoid)
+MIXED_TILE_H = {2: 16, 1: 8, 0: 8}
 MIXED_SECONDS = 5.0
 SERVING_PARAMS = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1)
 
@@ -674,7 +677,7 @@ def mixed_workload(esi, seconds, sinks=False, scene_s=None):
     t_end = int(round(seconds * 1e6))
     evs = [synth.stream_events(w) for w in ws]
     specs, parts, sink = [], [], []
-    tile_h = {2: 16, 1: 8, 0: 8}
+    tile_h = MIXED_TILE_H
     for k, (w, arr) in enumerate(zip(ws, arrs)):
         sp = esi.esi_stream_spec()
         sp.width, sp.height = w["W"], w["H"]
@@ -716,7 +719,8 @@ def mixed_serving_leg(esi, seconds=SERVING_SECONDS):
                        f"late, {sum(w['t_leave_us'] is not None for w in ws)} leave, Poisson packets "
                        f"1 ms, 100 frames/s, {seconds} s",
            "events": n_ev, "state_budget_bytes": budget,
-           "tile_h": "16 rows for 1280x720, 8 for the others"}
+           "tile_h": {"1280x720": MIXED_TILE_H[2], "640x480": MIXED_TILE_H[1],
+                      "346x260": MIXED_TILE_H[0]}}
     for mode in ("batched", "batched_throughput"):
         for sp in specs:
             sp.stream_id = -1

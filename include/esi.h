@@ -365,6 +365,14 @@ typedef struct {
     int32_t copy_threads;         /* host threads that copy a large push into its
                                    * ring, the caller's included: 0 = default (4),
                                    * 1 .. 16                                   */
+    int32_t fuse_tick;            /* 0 = default (1); 1: a tick whose streams all
+                                   * use 8-row tiles, have at most 256 tiles of
+                                   * 128 x 8 pixels each (about 260 k pixels) and
+                                   * share render mode and decay kind runs as one
+                                   * persistent launch (binning and tiles); 2:
+                                   * always one binning launch and one tile
+                                   * launch per variant                          */
+    int32_t _reserved;
     int64_t host_pool_bytes;      /* pinned, mapped host memory holding the
                                    * streams' pending events (a ring per stream,
                                    * grown on demand) and frame slots

@@ -153,11 +153,14 @@ constexpr int kTickGroups = 36;
 struct TickDir {
     int n_chunks;
     int n_items[kTickGroups];
-    int pad[3];
+    int fused_n_items;            // work items of the fused tick launch
+    int pad[2];
     long long off_binjob;
     long long off_chunkjob;
     long long off_tilejob;
     long long off_items[kTickGroups];
+    long long fused_off_items;    // its items (a run of the groups' item lists)
+    long long off_sync;           // u32 [0]: work counter; [1 + job]: the job's chunks binned
 };
 
 // Record layout (8 bytes): low 32 bits t - t_base; high 32 bits
@@ -206,6 +209,14 @@ cudaError_t set_tile_attributes_w32();
 cudaError_t set_tile_attributes_w64();
 cudaError_t launch_bin_batch_tab(const unsigned char *tab, int grid, int chunk, int max_tiles,
                                  bool mask, cudaStream_t s);
+// One launch for a whole serving tick whose streams all use 8-row tiles and
+// share render mode rd and decay kind dk: a persistent grid takes the tick's
+// binning chunks, then its tile items, from one counter; a tile item waits
+// (bounded) until its stream's chunks are binned.
+cudaError_t launch_tick_fused(const unsigned char *tab, int grid, int rd, int dk, size_t smem,
+                              cudaStream_t s);
+size_t tick_fused_smem_bytes(int chunk, int max_tiles, bool mask, int batch, int max_chunks);
+int tick_fused_blocks_per_sm(int rd, int dk, size_t smem);
 // Resident blocks per SM of the batched binning kernel (its persistent grid).
 int bin_tab_blocks_per_sm(int chunk, int max_tiles, bool mask);
 cudaError_t launch_tile_batch_tab(const unsigned char *tab, int group, int grid, int tile_h, int rd,

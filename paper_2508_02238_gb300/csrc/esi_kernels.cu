@@ -30,6 +30,7 @@ namespace esi {
 constexpr int kBinThreads = 256;
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
 constexpr int kWhereBinCopy = 1;
+constexpr int kWhereTickWait = 2;
 
 static __host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
@@ -267,6 +268,105 @@ __global__ void __launch_bounds__(kBinThreads) esi_bin_tab_kernel(const unsigned
     }
 }
 
+// Until the counter reaches need (bounded by limit_ns): the acquire load
+// orders the reads that follow after the writes released before each add.
+__device__ __forceinline__ bool wait_count(const unsigned *p, unsigned need, unsigned long long limit_ns)
+{
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+        if (v >= need) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+        __nanosleep(128);
+    }
+}
+
+// A whole serving tick in one launch (streams with 8-row tiles, one render
+// mode and decay kind; the row alignment is read per stream).  The blocks
+// take the tick's binning chunks from a counter in the tick table until none
+// is left, then walk the tile items grid-stride; a block reaches the items
+// only after every chunk has been taken by a running block, so its wait for
+// a stream's chunks always ends.
+template <int RD, int DK>
+__global__ void __launch_bounds__(kBinThreads) esi_tick_fused_kernel(const unsigned char *tab)
+{
+    static_assert(kBinThreads == 8 * 32, "one warp per row of an 8-row tile");
+    const TickDir *d = reinterpret_cast<const TickDir *>(tab);
+    const BinJob *bjobs = reinterpret_cast<const BinJob *>(tab + d->off_binjob);
+    const int *cj = reinterpret_cast<const int *>(tab + d->off_chunkjob);
+    const TileArgs *tjobs = reinterpret_cast<const TileArgs *>(tab + d->off_tilejob);
+    const int2 *items = reinterpret_cast<const int2 *>(tab + d->fused_off_items);
+    unsigned *sync = reinterpret_cast<unsigned *>(const_cast<unsigned char *>(tab) + d->off_sync);
+    const int n_chunks = d->n_chunks, n_items = d->fused_n_items;
+    __shared__ int s_w, s_ok;
+    for (;;) {
+        if (threadIdx.x == 0) s_w = (int)atomicAdd(&sync[0], 1u);
+        __syncthreads();
+        const int w = s_w;
+        if (w >= n_chunks) break;
+        const int j = cj[w];
+        bin_chunk<false, true>(bjobs[j].args, w - bjobs[j].first_chunk);
+        __syncthreads();  // every record and run entry of the chunk is written; s_w is read
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&sync[1 + j], 1u);
+        }
+    }
+    for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
+        const int2 it = items[i];
+        if (threadIdx.x == 0) {
+            const BinArgs &ba = bjobs[it.x].args;
+            const unsigned need = (unsigned)((ba.n + ba.chunk - 1) / ba.chunk);
+            s_ok = wait_count(&sync[1 + it.x], need, kWaitLimitNs) ? 1 : 0;
+            if (!s_ok) set_error(ba.status, ESI_ETIMEOUT, kWhereTickWait);
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_ok) tile_body<8, 4, RD, DK, false, false, true>(tjobs[it.x], it.y);
+        __syncthreads();  // shared memory serves the next item; s_ok is rewritten
+    }
+}
+
+size_t tick_fused_smem_bytes(int chunk, int max_tiles, bool mask, int batch, int max_chunks)
+{
+    const size_t b = bin_smem_bytes(chunk, max_tiles, mask);
+    const size_t t = tile_smem_bytes(8, batch, max_chunks);
+    return b > t ? b : t;
+}
+
+#define ESI_TICK_FUSED_VARIANTS X(0, kDecayGeneral) X(0, kDecaySquare) X(0, kDecayNone) \
+    X(1, kDecayGeneral) X(1, kDecaySquare) X(1, kDecayNone)
+
+int tick_fused_blocks_per_sm(int rd, int dk, size_t smem)
+{
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define X(RD, DK) \
+    if (rd == RD && dk == DK) \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, esi_tick_fused_kernel<RD, DK>, kBinThreads, smem);
+    ESI_TICK_FUSED_VARIANTS
+#undef X
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_tick_fused(const unsigned char *tab, int grid, int rd, int dk, size_t smem,
+                              cudaStream_t s)
+{
+#define X(RD, DK)                                                                        \
+    if (rd == RD && dk == DK) {                                                          \
+        esi_tick_fused_kernel<RD, DK><<<grid, kBinThreads, smem, s>>>(tab);              \
+        return cudaGetLastError();                                                       \
+    }
+    ESI_TICK_FUSED_VARIANTS
+#undef X
+    return cudaErrorInvalidValue;
+}
+
 // Dynamic shared memory a kernel may ask for: the 227 KB per block minus its
 // static part.
 cudaError_t allow_dynamic_smem_impl(const void *kernel)
@@ -311,6 +411,10 @@ cudaError_t set_kernel_attributes()
     cudaError_t e = allow_dynamic_smem_impl((const void *)esi_bin_kernel);
     if (e == cudaSuccess) e = allow_dynamic_smem_impl((const void *)esi_bin_ev_kernel);
     if (e == cudaSuccess) e = allow_dynamic_smem_impl((const void *)esi_bin_tab_kernel);
+#define X(RD, DK) \
+    if (e == cudaSuccess) e = allow_dynamic_smem_impl((const void *)esi_tick_fused_kernel<RD, DK>);
+    ESI_TICK_FUSED_VARIANTS
+#undef X
     if (e == cudaSuccess) e = set_tile_attributes_w128();
     if (e == cudaSuccess) e = set_tile_attributes_w32();
     if (e == cudaSuccess) e = set_tile_attributes_w64();

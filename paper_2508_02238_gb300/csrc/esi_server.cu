@@ -192,6 +192,7 @@ constexpr int kBatch = 2048;
 constexpr int kMaxChunksPerStream = 64;
 constexpr long long kDeferCap = 65536;  // AT_FRAMES: pending events applied without a frame
 constexpr unsigned long long kRingInit = 16384;  // events of a new stream's ring
+constexpr int kFusedMaxTiles = 256;  // the fused tick launch serves streams of at most this many tiles
 constexpr int kTickSlots = 64;  // completion stamps kept for ticks in flight
 constexpr int kMaxSlots = 1 << 20;  // caller stream slots of one esi_server_run
 
@@ -338,6 +339,10 @@ struct esi_server {
 
     cudaGraphExec_t gexec = nullptr;
     unsigned long long graph_groups = 0;  // bit g set: the graph launches group g
+    int graph_fused = -1;                 // the graph is the fused launch of variant rd * 3 + dk
+    int fused_grid[6] = {0, 0, 0, 0, 0, 0};  // persistent grid per fused variant (0: not yet sized)
+    size_t fused_smem = 0;                // its shared memory (0: not yet sized)
+    size_t off_sync = 0;
     Completion *comp = nullptr;
     unsigned long long ticks_issued = 0;
     std::vector<TickRec *> inflight;
@@ -612,15 +617,29 @@ cudaError_t launch_group(esi_server *s, int g, cudaStream_t cs)
                                  group_dk(g), group_vec(g), kBatch, kMaxChunksPerStream, cs);
 }
 
-// Capture the per-tick graph for the variant groups in `groups`: binning,
-// then the groups' tile launches as parallel branches (they touch disjoint
-// streams), joined at the end.
-int build_graph(esi_server *s, unsigned long long groups)
+// The fused tick launch of variant fv = rd * 3 + dk (grid sized once).
+cudaError_t launch_fused(esi_server *s, int fv, cudaStream_t cs)
+{
+    if (!s->fused_grid[fv]) {
+        int sms = 0;
+        cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+        if (e != cudaSuccess) return e;
+        s->fused_grid[fv] = std::max(1, sms) * tick_fused_blocks_per_sm(fv / 3, fv % 3, s->fused_smem);
+    }
+    return launch_tick_fused(s->dtab, s->fused_grid[fv], fv / 3, fv % 3, s->fused_smem, cs);
+}
+
+// Capture the per-tick graph: the fused launch of variant fused (>= 0), or
+// for the variant groups in `groups` binning, then the groups' tile
+// launches as parallel branches (they touch disjoint streams), joined at the
+// end.
+int build_graph(esi_server *s, unsigned long long groups, int fused)
 {
     if (s->gexec) {
         cudaGraphExecDestroy(s->gexec);
         s->gexec = nullptr;
     }
+    if (fused >= 0) groups = 0;
     std::vector<int> gl;
     for (int gi = 0; gi < kGroups; ++gi)
         if (groups & (1ull << gi)) gl.push_back(gi);
@@ -638,7 +657,8 @@ int build_graph(esi_server *s, unsigned long long groups)
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         capturing = e == cudaSuccess;
     }
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && fused >= 0) e = launch_fused(s, fused, cs);
+    if (e == cudaSuccess && fused < 0)
         e = launch_bin_batch_tab(s->dtab, s->bin_grid, kChunk, s->max_tiles, s->bin_mask, cs);
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], cs);  // fork after binning
     for (size_t i = 1; i < gl.size() && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(br[i], ev[0], 0);
@@ -662,6 +682,7 @@ int build_graph(esi_server *s, unsigned long long groups)
         return cuda_note(s, "tick graph", e);
     }
     s->graph_groups = groups;
+    s->graph_fused = fused;
     return ESI_OK;
 }
 
@@ -707,13 +728,15 @@ int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts, vo
     if (!o.apply_mode) o.apply_mode = ESI_APPLY_EVERY_TICK;
     if (!o.host_pool_bytes) o.host_pool_bytes = 512ll << 20;
     if (!o.copy_threads) o.copy_threads = 4;
+    if (!o.fuse_tick) o.fuse_tick = 1;
     if (!opts) o.use_graph = 1;
     if (o.frame_period_us < 1 || o.max_events_per_tick < kChunk || o.max_streams < 1 ||
         o.max_streams > 4096 || o.frame_slots < 2 || o.frame_slots > 64 ||
         (o.tile_h != 4 && o.tile_h != 8 && o.tile_h != 16) ||
         o.max_stream_pixels < 1 || o.scan_chain < 1 || o.scan_chain > kScanNever ||
         (o.apply_mode != ESI_APPLY_EVERY_TICK && o.apply_mode != ESI_APPLY_AT_FRAMES) ||
-        o.copy_threads < 1 || o.copy_threads > 16 ||
+        o.copy_threads < 1 || o.copy_threads > 16 || o.fuse_tick < 1 || o.fuse_tick > 2 ||
+        o._reserved != 0 ||
         o.host_pool_bytes < (long long)(kRingInit * sizeof(esi_event)) ||
         state_budget_bytes == 0)
         return ESI_EINVAL;
@@ -758,10 +781,13 @@ int esi_server_create(size_t state_budget_bytes, const esi_server_opts *opts, vo
     off = align_up(off + sizeof(WinInfo) * (size_t)s->cap_frames, 256);
     s->off_fout = off;
     off = align_up(off + sizeof(void *) * (size_t)s->cap_frames, 256);
+    s->off_sync = off;
+    off = align_up(off + sizeof(unsigned) * (size_t)(s->cap_jobs + 1), 256);
     s->off_items = off;
     off = align_up(off + sizeof(int2) * (size_t)s->cap_items, 256);
     s->tab_bytes = off;
-    s->hrow_cap = (size_t)s->cap_chunks * (size_t)s->max_tiles;
+    // each stream's run table starts on a 128-byte line of its own
+    s->hrow_cap = (size_t)s->cap_chunks * (size_t)s->max_tiles + (size_t)s->cap_jobs * 32;
     s->bin_mask = bin_mask_fits(kChunk, s->max_tiles);
 
     cudaError_t e = cudaGetDevice(&s->device);
@@ -1193,7 +1219,7 @@ int tick_impl(esi_server *s, long long now_us, int flush)
         n_ev += (long long)take;
         n_chunks += chunks;
         n_frames += (int)fr.size();
-        hrow_off += (size_t)chunks * st.n_tiles;
+        hrow_off = (hrow_off + (size_t)chunks * st.n_tiles + 31) & ~(size_t)31;
         dir->n_items[st.group] += st.n_tiles;
         n_items_total += st.n_tiles;
     }
@@ -1226,6 +1252,32 @@ int tick_impl(esi_server *s, long long now_us, int flush)
     dir->off_binjob = (long long)s->off_binjob;
     dir->off_chunkjob = (long long)s->off_chunkjob;
     dir->off_tilejob = (long long)s->off_tilejob;
+    // one fused launch when every group of the tick has 8-row tiles and the
+    // same render mode and decay kind (the two row alignments of one
+    // variant are adjacent groups, so their items form one run), and no
+    // stream has more than kFusedMaxTiles tiles: the binning's per-tile
+    // counters then leave the fused blocks as many per SM as the separate
+    // launches get (with 900-tile streams the fused launch was measured
+    // slower than binning plus tile launches)
+    int fused = -1;
+    if (s->opts.fuse_tick == 1 && groups) {
+        const int g0 = __builtin_ctzll(groups) & ~1;
+        int maxt = 0;
+        for (auto &js : job_stream) maxt = std::max(maxt, s->streams[js.second].n_tiles);
+        if (group_tile_h(g0) == 8 && (groups & ~(3ull << g0)) == 0 && maxt <= kFusedMaxTiles) {
+            fused = group_rd(g0) * 3 + group_dk(g0);
+            const int gf = (groups >> g0) & 1ull ? g0 : g0 + 1;
+            dir->fused_off_items = dir->off_items[gf];
+            dir->fused_n_items = dir->n_items[g0] + dir->n_items[g0 + 1];
+            if (!s->fused_smem) {
+                s->fused_smem = tick_fused_smem_bytes(kChunk, std::min(kFusedMaxTiles, s->max_tiles),
+                                                      s->bin_mask, kBatch, kMaxChunksPerStream);
+                s->graph_fused = -1;
+            }
+        }
+    }
+    dir->off_sync = (long long)s->off_sync;
+    std::memset(stg + s->off_sync, 0, sizeof(unsigned) * (size_t)(n_jobs + 1));
 
     // a tick that fails to queue returns its events to the pool
     auto drop = [&](int rc) {
@@ -1253,14 +1305,20 @@ int tick_impl(esi_server *s, long long now_us, int flush)
     for (int g = 0; g < kGroups; ++g) ngroups += (int)((groups >> g) & 1ull);
     if (e == cudaSuccess) {
         if (s->opts.use_graph) {
-            if (!s->gexec || (groups & ~s->graph_groups)) {
-                int rc = build_graph(s, groups | s->graph_groups);
+            const bool stale = fused >= 0 ? s->graph_fused != fused
+                                          : s->graph_fused >= 0 || (groups & ~s->graph_groups);
+            if (!s->gexec || stale) {
+                int rc = build_graph(s, fused >= 0 ? 0ull : groups | (s->graph_fused >= 0 ? 0ull : s->graph_groups),
+                                     fused);
                 if (rc) return drop(rc);
             }
             e = cudaGraphLaunch(s->gexec, s->stream);
             int ng = 0;
             for (int g = 0; g < kGroups; ++g) ng += (int)((s->graph_groups >> g) & 1ull);
-            s->launches_per_tick = 1 + ng;
+            s->launches_per_tick = fused >= 0 ? 1 : 1 + ng;
+        } else if (fused >= 0) {
+            e = launch_fused(s, fused, s->stream);
+            s->launches_per_tick = 1;
         } else {
             e = launch_bin_batch_tab(s->dtab, s->bin_grid, kChunk, s->max_tiles, s->bin_mask, s->stream);
             for (int g = 0; g < kGroups && e == cudaSuccess; ++g)

@@ -203,10 +203,10 @@ __device__ __forceinline__ float apply_group(const RowState &rs, float4 *sc, uns
 
 // Eq. 14 codes of the lane's PPL pixels at a frame (the decay view to the
 // frame time when RD): one 32-bit word (PPL = 4), one 16-bit word (PPL = 2)
-// when VEC, else byte by byte.  fr: the frame at the lane's first pixel.
-template <int PPL, int RD, int DK, bool VEC>
+// when vec, else byte by byte.  fr: the frame at the lane's first pixel.
+template <int PPL, int RD, int DK>
 __device__ __forceinline__ void emit_codes(const RowState &rs, unsigned char *fr, int nval, float tf_f,
-                                           const DecayParams &dp, const MapParams &mp)
+                                           const DecayParams &dp, const MapParams &mp, bool vec)
 {
     const int lane = threadIdx.x & 31;
     if constexpr (PPL == 4) {
@@ -222,7 +222,7 @@ __device__ __forceinline__ void emit_codes(const RowState &rs, unsigned char *fr
         unsigned code[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) code[q] = quantize_u8(fmaf(v[q], mp.scale, mp.offs));
-        if (VEC) {
+        if (vec) {
             if (nval == 4)
                 *reinterpret_cast<unsigned *>(fr) =
                     code[0] | (code[1] << 8) | (code[2] << 16) | (code[3] << 24);
@@ -241,7 +241,7 @@ __device__ __forceinline__ void emit_codes(const RowState &rs, unsigned char *fr
         }
         const unsigned c0 = quantize_u8(fmaf(v0, mp.scale, mp.offs));
         const unsigned c1 = quantize_u8(fmaf(v1, mp.scale, mp.offs));
-        if (VEC) {
+        if (vec) {
             if (nval == 2) *reinterpret_cast<unsigned short *>(fr) = (unsigned short)(c0 | (c1 << 8));
         } else {
             if (nval > 0) fr[0] = (unsigned char)c0;
@@ -267,8 +267,9 @@ __device__ __forceinline__ void emit_codes(const RowState &rs, unsigned char *fr
 // pixels move as one float4 / two longlong2 / one 32-bit frame word (PPL = 4)
 // or one 16-bit frame word (PPL = 2).  EV: every record's event index is
 // carried beside it and S after each event is stored at that index
-// (esi_event_states; launched with no frames).
-template <int TH, int PPL, int RD, int DK, bool VEC, bool EV = false>
+// (esi_event_states; launched with no frames).  VECRT: the row alignment is
+// read from a.W at run time instead of VEC (one instance serves both).
+template <int TH, int PPL, int RD, int DK, bool VEC, bool EV = false, bool VECRT = false>
 __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
 {
     constexpr int NT = TH * 32;
@@ -304,6 +305,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
     }
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool vec = VECRT ? (a.W % PPL == 0) : VEC;
     const int x0 = (tile % a.tiles_x) * TWP + PPL * lane;
     const int y = (tile / a.tiles_x) * TH + warp;
     const int nval = (y < a.H) ? max(0, min(PPL, a.W - x0)) : 0;
@@ -365,7 +367,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
     {
         float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         long long o4[4] = {0, 0, 0, 0};
-        if (PPL == 4 && VEC && nval == 4) {
+        if (PPL == 4 && vec && nval == 4) {
             const float4 v = *reinterpret_cast<const float4 *>(a.S + pix0);
             const longlong2 t01 = *reinterpret_cast<const longlong2 *>(a.T + pix0);
             const longlong2 t23 = *reinterpret_cast<const longlong2 *>(a.T + pix0 + 2);
@@ -474,7 +476,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
             // Eq. 14 codes of the lane's pixels at this frame
             unsigned char *fr =
                 (a.frame_outs ? a.frame_outs[wi] : a.frames + (long long)wi * a.P) + pix0;
-            emit_codes<PPL, RD, DK, VEC>(rs, fr, nval, wv.tf_f, dp, mp);
+            emit_codes<PPL, RD, DK>(rs, fr, nval, wv.tf_f, dp, mp, vec);
             ++wi;
         }
         // the rest of this batch's row precedes the next batch's records
@@ -488,7 +490,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int tile)
     }
 
     __syncwarp();
-    if (PPL == 4 && VEC && nval == 4) {
+    if (PPL == 4 && vec && nval == 4) {
         const float4 s4 = *reinterpret_cast<const float4 *>(rS + 4 * lane);
         *reinterpret_cast<float4 *>(a.S + pix0) = s4;
         *reinterpret_cast<longlong2 *>(a.T + pix0) =

@@ -602,7 +602,7 @@ __device__ __forceinline__ void tile_body_split(const TileArgs &a, int tile)
                     if (nv < 32) break;
                 }
                 unsigned char *fr = (a.frame_outs ? a.frame_outs[f] : a.frames + (long long)f * a.P) + pix0;
-                emit_codes<PPL, RD, DK, VEC>(rs, fr, nval, tf_of(f), dp, mp);
+                emit_codes<PPL, RD, DK>(rs, fr, nval, tf_of(f), dp, mp, VEC);
             }
             for (; cur < end; cur += 32) {
                 ring_need(cur, cur + 32u);

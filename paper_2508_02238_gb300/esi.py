@@ -59,6 +59,7 @@ class esi_server_opts(ctypes.Structure):
                 ("use_graph", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("max_stream_pixels", ctypes.c_int32), ("scan_chain", ctypes.c_int32),
                 ("apply_mode", ctypes.c_int32), ("copy_threads", ctypes.c_int32),
+                ("fuse_tick", ctypes.c_int32), ("_reserved", ctypes.c_int32),
                 ("host_pool_bytes", ctypes.c_int64)]
 
 

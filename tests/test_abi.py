@@ -93,6 +93,7 @@ def test_method_constants_match_the_header():
 def test_server_options_are_checked_before_touching_cuda():
     for field, bad in (("apply_mode", 3), ("apply_mode", -1), ("copy_threads", 17),
                        ("copy_threads", -1), ("host_pool_bytes", 4096), ("scan_chain", 34),
+                       ("fuse_tick", 3), ("fuse_tick", -1), ("_reserved", 1),
                        ("frame_slots", 1), ("tile_h", 5)):
         opts = esi.esi_server_opts()
         setattr(opts, field, bad)

@@ -84,15 +84,17 @@ def drive(esi, srv, ids, events, dims, t_end, tick_us=1000, start=0, on_tick=Non
 
 
 def serve(stream_specs, t_end, use_graph=1, budget=256 << 20, tile_hs=None, retile=None,
-          scan_chain=0, apply_mode=0):
+          scan_chain=0, apply_mode=0, fuse_tick=0):
     """tile_hs: {spec index: tile height} set at open; retile: (time, {index: tile height})
     applied before that tick; scan_chain: the server's segmented-scan knob (33: off);
-    apply_mode: when the server applies a stream's events (0: default)."""
+    apply_mode: when the server applies a stream's events (0: default); fuse_tick: one
+    launch per tick where the streams allow it (0, 1) or always separate launches (2)."""
     esi = _esi()
     opts = esi.esi_server_opts()
     opts.use_graph = use_graph
     opts.scan_chain = scan_chain
     opts.apply_mode = apply_mode
+    opts.fuse_tick = fuse_tick
     opts.host_pool_bytes = 64 << 20
     rc, srv = esi.esi_server_create(budget, opts, 0)
     assert rc == 0
@@ -323,7 +325,7 @@ def test_apply_mode_validation():
     for mode, threads, ok in ((0, 0, True), (1, 1, True), (2, 16, True), (3, 0, False),
                               (-1, 0, False), (0, 17, False)):
         opts = esi.esi_server_opts()
-        opts.apply_mode, opts.copy_threads = mode, threads
+        opts.apply_mode, opts.copy_threads, opts.fuse_tick = mode, threads, mode % 3
         rc, srv = esi.esi_server_create(1 << 20, opts, 0)
         assert (rc == 0) == ok, (mode, threads, rc)
         if rc == 0:
@@ -361,6 +363,37 @@ def test_served_stream_equals_single_sensor_handle():
         Sh, Th = g.state()
     assert np.array_equal(np.stack([frames[t] for t in tf]), fr)
     assert np.array_equal(S, Sh) and np.array_equal(T, Th)
+
+
+def test_fused_tick_launch_equals_separate_launches():
+    # streams that all use 8-row tiles and share render mode and decay kind
+    # (row widths with and without 4-pixel alignment): one persistent launch
+    # per tick gives exactly what the binning launch plus per-variant tile
+    # launches give, graph or not
+    specs = [(1, STREAMS[1]), (2, (200, 150, dict(STREAMS[1][2]), "random")),
+             (0, (64, 48, dict(STREAMS[1][2]), "random")), (5, (131, 77, dict(STREAMS[1][2]), "random"))]
+    t_end = 70_000
+    sep, st_s = serve(specs, t_end, fuse_tick=2)
+    fus, st_f = serve(specs, t_end, fuse_tick=1)
+    fus_direct, st_d = serve(specs, t_end, fuse_tick=1, use_graph=0)
+    assert st_f.kernel_launches_per_tick == 1 and st_d.kernel_launches_per_tick == 1
+    assert st_s.kernel_launches_per_tick >= 3
+    for i, _ in specs:
+        for other in (fus, fus_direct):
+            assert sorted(sep[i][0]) == sorted(other[i][0])
+            for t in sep[i][0]:
+                assert np.array_equal(sep[i][0][t], other[i][0][t]), (i, t)
+            assert np.array_equal(sep[i][1][0], other[i][1][0]) and np.array_equal(sep[i][1][1], other[i][1][1])
+
+
+def test_fused_tick_is_skipped_when_streams_differ_in_tile_height():
+    specs = list(enumerate(STREAMS[:2]))
+    res, st = serve(specs, 40_000, tile_hs={0: 4})
+    assert st.kernel_launches_per_tick >= 3
+    ref, _ = serve(specs, 40_000, fuse_tick=2, tile_hs={0: 4})
+    for i, _ in specs:
+        for t in ref[i][0]:
+            assert np.array_equal(ref[i][0][t], res[i][0][t])
 
 
 def test_graph_and_direct_launches_agree():

@@ -68,7 +68,9 @@ HEADLINE = "c2"
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of a full launch of the headline's shape (--ncu-case: its
 # second sub-batch, 4.19 M events and 8 frames), keyed by kernel.
-NCU_TRAFFIC_PER_LAUNCH = {"esi_tile": 48845312, "esi_bin": 70952448}
+NCU_TRAFFIC_PER_LAUNCH = {"esi_tile": 48737792, "esi_bin": 70952448}
+# Warp instructions per launch (smsp__inst_executed.sum) from the same capture.
+NCU_INST_PER_LAUNCH = {"esi_tile": 54074602}
 
 
 def parse_args():
@@ -231,6 +233,28 @@ def tile_roofline(prof, P, frames_per_step, steps, n_ev, peak, peak_kind, traffi
             "bytes_per_launch": bytes_per_launch}
 
 
+def issue_roofline(roof, clocks, name=DOMINANT):
+    """The dominant kernel against the SMs' instruction issue rate (4 warp
+    instructions per cycle per SM at the SM clock sampled during the timed
+    region): its warp instructions per launch (ncu) over its average launch
+    time.  The tile kernel is bound here, not by HBM."""
+    inst = NCU_INST_PER_LAUNCH.get(name)
+    if not roof or not inst:
+        return None
+    import torch
+    try:
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+    except Exception:
+        return None
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * 4 * mhz * 1e6 / 1e9
+    achieved = inst / (roof["avg_launch_us"] * 1e-6) / 1e9
+    return {"bound": "issue", "kernel": name, "achieved": achieved, "peak": peak,
+            "unit": "G warp-instructions/s", "frac": achieved / peak,
+            "inst_per_launch": inst, "sm_mhz": mhz, "sms": sms,
+            "peak_kind": "4 warp instructions per cycle per SM at the sampled SM clock"}
+
+
 def kernel_shares(prof):
     tot = max(1e-9, sum(x[1] for x in prof.values()))
     return {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / tot} for k, v in prof.items()}
@@ -363,6 +387,7 @@ def bench_esi(args):
                    "parallelism": f"replicas x{ws}"},
         "frames_per_s": frames_per_s,
         "roofline": roof,
+        "roofline_issue": issue_roofline(roof, r["clocks"]),
         "roofline_binning": tile_roofline(r["prof"], P, M, args.steps, n_ev, peak, peak_kind,
                                           traffic=NCU_TRAFFIC_PER_LAUNCH.get("esi_bin"),
                                           name="esi_bin"),
@@ -423,7 +448,9 @@ def e2e_leg(esi, torch, r, steps):
     overlaps this step's render; one esi_synchronize ends the timed region.
     Synchronous (reported beside it): each render waits for its frames.
     Three pinned input buffers are refilled (their times shifted) between
-    the timed runs, outside the timed region."""
+    the timed runs, outside the timed region.  Each mode is timed in three
+    runs of three steps; the median run is reported (the host link of a
+    shared box varies from run to run), all three beside it."""
     h, ev, span, win, M, sc = r["handle"], r["ev"], r["span"], r["win"], r["M"], r["sc"]
     n_ev = len(ev)
     k0 = r["total"]
@@ -451,16 +478,23 @@ def e2e_leg(esi, torch, r, steps):
 
     fill()
     run(2)               # warm
-    fill()
-    dt = run(2)
-    fill()
-    dt_sync = run(0)
+    dts, dts_sync = [], []
+    for _ in range(3):
+        fill()
+        dts.append(run(2))
+    for _ in range(3):
+        fill()
+        dts_sync.append(run(0))
+    dt, dt_sync = statistics.median(dts), statistics.median(dts_sync)
     return {"value": n_ev * nb / dt, "unit": "events/s",
             "h2d_bytes_per_step": n_ev * 16, "d2h_bytes_per_step": M * sc.W * sc.H,
             "frames_per_s": M * nb / dt, "steps": nb,
-            "mode": "pipelined: push of step k+1 overlaps the render of step k (out_on_device=2)",
+            "runs_events_per_s": [round(n_ev * nb / x) for x in dts],
+            "mode": "pipelined: push of step k+1 overlaps the render of step k (out_on_device=2); "
+                    "median of 3 runs",
             "synchronous": {"value": n_ev * nb / dt_sync, "unit": "events/s",
-                            "mode": "each render waits for its frames (out_on_device=0)"}}
+                            "runs_events_per_s": [round(n_ev * nb / x) for x in dts_sync],
+                            "mode": "each render waits for its frames (out_on_device=0); median of 3 runs"}}
 
 
 def latency_leg(esi):

@@ -560,6 +560,10 @@ void esi_destroy(esi_handle *h)
 static constexpr size_t kHostCheckMax = 1u << 16;
 // events per chunk of a device-checked push
 static constexpr unsigned long long kPushChunk = 1ull << 21;
+// a host push that would overwrite ring slots a queued render still bins
+// grows the ring (up to this many events) instead of waiting for it, so the
+// next step's copy overlaps the current render
+static constexpr unsigned long long kOverlapRingMax = 1ull << 28;
 
 int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_device)
 {
@@ -568,6 +572,26 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
     const unsigned long long pending = h->tail - h->head;
     int rc = ensure_ring(h, pending + n);
     if (rc) return rc;
+    if (!ev_on_device && !h->tmirror && h->tail + n > h->cap) {
+        // the oldest render still binning slots this push would overwrite
+        const unsigned long long o1 = h->tail + n - h->cap;
+        unsigned long long a0 = ~0ull;
+        for (int r = 0; r < esi_handle::kSpans; ++r) {
+            const auto &sp = h->span[r];
+            if (!sp.live || sp.a0 >= o1) continue;
+            if (cudaEventQuery(sp.ev) == cudaErrorNotReady) {
+                a0 = std::min(a0, sp.a0);
+                // "not ready" is no failure: keep it out of the launch checks
+                if (cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();
+            }
+        }
+        if (a0 != ~0ull && h->tail - a0 + n <= kOverlapRingMax) {
+            // room for twice that, so a deeper pipeline later needs no second
+            // growth (each waits for the queued work)
+            rc = ensure_ring(h, std::min(2 * (h->tail - a0 + n), kOverlapRingMax));
+            if (rc) return rc;
+        }
+    }
     const unsigned long long mask = h->cap - 1;
     const long long prev = std::max(h->push_floor, h->last_event_t);
     const cudaMemcpyKind kind = ev_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -634,9 +658,10 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
             h->exact_spans.push_back({h->tail, h->tail + n});
         h->last_event_t = ev[n - 1].t_us;
     } else {
-        // chunk by chunk: copy in, check on the device and keep every
-        // kSparse-th time (push stream), then bring those to the sparse
-        // mirror (aux stream) while the next chunk is copied in
+        // chunk by chunk: the copies follow one another on the push stream;
+        // each chunk, once in, is checked on the device, and every
+        // kSparse-th time kept and brought to the sparse mirror, on the aux
+        // stream while the next chunks are copied in
         const unsigned long long g0 = (h->tail + kSparse - 1) / kSparse * kSparse;
         rc = ensure_device(h, &h->dsparse, &h->dsparse_cap, (size_t)(n / kSparse + 2));
         if (rc) return rc;
@@ -646,11 +671,11 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
         for (unsigned long long c0 = 0; e == cudaSuccess && c0 < n; c0 += kPushChunk, ++j) {
             const unsigned long long c1 = std::min<unsigned long long>(n, c0 + kPushChunk);
             copy_in(c0, c1);
-            if (e == cudaSuccess)
-                e = launch_push_check(h->ring, mask, h->tail, c0, (long long)(c1 - c0), n, prev, g0,
-                                      h->dsparse, h->dres, cs);
             if (e == cudaSuccess) e = cudaEventRecord(h->ev_chunk[j & 3], cs);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux_stream, h->ev_chunk[j & 3], 0);
+            if (e == cudaSuccess)
+                e = launch_push_check(h->ring, mask, h->tail, c0, (long long)(c1 - c0), n, prev, g0,
+                                      h->dsparse, h->dres, h->aux_stream);
             // sparse entries j of this chunk: indices g0 + j kSparse in [tail + c0, tail + c1)
             const unsigned long long ja = (std::max(g0, (h->tail + c0 + kSparse - 1) / kSparse * kSparse) - g0) / kSparse;
             const unsigned long long jb = (std::max(g0, (h->tail + c1 + kSparse - 1) / kSparse * kSparse) - g0) / kSparse;
@@ -663,7 +688,8 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
             }
         }
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(h->hres, h->dres, sizeof(PushResult), cudaMemcpyDeviceToHost, cs);
+            e = cudaMemcpyAsync(h->hres, h->dres, sizeof(PushResult), cudaMemcpyDeviceToHost,
+                                h->aux_stream);
         // the caller may reuse its buffer as soon as this returns
         if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->aux_stream);

@@ -453,12 +453,15 @@ def test_large_pushes_are_checked_on_the_device():
     compare({"S": S, "T": T, "frames": fr}, ref, p["C"], "large pushes")
 
 
-def test_async_host_output_with_overlapping_pushes():
+@pytest.mark.parametrize("small_first", [False, True])
+def test_async_host_output_with_overlapping_pushes(small_first):
     # out_on_device = 2 returns once the render is queued; the next host push
     # runs on its own stream and may only overwrite ring slots the previous
     # render has binned.  Each push here fills the whole initial ring (2^20
-    # events) and each render consumes all of it, so every push overwrites
-    # exactly the slots the previous render reads.
+    # events) and each render consumes all of it, so every push would
+    # overwrite exactly the slots the previous render reads: the handle grows
+    # the ring once instead of waiting.  After a small push (checked on the
+    # host, whose time mirror the ring would have to carry) it waits instead.
     import torch
     rng = np.random.default_rng(15)
     W, H = 160, 120
@@ -474,7 +477,11 @@ def test_async_host_output_with_overlapping_pushes():
     with GpuStream(W, H, p) as g:
         outs = []
         for k in range(K):
-            assert g.push(ev[k * n:(k + 1) * n]) == 0
+            if small_first and k == 0:
+                assert g.push(ev[:1000]) == 0
+                assert g.push(ev[1000:n]) == 0
+            else:
+                assert g.push(ev[k * n:(k + 1) * n]) == 0
             if k % 2 == 0:
                 o = torch.empty((per, H, W), dtype=torch.uint8, pin_memory=True)
             else:

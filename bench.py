@@ -448,9 +448,10 @@ def e2e_leg(esi, torch, r, steps):
     overlaps this step's render; one esi_synchronize ends the timed region.
     Synchronous (reported beside it): each render waits for its frames.
     Three pinned input buffers are refilled (their times shifted) between
-    the timed runs, outside the timed region.  Each mode is timed in three
-    runs of three steps; the median run is reported (the host link of a
-    shared box varies from run to run), all three beside it."""
+    the timed runs, outside the timed region.  Each mode is timed in five
+    runs of three steps after two warm-up runs; the median run is reported
+    (the host link of a shared box varies from run to run), all five beside
+    it."""
     h, ev, span, win, M, sc = r["handle"], r["ev"], r["span"], r["win"], r["M"], r["sc"]
     n_ev = len(ev)
     k0 = r["total"]
@@ -476,13 +477,14 @@ def e2e_leg(esi, torch, r, steps):
         k[0] += nb
         return dt
 
-    fill()
-    run(2)               # warm
+    for _ in range(2):   # warm (the handle sizes its ring for the overlap here)
+        fill()
+        run(2)
     dts, dts_sync = [], []
-    for _ in range(3):
+    for _ in range(5):
         fill()
         dts.append(run(2))
-    for _ in range(3):
+    for _ in range(5):
         fill()
         dts_sync.append(run(0))
     dt, dt_sync = statistics.median(dts), statistics.median(dts_sync)
@@ -491,10 +493,10 @@ def e2e_leg(esi, torch, r, steps):
             "frames_per_s": M * nb / dt, "steps": nb,
             "runs_events_per_s": [round(n_ev * nb / x) for x in dts],
             "mode": "pipelined: push of step k+1 overlaps the render of step k (out_on_device=2); "
-                    "median of 3 runs",
+                    "median of 5 runs",
             "synchronous": {"value": n_ev * nb / dt_sync, "unit": "events/s",
                             "runs_events_per_s": [round(n_ev * nb / x) for x in dts_sync],
-                            "mode": "each render waits for its frames (out_on_device=0); median of 3 runs"}}
+                            "mode": "each render waits for its frames (out_on_device=0); median of 5 runs"}}
 
 
 def latency_leg(esi):

@@ -913,10 +913,11 @@ def cpu_baseline_parallel(name):
 class ParityAcc:
     """Maximum errors of GPU results against the oracle's, for one workload:
     state error |dS| / max(|S_ref|, C) (the tests' bar, 1e-5) and with the
-    floor 1e-3 C, T exactness, frame LSB differences."""
+    floor 1e-3 C, the largest |dS| where |S_ref| < C in units in the last
+    place of C in FP32, T exactness, frame LSB differences."""
 
     def __init__(self):
-        self.err_c = self.err_mc = 0.0
+        self.err_c = self.err_mc = self.ulps_c = 0.0
         self.t_exact = True
         self.lsb = self.off = self.frames = self.pixels = 0
 
@@ -925,6 +926,10 @@ class ParityAcc:
         if d.size:
             self.err_c = max(self.err_c, float(np.max(d / np.maximum(np.abs(S_ref), C))))
             self.err_mc = max(self.err_mc, float(np.max(d / np.maximum(np.abs(S_ref), 1e-3 * C))))
+            small = np.abs(S_ref) < C
+            if small.any():
+                ulp = float(np.spacing(np.float32(C)))
+                self.ulps_c = max(self.ulps_c, float(np.max(d[small])) / ulp)
         self.t_exact &= bool(np.array_equal(T, T_ref))
         self.pixels += int(d.size)
 
@@ -937,6 +942,7 @@ class ParityAcc:
 
     def out(self):
         return {"state_err": self.err_c, "state_err_floor_1e-3C": self.err_mc,
+                "abs_err_near_zero_ulps_of_C": round(self.ulps_c, 2),
                 "T_exact": self.t_exact, "frame_max_lsb": self.lsb,
                 "frame_off_by_one": self.off, "frames": self.frames, "pixels": self.pixels,
                 "pass": self.err_c <= 1e-5 and self.t_exact and self.lsb <= 1}
@@ -1083,9 +1089,9 @@ def summary(line):
              "max_Gev_s": g(d["batched_throughput"]["events_per_s"])}
         sv[tag] = e
     s["serving"] = sv
-    s["parity(err,err1e-3C,lsb,off,frames)"] = {
+    s["parity(err,err1e-3C,ulpsC,lsb,off,frames)"] = {
         k: [float(f"{v['state_err']:.2e}"), float(f"{v['state_err_floor_1e-3C']:.2e}"),
-            v["frame_max_lsb"], v["frame_off_by_one"], v["frames"]]
+            v.get("abs_err_near_zero_ulps_of_C"), v["frame_max_lsb"], v["frame_off_by_one"], v["frames"]]
         for k, v in (line.get("parity") if ok(line.get("parity")) else {}).items()}
     return s
 

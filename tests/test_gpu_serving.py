@@ -320,6 +320,48 @@ def test_tick_trace_records_every_tick_with_work():
         esi.esi_server_destroy(srv)
 
 
+def test_close_with_frames_in_flight_and_an_id_reused_at_once():
+    # esi_stream_close returns without waiting: the closed stream's frames
+    # still reach its sink, and a stream opened on the same id right away
+    # sees none of them
+    esi = _esi()
+    W, H = 120, 90
+    pp = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1, t_origin_us=0)
+    rc, srv = esi.esi_server_create(64 << 20, None, 0)
+    assert rc == 0
+    try:
+        rc, a = esi.esi_stream_open(srv, W, H, esi.make_params(**pp))
+        assert rc == 0
+        sink = np.zeros((3, H, W), dtype=np.uint8)
+        sink_t = np.zeros(3, dtype=np.int64)
+        assert esi.esi_stream_set_frame_sink(srv, a, sink, 3, sink_t) == 0
+        ev_a = random_events(np.random.default_rng(31), W, H, 60_000, 0, 30_000)
+        assert esi.esi_stream_push(srv, a, ev_a, len(ev_a)) == 0
+        assert esi.esi_server_tick(srv, 30_000) == 0          # frames 10, 20, 30 ms queued
+        assert esi.esi_stream_close(srv, a) == 0               # no wait
+        pb = dict(pp, C=0.3, t_origin_us=30_000)
+        rc, b = esi.esi_stream_open(srv, W, H, esi.make_params(**pb))
+        assert rc == 0 and b == a                              # the id comes back at once
+        ev_b = random_events(np.random.default_rng(32), W, H, 20_000, 30_000, 50_000)
+        assert esi.esi_stream_push(srv, b, ev_b, len(ev_b)) == 0
+        assert esi.esi_server_tick(srv, 45_000) == 0           # frame 40 ms of the new stream
+        assert esi.esi_server_sync(srv) == 0
+        rc, n_b = esi.esi_stream_frames_done(srv, b)
+        assert rc == 0 and n_b == 1
+        out = np.empty((H, W), dtype=np.uint8)
+        rc, tf = esi.esi_stream_frame_seq(srv, b, 0, out)
+        assert rc == 0 and tf == 40_000
+        ref_b = oracle.OracleState(W, H, oracle_params(pb))
+        fb, _ = ref_b.replay(ev_b, np.array([40_000], dtype=np.int64))
+        assert int(np.abs(out.astype(np.int16) - fb[0].astype(np.int16)).max()) <= 1
+        ref_a = oracle.OracleState(W, H, oracle_params(pp))
+        fa, _ = ref_a.replay(ev_a, np.array([10_000, 20_000, 30_000], dtype=np.int64))
+        assert list(sink_t) == [10_000, 20_000, 30_000]
+        assert int(np.abs(sink.astype(np.int16) - fa.astype(np.int16)).max()) <= 1
+    finally:
+        esi.esi_server_destroy(srv)
+
+
 def test_apply_mode_validation():
     esi = _esi()
     for mode, threads, ok in ((0, 0, True), (1, 1, True), (2, 16, True), (3, 0, False),

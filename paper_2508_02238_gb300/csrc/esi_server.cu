@@ -1618,7 +1618,11 @@ int esi_server_run(esi_server *s, const esi_packet *pk, size_t n, int64_t tick_u
         } else {
             now = next_tick;
         }
-        for (; i < n && pk[i].arrival_us <= now; ++i) {
+        // a packet that makes its stream's frame due is rendered before the
+        // packets queued behind it are taken (the watermarks of their
+        // streams keep their events and frames out of that tick)
+        bool early = false;
+        for (; i < n && pk[i].arrival_us <= now && !early; ++i) {
             const esi_packet &q = pk[i];
             int rc = ESI_OK;
             if (q.kind == ESI_PACKET_OPEN) {
@@ -1649,6 +1653,8 @@ int esi_server_run(esi_server *s, const esi_packet *pk, size_t n, int64_t tick_u
                 } else {
                     rc = esi_stream_push(s, id, q.ev, (size_t)q.n);
                     if (!rc) rc = esi_stream_watermark(s, id, q.arrival_us);
+                    early = !rc && realtime && now < t_end_us && now - last_tick >= min_gap &&
+                            frames_due(s->streams[id], now);
                 }
             }
             if (rc) {

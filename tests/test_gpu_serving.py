@@ -583,10 +583,13 @@ def _state_bytes(W, H):
     return ((P * 4 + 255) // 256 * 256 + P * 8 + 255) // 256 * 256
 
 
-def test_executor_join_leave_and_admission():
+@pytest.mark.parametrize("realtime", [0, 1])
+def test_executor_join_leave_and_admission(realtime):
     """Streams join and leave through the executor's OPEN / CLOSE packets; a
     join that does not fit the state budget is refused and its events dropped;
-    a later join fits again once a stream has left."""
+    a later join fits again once a stream has left.  As fast as possible, and
+    paced by the wall clock (where a packet that makes a frame due is
+    rendered before the packets behind it are taken)."""
     esi = _esi()
     P = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1)
     t_end = 60_000
@@ -626,7 +629,7 @@ def test_executor_join_leave_and_admission():
     rc, srv = esi.esi_server_create(budget, None, 0)
     assert rc == 0
     try:
-        assert esi.esi_server_run(srv, pk, len(items), 1000, t_end, 0) == 0
+        assert esi.esi_server_run(srv, pk, len(items), 1000, t_end, realtime) == 0
         rc, st = esi.esi_server_get_stats(srv)
         assert rc == 0
         assert st.streams_admitted == 4 and st.streams_refused == 1

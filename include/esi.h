@@ -516,7 +516,7 @@ typedef struct {
                            * before issued_ns: a small tick can finish on the
                            * device before its call returns)                    */
     float copy_ms;        /* device: the tick's table copy                         */
-    float kernels_ms;     /* device: the tick's kernels and completion stamp       */
+    float kernels_ms;     /* device: the tick's kernels                           */
     float gap_ms;         /* device: from the previous traced tick's end to this
                            * tick's start; near 0 when it queued behind it; -1 for
                            * the first                                              */
@@ -565,8 +565,10 @@ typedef struct {
  * they arrive (esi_stream_push, then esi_stream_watermark(arrival_us)) and
  * ticks every tick_us of stream time until t_end_us, then waits for the
  * device.  realtime = 1 paces stream time with the wall clock (stream time 0
- * = the call), so latencies are those of live serving; realtime = 0 advances
- * tick by tick as fast as host and device allow (throughput).
+ * = the call), so latencies are those of live serving: a packet that makes
+ * its stream's frame due is followed by a tick at once (at most one every
+ * tick_us / 5), before the packets queued behind it are taken; realtime = 0
+ * advances tick by tick as fast as host and device allow (throughput).
  *
  * Streams join and leave on the packets' schedule.  An OPEN packet opens a
  * stream (esi_stream_open, then its tile height) and binds the packet's slot

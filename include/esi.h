@@ -419,6 +419,8 @@ typedef struct {
     uint64_t host_pool_used_bytes;  /* held by rings now (retired ones included) */
     uint64_t host_pool_peak_bytes;  /* the most held since the last reset        */
     uint64_t ring_grows;          /* rings moved into larger ones              */
+    uint64_t events_dropped;      /* x >= W or y >= H: never applied (as of the
+                                   * last esi_server_sync or state read)      */
 } esi_server_stats;
 
 typedef struct esi_server esi_server;
@@ -496,7 +498,9 @@ int esi_stream_state(esi_server *srv, int stream_id, float *S, int64_t *T);
  * needs that memory). */
 int esi_stream_close(esi_server *srv, int stream_id);
 
-/* Wait for all queued ticks. */
+/* Wait for all queued ticks.  Returns a failure the device detected in them
+ * (ESI_ETIMEOUT: a bounded wait in a kernel gave up; esi_server_last_error
+ * says which), once and for every later call. */
 int esi_server_sync(esi_server *srv);
 
 int esi_server_get_stats(esi_server *srv, esi_server_stats *out);

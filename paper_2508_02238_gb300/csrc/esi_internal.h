@@ -48,8 +48,10 @@ struct MapParams {
 struct DevStatus {
     unsigned long long dropped;   // events with x >= W or y >= H
     int err;                      // ESI_* code of a device-detected failure
-    int err_where;                // which kernel / wait gave up
+    int err_where;                // which kernel / wait gave up (kWhere*)
 };
+constexpr int kWhereBinCopy = 1;   // the binning's bulk copy of its chunk
+constexpr int kWhereTickWait = 2;  // a fused tick's tile item waiting for its stream's binning
 
 // The binning finds same-tile lanes of a warp through kBinMaskSlots mask
 // words per warp in shared memory, indexed by tile mod kBinMaskSlots, and one

@@ -29,8 +29,6 @@ namespace esi {
 
 constexpr int kBinThreads = 256;
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
-constexpr int kWhereBinCopy = 1;
-constexpr int kWhereTickWait = 2;
 
 static __host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 

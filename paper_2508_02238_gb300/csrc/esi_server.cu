@@ -356,6 +356,7 @@ struct esi_server {
     size_t trace_n = 0;                  // records written since the reset
     cudaEvent_t prev_end = nullptr;      // the last traced tick's end
     std::string err;  // the last failure, for esi_server_last_error
+    unsigned long long dropped = 0;  // events outside their sensor, as last read
     // pinned host pool of the streams' event rings, and rings replaced by
     // larger ones that ticks in flight may still read: freed once the tick
     // count reaches the tag
@@ -601,7 +602,19 @@ int wait_all(esi_server *s)
         if (wall_ns() > t_give_up) return ESI_ETIMEOUT;
     }
     poll(s);
-    return cuda_note(s, "waiting for ticks", e);
+    if (e != cudaSuccess) return cuda_note(s, "waiting for ticks", e);
+    // what the kernels detected (the stream is idle: the status is final)
+    DevStatus st{};
+    e = cudaMemcpy(&st, s->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_note(s, "reading the device status", e);
+    s->dropped = st.dropped;
+    if (st.err) {
+        s->err = std::string("device: a bounded wait gave up in ") +
+                 (st.err_where == kWhereTickWait ? "a tick's tile items (their stream's binning)"
+                                                  : "the binning's chunk copy");
+        return st.err;
+    }
+    return ESI_OK;
 }
 
 // Variant group g: tile height index g / 12 (4, 8, 16 rows), then render
@@ -1493,6 +1506,7 @@ int esi_server_get_stats(esi_server *s, esi_server_stats *out)
     out->host_pool_used_bytes = s->harena.used();
     out->host_pool_peak_bytes = s->hpool_peak;
     out->ring_grows = s->ring_grows;
+    out->events_dropped = s->dropped;
     return ESI_OK;
 }
 

@@ -75,7 +75,8 @@ class esi_server_stats(ctypes.Structure):
                 ("events_refused", ctypes.c_uint64), ("host_tick_p50_ms", ctypes.c_double),
                 ("host_tick_p99_ms", ctypes.c_double), ("gpu_tick_p99_ms", ctypes.c_double),
                 ("host_pool_bytes", ctypes.c_uint64), ("host_pool_used_bytes", ctypes.c_uint64),
-                ("host_pool_peak_bytes", ctypes.c_uint64), ("ring_grows", ctypes.c_uint64)]
+                ("host_pool_peak_bytes", ctypes.c_uint64), ("ring_grows", ctypes.c_uint64),
+                ("events_dropped", ctypes.c_uint64)]
 
 
 ESI_PACKET_EVENTS, ESI_PACKET_OPEN, ESI_PACKET_CLOSE = 0, 1, 2

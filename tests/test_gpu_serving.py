@@ -362,6 +362,37 @@ def test_close_with_frames_in_flight_and_an_id_reused_at_once():
         esi.esi_server_destroy(srv)
 
 
+def test_served_events_outside_the_sensor_are_dropped_and_counted():
+    esi = _esi()
+    W, H = 100, 60
+    pp = dict(C=0.2, k_per_s=10.0, b=2.0, s_min=-1.0, s_max=1.0, render_decay=1, t_origin_us=0)
+    rc, srv = esi.esi_server_create(64 << 20, None, 0)
+    assert rc == 0
+    try:
+        rc, sid = esi.esi_stream_open(srv, W, H, esi.make_params(**pp))
+        assert rc == 0
+        ev = random_events(np.random.default_rng(41), W + 7, H + 3, 30_000, 0, 20_000)
+        bad = int(np.count_nonzero((ev["x"] >= W) | (ev["y"] >= H)))
+        assert bad > 0
+        assert esi.esi_stream_push(srv, sid, ev, len(ev)) == 0
+        assert esi.esi_server_tick(srv, 20_000) == 0
+        assert esi.esi_server_sync(srv) == 0
+        rc, st = esi.esi_server_get_stats(srv)
+        assert rc == 0 and st.events_dropped == bad and st.events == len(ev)
+        S = np.empty(W * H, dtype=np.float32)
+        T = np.empty(W * H, dtype=np.int64)
+        assert esi.esi_stream_state(srv, sid, S, T) == 0
+        ref = oracle.OracleState(W, H, oracle_params(pp))
+        ref.integrate(ev)
+        assert np.array_equal(T, ref.T)
+        assert state_error(S, ref.S, pp["C"]) <= STATE_TOL
+        out = np.empty((H, W), dtype=np.uint8)
+        rc, tf = esi.esi_stream_frame_seq(srv, sid, 1, out)
+        assert rc == 0 and tf == 20_000
+    finally:
+        esi.esi_server_destroy(srv)
+
+
 def test_apply_mode_validation():
     esi = _esi()
     for mode, threads, ok in ((0, 0, True), (1, 1, True), (2, 16, True), (3, 0, False),

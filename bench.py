@@ -488,7 +488,10 @@ def e2e_leg(esi, torch, r, steps):
         fill()
         dts_sync.append(run(0))
     dt, dt_sync = statistics.median(dts), statistics.median(dts_sync)
+    rc, st = esi.esi_get_stats(h)
     return {"value": n_ev * nb / dt, "unit": "events/s",
+            "ring": {"capacity_events": int(st.ring_capacity), "grows": int(st.ring_grows),
+                     "push_waits": int(st.push_waits)},
             "h2d_bytes_per_step": n_ev * 16, "d2h_bytes_per_step": M * sc.W * sc.H,
             "frames_per_s": M * nb / dt, "steps": nb,
             "runs_events_per_s": [round(n_ev * nb / x) for x in dts],

@@ -102,6 +102,9 @@ typedef struct {
     uint64_t kernel_launches;  /* device kernels this handle has launched   */
     int64_t last_event_t_us;
     int64_t last_frame_t_us;
+    uint64_t ring_capacity;    /* events the device ring holds now          */
+    uint64_t ring_grows;       /* times it moved into a larger one          */
+    uint64_t push_waits;       /* host pushes queued behind a render still binning */
 } esi_stats;
 
 /*

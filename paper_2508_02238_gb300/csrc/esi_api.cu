@@ -228,6 +228,7 @@ static int ensure_ring(esi_handle *h, unsigned long long need)
     if (h->ring) cudaFree(h->ring);
     if (h->tmirror) cudaFreeHost(h->tmirror);
     if (h->tsparse) cudaFreeHost(h->tsparse);
+    if (h->ring) h->ring_grows += 1;
     h->ring = nr;
     h->cap = nc;
     h->tmirror = nm;
@@ -621,7 +622,16 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
             }
         }
         if (pick < 0 && oldest >= 0 && o0 < oldest_a0) pick = oldest;
-        if (pick >= 0) e = cudaStreamWaitEvent(cs, h->span[pick].ev, 0);
+        if (pick >= 0) {
+            const cudaError_t q = cudaEventQuery(h->span[pick].ev);
+            if (q == cudaErrorNotReady) {
+                if (cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();
+                e = cudaStreamWaitEvent(cs, h->span[pick].ev, 0);
+                h->push_waits += 1;
+            } else if (q != cudaSuccess) {
+                e = q;
+            }
+        }
     }
     if (e != cudaSuccess) return cuda_fail(h, e);
     // events [i0, i1) of the push into their ring slots (split at the wrap)
@@ -785,6 +795,9 @@ int esi_get_stats(esi_handle *h, esi_stats *out)
     out->kernel_launches = h->launches;
     out->last_event_t_us = h->last_event_t;
     out->last_frame_t_us = h->last_frame_t;
+    out->ring_capacity = h->cap;
+    out->ring_grows = h->ring_grows;
+    out->push_waits = h->push_waits;
     return rc;
 }
 

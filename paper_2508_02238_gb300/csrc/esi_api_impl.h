@@ -125,6 +125,7 @@ struct esi_handle {
     long long last_event_t = 0;
     long long last_frame_t = 0;
     unsigned long long pushed = 0, consumed = 0, dropped = 0, frames = 0, launches = 0;
+    unsigned long long ring_grows = 0, push_waits = 0;
 
     bool prof_on = false;
     std::vector<esi::ProfRec> prof_recs;

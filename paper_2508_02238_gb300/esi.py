@@ -38,7 +38,9 @@ class esi_stats(ctypes.Structure):
     _fields_ = [("events_pushed", ctypes.c_uint64), ("events_consumed", ctypes.c_uint64),
                 ("events_dropped", ctypes.c_uint64), ("events_pending", ctypes.c_uint64),
                 ("frames_rendered", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
-                ("last_event_t_us", ctypes.c_int64), ("last_frame_t_us", ctypes.c_int64)]
+                ("last_event_t_us", ctypes.c_int64), ("last_frame_t_us", ctypes.c_int64),
+                ("ring_capacity", ctypes.c_uint64), ("ring_grows", ctypes.c_uint64),
+                ("push_waits", ctypes.c_uint64)]
 
 
 class esi_tuning(ctypes.Structure):

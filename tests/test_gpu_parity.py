@@ -491,6 +491,10 @@ def test_async_host_output_with_overlapping_pushes(small_first):
         assert g.esi.esi_synchronize(g.h) == 0
         frames = np.concatenate([o.numpy() if hasattr(o, "numpy") else o for o in outs])
         S, T = g.state()
+        rc, st = g.esi.esi_get_stats(g.h)
+        assert rc == 0 and st.ring_capacity >= n and st.ring_capacity & (st.ring_capacity - 1) == 0
+        if small_first:   # the host time mirror keeps the ring at its size: pushes wait
+            assert st.ring_grows == 0 and st.ring_capacity == n
     ref = run_oracle(ev, W, H, p, np.concatenate(tfs))
     compare({"S": S, "T": T, "frames": frames}, ref, p["C"], "async host output")
 

@@ -630,14 +630,27 @@ def _server_run(esi, srv, pk, npk, t_end, realtime, tick_us=1000):
 
 def _tick_gaps(esi, srv):
     """From the server's tick trace: the longest wait between two tick calls
-    with work, and how many exceeded 2 ms (the executor fell behind)."""
+    with work, how many exceeded 2 ms (the executor fell behind), and where a
+    tick with frames spends its time (p50 / p99 in ms: host packing and
+    queueing, the table copy, the kernels, call to completion stamp; and the
+    share of ticks whose work queued behind the previous tick's)."""
     rc, tr = esi.esi_server_trace(srv)
     if rc or tr is None or len(tr) < 2:
         return {}
     gaps = np.diff(tr["call_ns"]) / 1e6
-    return {"max_tick_gap_ms": round(float(gaps.max()), 3),
-            "tick_gaps_over_2ms": int((gaps > 2.0).sum()),
-            "traced_ticks": int(len(tr))}
+    out = {"max_tick_gap_ms": round(float(gaps.max()), 3),
+           "tick_gaps_over_2ms": int((gaps > 2.0).sum()),
+           "traced_ticks": int(len(tr))}
+    f = tr[tr["frames"] > 0]
+    if len(f):
+        def pp(x):
+            return [round(float(np.percentile(x, 50)), 3), round(float(np.percentile(x, 99)), 3)]
+        out["frame_ticks_ms(p50,p99)"] = {
+            "host": pp((f["issued_ns"] - f["call_ns"]) / 1e6),
+            "copy": pp(f["copy_ms"]), "kernels": pp(f["kernels_ms"]),
+            "call_to_ready": pp((f["ready_ns"] - f["call_ns"]) / 1e6),
+            "queued_share": round(float(np.mean((f["gap_ms"] >= 0) & (f["gap_ms"] < 0.005))), 3)}
+    return out
 
 
 def _stats(st, dt, realtime, n_ev, expected=None):

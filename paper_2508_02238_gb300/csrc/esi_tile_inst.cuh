@@ -6,7 +6,10 @@
 
 namespace esi {
 
-#define ESI_TILE_BOUNDS(TH) __launch_bounds__(TH * 32, (TH * 32 >= 1024) ? 1 : 1024 / (TH * 32))
+// 8-row tiles: at least three blocks per SM (their shared memory allows
+// three at the default batch), so the compiler may use up to 85 registers a
+// thread; other heights: as many blocks as fill 1024 threads
+#define ESI_TILE_BOUNDS(TH) __launch_bounds__(TH * 32, (TH * 32 >= 1024) ? 1 : (TH == 8 ? 3 : 1024 / (TH * 32)))
 
 template <int TH, int PPL, int RD, int DK, bool VEC, bool EV = false>
 __global__ void ESI_TILE_BOUNDS(TH) esi_tile_kernel(TileArgs a)

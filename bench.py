@@ -68,9 +68,9 @@ HEADLINE = "c2"
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of a full launch of the headline's shape (--ncu-case: its
 # second sub-batch, 4.19 M events and 8 frames), keyed by kernel.
-NCU_TRAFFIC_PER_LAUNCH = {"esi_tile": 48737792, "esi_bin": 70952448}
+NCU_TRAFFIC_PER_LAUNCH = {"esi_tile": 48732160, "esi_bin": 70952448}
 # Warp instructions per launch (smsp__inst_executed.sum) from the same capture.
-NCU_INST_PER_LAUNCH = {"esi_tile": 54074602}
+NCU_INST_PER_LAUNCH = {"esi_tile": 53456009}
 
 
 def parse_args():

@@ -90,6 +90,8 @@ def parse_args():
     ap.add_argument("--ncu-case", action="store_true",
                     help="run the small profiling case (0.25 s of the headline stream, 25 frames, "
                          "3 renders) and print no bench line; for ncu captures")
+    ap.add_argument("--scan-chain", type=int, default=0,
+                    help="esi_tuning.scan_chain of the --ncu-case handle (0: default; 33: scan off)")
     ap.add_argument("--diagnostics-only", action="store_true",
                     help="run only the diagnostics leg (event counts, per-event states, noise "
                          "map) and print its JSON; also the case for their ncu captures")
@@ -1112,11 +1114,12 @@ def summary(line):
     return s
 
 
-def ncu_case():
+def ncu_case(scan_chain=0):
     """A small case of the headline's launch shape for kernel captures: the
     first 0.25 s of the 1280x720 stream (about 12 M events, 200 MB, three
     4 M-event sub-batches per render as in the bench), 25 frames per render,
-    three renders."""
+    three renders.  scan_chain: esi_tuning.scan_chain (0: default; 33: the
+    segmented scan off)."""
     import torch  # noqa: F401  (CUDA context as in the bench)
     import synth
     from paper_2508_02238_gb300 import esi
@@ -1125,6 +1128,10 @@ def ncu_case():
     span = 250_000
     rc, h = esi.esi_create(sc.W, sc.H, esi.make_params(**PARAMS), 0)
     esi.check(rc, "create")
+    if scan_chain:
+        t = esi.esi_tuning()
+        t.scan_chain = scan_chain
+        esi.check(esi.esi_set_tuning(h, t), "tuning")
     out = torch.empty((25, sc.H, sc.W), dtype=torch.uint8, device="cuda")
     for k in range(3):
         esi.check(esi.esi_push_events(h, shifted(ev, k * span), len(ev), 0))
@@ -1141,7 +1148,7 @@ def main():
     args = parse_args()
     SERVING_APPLY = args.serving_apply
     if args.ncu_case:
-        ncu_case()
+        ncu_case(args.scan_chain)
         return
     if args.diagnostics_only or args.serving_only or args.parity_only:
         import torch

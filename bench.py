@@ -13,9 +13,9 @@ value: events/s with every step's events already resident in device memory
 (pushed before the timed region), frames written to device memory; inputs
 per step (800 MB) exceed the 129 MB L2.  e2e: the same metric through the C
 ABI with pinned host buffers inside the timed region: each step pushes its
-events from host memory and renders its frames into a host buffer, the next
-step's push overlapping this step's render (the synchronous variant is
-reported beside it).  With --gpus N (torchrun) every rank runs its own replica
+events (8-byte packed; 16-byte events beside it) from host memory and
+renders its frames into a host buffer, the next step's push overlapping this
+step's render (the synchronous variant is reported beside it).  With --gpus N (torchrun) every rank runs its own replica
 on its own GPU (no collective on the data path; weak scaling).
 
 Further legs on rank 0 (skipped with --no-extras): the other single-sensor
@@ -449,59 +449,88 @@ def e2e_leg(esi, torch, r, steps):
     render into a host buffer (out_on_device = 2), so the next step's push
     overlaps this step's render; one esi_synchronize ends the timed region.
     Synchronous (reported beside it): each render waits for its frames.
-    Three pinned input buffers are refilled (their times shifted) between
-    the timed runs, outside the timed region.  Each mode is timed in five
-    runs of three steps after two warm-up runs; the median run is reported
-    (the host link of a shared box varies from run to run), all five beside
-    it."""
+    Inputs: 8-byte packed events (esi_push_packed, the reported value) and
+    16-byte events (esi_push_events, beside it), three pinned buffers of
+    each.  A step's 16-byte buffer is refilled (times shifted) between the
+    timed runs, outside the timed region; a packed buffer needs no refill
+    (the shift moves only the push's time base).  Each variant is timed in
+    five runs of three steps after two warm-up runs; the median run is
+    reported (the host link of a shared box varies from run to run), all
+    five beside it."""
+    import synth
     h, ev, span, win, M, sc = r["handle"], r["ev"], r["span"], r["win"], r["M"], r["sc"]
     n_ev = len(ev)
     k0 = r["total"]
     nb = 3
     host_in = [torch.empty(n_ev * 16, dtype=torch.uint8, pin_memory=True) for _ in range(nb)]
     views = [b.numpy().view(ev.dtype) for b in host_in]
+    t0 = int(ev["t"][0])
+    words = synth.pack_events(ev, t0)
+    host_pk = [torch.empty(n_ev * 8, dtype=torch.uint8, pin_memory=True) for _ in range(nb)]
+    for b in host_pk:
+        b.numpy().view(np.uint64)[:] = words
+    del words
     host_out = [torch.empty((M, sc.H, sc.W), dtype=torch.uint8, pin_memory=True) for _ in range(2)]
     k = [k0]
 
-    def fill():
+    def fill(packed):
+        if packed:
+            return
         for i in range(nb):
             views[i][:] = ev
             views[i]["t"] += (k[0] + i) * span
 
-    def run(mode):
-        t0 = time.perf_counter()
+    def run(mode, packed):
+        ts = time.perf_counter()
         for i in range(nb):
-            esi.check(esi.esi_push_events(h, host_in[i], n_ev, 0), "push")
+            if packed:
+                esi.check(esi.esi_push_packed(h, host_pk[i], n_ev, t0 + (k[0] + i) * span, 0),
+                          "push")
+            else:
+                esi.check(esi.esi_push_events(h, host_in[i], n_ev, 0), "push")
             esi.check(esi.esi_render_frames(h, frame_times(k[0] + i, span, win), M,
                                             host_out[i % 2], mode), "render")
         esi.check(esi.esi_synchronize(h), "sync")
-        dt = time.perf_counter() - t0
+        dt = time.perf_counter() - ts
         k[0] += nb
         return dt
 
-    for _ in range(2):   # warm (the handle sizes its ring for the overlap here)
-        fill()
-        run(2)
-    dts, dts_sync = [], []
-    for _ in range(5):
-        fill()
-        dts.append(run(2))
-    for _ in range(5):
-        fill()
-        dts_sync.append(run(0))
-    dt, dt_sync = statistics.median(dts), statistics.median(dts_sync)
+    def timed(mode, packed):
+        dts = []
+        for _ in range(5):
+            fill(packed)
+            dts.append(run(mode, packed))
+        return statistics.median(dts), [round(n_ev * nb / x) for x in dts]
+
+    for packed in (False, True):
+        for _ in range(2):   # warm (the handle sizes its ring for the overlap here)
+            fill(packed)
+            run(2, packed)
+    res = {}
+    for packed in (True, False):
+        for mode in (2, 0):
+            res[packed, mode] = timed(mode, packed)
     rc, st = esi.esi_get_stats(h)
-    return {"value": n_ev * nb / dt, "unit": "events/s",
-            "ring": {"capacity_events": int(st.ring_capacity), "grows": int(st.ring_grows),
-                     "push_waits": int(st.push_waits)},
-            "h2d_bytes_per_step": n_ev * 16, "d2h_bytes_per_step": M * sc.W * sc.H,
-            "frames_per_s": M * nb / dt, "steps": nb,
-            "runs_events_per_s": [round(n_ev * nb / x) for x in dts],
-            "mode": "pipelined: push of step k+1 overlaps the render of step k (out_on_device=2); "
-                    "median of 5 runs",
-            "synchronous": {"value": n_ev * nb / dt_sync, "unit": "events/s",
-                            "runs_events_per_s": [round(n_ev * nb / x) for x in dts_sync],
-                            "mode": "each render waits for its frames (out_on_device=0); median of 5 runs"}}
+    pipe = "pipelined: push of step k+1 overlaps the render of step k (out_on_device=2); " \
+           "median of 5 runs"
+    sync = "each render waits for its frames (out_on_device=0); median of 5 runs"
+
+    def variant(packed, mode, text):
+        dt, runs = res[packed, mode]
+        return {"value": n_ev * nb / dt, "unit": "events/s", "runs_events_per_s": runs,
+                "mode": text}
+
+    out = variant(True, 2, pipe)
+    out.update({"input": "8-byte packed events from pinned host memory (esi_push_packed)",
+                "ring": {"capacity_events": int(st.ring_capacity), "grows": int(st.ring_grows),
+                         "push_waits": int(st.push_waits)},
+                "h2d_bytes_per_step": n_ev * 8, "d2h_bytes_per_step": M * sc.W * sc.H,
+                "frames_per_s": M * nb / res[True, 2][0], "steps": nb,
+                "synchronous": variant(True, 0, sync),
+                "events16": dict(variant(False, 2, pipe), h2d_bytes_per_step=n_ev * 16,
+                                 input="16-byte events from pinned host memory (esi_push_events)",
+                                 synchronous=variant(False, 0, sync))})
+    return out
 
 
 def latency_leg(esi):
@@ -1085,7 +1114,8 @@ def summary(line):
     s = {"Gev_s": {HEADLINE: g(line["value"])},
          "tile_frac": {HEADLINE: round(line["roofline"]["frac"], 4) if line.get("roofline") else None},
          "step_frac": {HEADLINE: round(line["step_roofline"]["frac"], 4)},
-         "e2e_Gev_s": g(line["e2e"]["value"]) if (line.get("e2e") or {}).get("value") else None}
+         "e2e_Gev_s": g(line["e2e"]["value"]) if (line.get("e2e") or {}).get("value") else None,
+         "e2e_events16_Gev_s": g(((line.get("e2e") or {}).get("events16") or {}).get("value"))}
 
     def ok(d):
         return isinstance(d, dict) and "error" not in d

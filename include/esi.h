@@ -182,6 +182,37 @@ int esi_create(int width, int height, const esi_params *params,
 int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_device);
 
 /*
+ * Packed events: one little-endian uint64 per event, half the bytes of
+ * esi_event on the host link.  The paper has no counterpart (it gives no
+ * encoding); the events it carries are those of Sec. III-A.
+ *   bits  0..15  x
+ *   bits 16..31  y
+ *   bit  32      polarity: 1 = +1, 0 = -1
+ *   bits 33..63  t_us - t_base_us, 0 .. 2^31 - 1 (about 35 minutes)
+ * ESI_PACK_EVENT builds one word; dt_us must be in that range.
+ */
+#define ESI_PACK_T_SHIFT 33
+#define ESI_PACK_EVENT(x, y, on, dt_us)                                           \
+    ((uint64_t)(uint16_t)(x) | ((uint64_t)(uint16_t)(y) << 16) |                 \
+     ((uint64_t)((on) ? 1 : 0) << 32) | ((uint64_t)(dt_us) << ESI_PACK_T_SHIFT))
+
+/*
+ * esi_push_events for n packed events: event i is
+ * {t_base_us + (pk[i] >> 33), x, y, +1 or -1} as laid out above, and every
+ * rule, error and return point of esi_push_events applies to those events
+ * (host pushes of at most 65,536 events are unpacked and checked on the
+ * host; larger ones and device pushes are unpacked into the device ring and
+ * checked there, chunk by chunk, the copy of the next chunk overlapping).
+ * pk: pk_on_device = 0 host array (page-locked for the fastest copy),
+ * 1 device array (8-byte aligned, read after the work queued on the
+ * handle's stream); the caller keeps ownership and may reuse it once the
+ * call returns.  ESI_EINVAL as esi_push_events, and also for a device pk
+ * that is not 8-byte aligned or t_base_us outside [-2^62, 2^62].
+ */
+int esi_push_packed(esi_handle *h, const uint64_t *pk, size_t n, int64_t t_base_us,
+                    int pk_on_device);
+
+/*
  * Apply every queued event with t <= t_frame_us in push order (Alg. 2
  * loop; a frame at t shows the events t_n <= t, the condition under Eq. 5)
  * and write the Eq. 14 frame, W * H bytes row-major (y * W + x), to out.

@@ -458,21 +458,26 @@ int esi_create(int width, int height, const esi_params *params, void *cuda_strea
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hstatus, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->hwin_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->bin_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) {
-        int least = 0, greatest = 0;
-        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-        if (e == cudaSuccess)
-            e = cudaStreamCreateWithPriority(&h->tile_stream, cudaStreamNonBlocking, greatest);
-    }
+    // block priorities: a push's short check (or unpack) kernels first, so a
+    // push overlapping a render does not wait for the render's queued blocks;
+    // then the tile kernel; the binning of the next sub-batch last
+    int least = 0, greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    const int tile_prio = greatest < least ? greatest + 1 : greatest;
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithPriority(&h->tile_stream, cudaStreamNonBlocking, tile_prio);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_tstart, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_tdone, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithPriority(&h->aux_stream, cudaStreamNonBlocking, greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->in_stream, cudaStreamNonBlocking);
     for (int r = 0; r < esi_handle::kSpans && e == cudaSuccess; ++r)
         e = cudaEventCreateWithFlags(&h->span[r].ev, cudaEventDisableTiming);
     for (int c = 0; c < 4 && e == cudaSuccess; ++c)
         e = cudaEventCreateWithFlags(&h->ev_chunk[c], cudaEventDisableTiming);
+    for (int c = 0; c < 2 && e == cudaSuccess; ++c)
+        e = cudaEventCreateWithFlags(&h->ev_unpk[c], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->dres, sizeof(PushResult));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hres, sizeof(PushResult));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hfetch, 2 * kSparse * sizeof(esi_event));
@@ -546,7 +551,10 @@ void esi_destroy(esi_handle *h)
         if (h->span[r].ev) cudaEventDestroy(h->span[r].ev);
     for (int c = 0; c < 4; ++c)
         if (h->ev_chunk[c]) cudaEventDestroy(h->ev_chunk[c]);
+    for (int c = 0; c < 2; ++c)
+        if (h->ev_unpk[c]) cudaEventDestroy(h->ev_unpk[c]);
     cudaFree(h->dsparse);
+    cudaFree(h->pk_stage);
     cudaFree(h->dres);
     cudaFreeHost(h->hres);
     cudaFreeHost(h->hfetch);
@@ -566,10 +574,13 @@ static constexpr unsigned long long kPushChunk = 1ull << 21;
 // next step's copy overlaps the current render
 static constexpr unsigned long long kOverlapRingMax = 1ull << 28;
 
-int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_device)
+// One push of n >= 1 events: ev (16-byte events) or, when pk is set, packed
+// words with times t_base + offset.  Packed host pushes reach here only above
+// kHostCheckMax events (smaller ones are unpacked on the host first).
+static int push_impl(esi_handle *h, const esi_event *ev, const unsigned long long *pk,
+                     long long t_base, size_t n, int ev_on_device)
 {
-    if (!h || (n && !ev) || (ev_on_device != 0 && ev_on_device != 1)) return ESI_EINVAL;
-    if (n == 0) return ESI_OK;
+    const bool packed = pk != nullptr;
     const unsigned long long pending = h->tail - h->head;
     int rc = ensure_ring(h, pending + n);
     if (rc) return rc;
@@ -643,14 +654,14 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
             i += len;
         }
     };
-    if (!ev_on_device && n <= kHostCheckMax && !h->tmirror) {
+    if (!packed && !ev_on_device && n <= kHostCheckMax && !h->tmirror) {
         e = cudaMallocHost((void **)&h->tmirror, h->cap * sizeof(long long));
         if (e != cudaSuccess) {
             h->tmirror = nullptr;
             return cuda_fail(h, e);
         }
     }
-    if (!ev_on_device && n <= kHostCheckMax) {
+    if (!packed && !ev_on_device && n <= kHostCheckMax) {
         // the copy starts first; the time-order check and the host mirror of
         // the times run meanwhile (a rejected batch leaves ring slots past
         // tail that nothing reads)
@@ -674,18 +685,44 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
         // stream while the next chunks are copied in
         const unsigned long long g0 = (h->tail + kSparse - 1) / kSparse * kSparse;
         rc = ensure_device(h, &h->dsparse, &h->dsparse_cap, (size_t)(n / kSparse + 2));
+        if (!rc && packed && !ev_on_device)
+            rc = ensure_device(h, &h->pk_stage, &h->pk_stage_cap, (size_t)(2 * kPushChunk));
         if (rc) return rc;
         const unsigned long long smask = h->cap / kSparse - 1;
         e = cudaMemsetAsync(h->dres, 0, sizeof(PushResult), cs);
         int j = 0;
         for (unsigned long long c0 = 0; e == cudaSuccess && c0 < n; c0 += kPushChunk, ++j) {
             const unsigned long long c1 = std::min<unsigned long long>(n, c0 + kPushChunk);
-            copy_in(c0, c1);
-            if (e == cudaSuccess) e = cudaEventRecord(h->ev_chunk[j & 3], cs);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux_stream, h->ev_chunk[j & 3], 0);
-            if (e == cudaSuccess)
-                e = launch_push_check(h->ring, mask, h->tail, c0, (long long)(c1 - c0), n, prev, g0,
-                                      h->dsparse, h->dres, h->aux_stream);
+            if (!packed) {
+                copy_in(c0, c1);
+                if (e == cudaSuccess) e = cudaEventRecord(h->ev_chunk[j & 3], cs);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux_stream, h->ev_chunk[j & 3], 0);
+                if (e == cudaSuccess)
+                    e = launch_push_check(h->ring, mask, h->tail, c0, (long long)(c1 - c0), n, prev,
+                                          g0, h->dsparse, h->dres, h->aux_stream);
+            } else {
+                // host words go through staging buffer j & 1 (free once the
+                // unpack of chunk j - 2 is done); device words are read where
+                // they are, after the work queued on the handle's stream
+                const unsigned long long *src = pk + c0;
+                if (!ev_on_device) {
+                    unsigned long long *st = h->pk_stage + (size_t)(j & 1) * kPushChunk;
+                    if (j >= 2) e = cudaStreamWaitEvent(cs, h->ev_unpk[j & 1], 0);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(st, pk + c0, (c1 - c0) * sizeof(unsigned long long),
+                                            cudaMemcpyHostToDevice, cs);
+                    src = st;
+                }
+                if (e == cudaSuccess && (!ev_on_device || j == 0)) {
+                    e = cudaEventRecord(h->ev_chunk[j & 3], cs);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux_stream, h->ev_chunk[j & 3], 0);
+                }
+                if (e == cudaSuccess)
+                    e = launch_push_unpack(src, h->ring, mask, h->tail, c0, (long long)(c1 - c0), n,
+                                           t_base, prev, g0, h->dsparse, h->dres, h->aux_stream);
+                if (e == cudaSuccess && !ev_on_device)
+                    e = cudaEventRecord(h->ev_unpk[j & 1], h->aux_stream);
+            }
             // sparse entries j of this chunk: indices g0 + j kSparse in [tail + c0, tail + c1)
             const unsigned long long ja = (std::max(g0, (h->tail + c0 + kSparse - 1) / kSparse * kSparse) - g0) / kSparse;
             const unsigned long long jb = (std::max(g0, (h->tail + c1 + kSparse - 1) / kSparse * kSparse) - g0) / kSparse;
@@ -711,6 +748,42 @@ int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_devi
     h->tail += n;
     h->pushed += n;
     return ESI_OK;
+}
+
+int esi_push_events(esi_handle *h, const esi_event *ev, size_t n, int ev_on_device)
+{
+    if (!h || (n && !ev) || (ev_on_device != 0 && ev_on_device != 1)) return ESI_EINVAL;
+    if (n == 0) return ESI_OK;
+    return push_impl(h, ev, nullptr, 0, n, ev_on_device);
+}
+
+int esi_push_packed(esi_handle *h, const uint64_t *pk, size_t n, int64_t t_base_us,
+                    int pk_on_device)
+{
+    if (!h || (n && !pk) || (pk_on_device != 0 && pk_on_device != 1)) return ESI_EINVAL;
+    if (t_base_us < -(1LL << 62) || t_base_us > (1LL << 62)) return ESI_EINVAL;
+    if (pk_on_device && (reinterpret_cast<uintptr_t>(pk) & 7u)) return ESI_EINVAL;
+    if (n == 0) return ESI_OK;
+    if (!pk_on_device && n <= kHostCheckMax) {
+        // small host pushes keep the host-checked path: unpack here
+        try {
+            h->pk_host.resize(n);
+        } catch (...) {
+            return ESI_ENOMEM;
+        }
+        for (size_t i = 0; i < n; ++i) {
+            const uint64_t w = pk[i];
+            esi_event &e = h->pk_host[i];
+            e.t_us = (long long)t_base_us + (long long)(w >> kPackTShift);
+            e.x = (uint16_t)(w & 0xffffu);
+            e.y = (uint16_t)((w >> 16) & 0xffffu);
+            e.p = ((w >> 32) & 1u) ? 1 : -1;
+            e._pad[0] = e._pad[1] = e._pad[2] = 0;
+        }
+        return push_impl(h, h->pk_host.data(), nullptr, 0, n, 0);
+    }
+    return push_impl(h, nullptr, reinterpret_cast<const unsigned long long *>(pk),
+                     (long long)t_base_us, n, pk_on_device);
 }
 
 int esi_render_frames(esi_handle *h, const int64_t *t_frames, size_t m, uint8_t *out,

@@ -73,6 +73,12 @@ struct esi_handle {
     cudaEvent_t ev_chunk[4] = {nullptr, nullptr, nullptr, nullptr};
     long long *dsparse = nullptr;        // every kSparse-th time of the push being checked
     size_t dsparse_cap = 0;
+    // packed host pushes: two device staging buffers of a chunk each, the
+    // copy of one overlapping the unpack of the other (ev_unpk: unpack done)
+    unsigned long long *pk_stage = nullptr;
+    size_t pk_stage_cap = 0;
+    cudaEvent_t ev_unpk[2] = {nullptr, nullptr};
+    std::vector<esi_event> pk_host;      // small packed host pushes, unpacked
     esi::PushResult *dres = nullptr;
     esi::PushResult *hres = nullptr;     // pinned
 
@@ -195,6 +201,13 @@ cudaError_t launch_push_check(const esi_event *ring, unsigned long long mask, un
                               unsigned long long first, long long cnt, unsigned long long n,
                               long long prev, unsigned long long g0, long long *sparse,
                               PushResult *res, cudaStream_t s);
+// The same for packed events: src[i] (esi.h's 8-byte layout, time
+// t_base + offset) is written to ring index a0 + first + i and checked.
+cudaError_t launch_push_unpack(const unsigned long long *src, esi_event *ring,
+                               unsigned long long mask, unsigned long long a0,
+                               unsigned long long first, long long cnt, unsigned long long n,
+                               long long t_base, long long prev, unsigned long long g0,
+                               long long *sparse, PushResult *res, cudaStream_t s);
 
 // Launch-shape measurement shared by esi_autotune and esi_stream_autotune:
 // cache lookup, candidate timing on a scratch handle, cache update.

@@ -72,6 +72,9 @@ struct PushResult {
 // planning (device-checked ones keep only those).
 constexpr unsigned kSparse = 32;
 
+// Packed events: time offset in the top 31 bits of the word (esi.h).
+constexpr int kPackTShift = 33;
+
 // Arguments of the binning kernel (one block per chunk of events).
 struct BinArgs {
     const esi_event *ring;        // pending-event ring

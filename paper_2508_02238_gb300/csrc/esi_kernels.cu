@@ -15,6 +15,8 @@
 //                    the due records 32 at a time through Alg. 2, then the
 //                    Eq. 14 codes of the row's pixels at the frame.
 //   esi_push_check_kernel  time-order check of a large push on the device.
+//   esi_push_unpack_kernel the same for packed 8-byte events, which it
+//                          widens into the ring's 16-byte slots.
 //
 // Per-pixel independence (each pixel's state depends only on its own
 // time-ordered events, Eq. 5 and Alg. 2) is what makes the reorder legal.
@@ -506,6 +508,46 @@ cudaError_t launch_push_check(const esi_event *ring, unsigned long long mask, un
     const long long blocks = std::min<long long>((cnt + 255) / 256, 152LL * 8);
     esi_push_check_kernel<<<(unsigned)blocks, 256, 0, s>>>(ring, mask, a0, first, cnt, n, prev, g0,
                                                            sparse, res);
+    return cudaGetLastError();
+}
+
+// The same checks for packed words: word i of src becomes ring slot a0 +
+// first + i (one 16-byte store), its time compared with word i - 1's (the
+// ring slot before it, written by the previous launch, at i = 0).
+__global__ void esi_push_unpack_kernel(const unsigned long long *src, esi_event *ring,
+                                       unsigned long long mask, unsigned long long a0,
+                                       unsigned long long first, long long cnt,
+                                       unsigned long long n, long long t_base, long long prev,
+                                       unsigned long long g0, long long *sparse, PushResult *res)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long k = first + (unsigned long long)i;
+        const unsigned long long g = a0 + k;
+        const unsigned long long w = src[i];
+        const long long t = t_base + (long long)(w >> kPackTShift);
+        // x, y as they are; polarity byte 1 or -1 (0xff); padding 0
+        const unsigned long long xyp =
+            (w & 0xffffffffull) | ((w >> 32) & 1ull ? 0x01ull : 0xffull) << 32;
+        *reinterpret_cast<longlong2 *>(ring + (g & mask)) = make_longlong2(t, (long long)xyp);
+        const long long tp = i ? t_base + (long long)(src[i - 1] >> kPackTShift)
+                               : (k ? ring[(g - 1) & mask].t_us : prev);
+        if (t < tp) res->bad = 1;
+        if (g % kSparse == 0) sparse[(g - g0) / kSparse] = t;
+        if (k == n - 1) res->last = t;
+    }
+}
+
+cudaError_t launch_push_unpack(const unsigned long long *src, esi_event *ring,
+                               unsigned long long mask, unsigned long long a0,
+                               unsigned long long first, long long cnt, unsigned long long n,
+                               long long t_base, long long prev, unsigned long long g0,
+                               long long *sparse, PushResult *res, cudaStream_t s)
+{
+    if (cnt <= 0) return cudaSuccess;
+    const long long blocks = std::min<long long>((cnt + 255) / 256, 152LL * 8);
+    esi_push_unpack_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, ring, mask, a0, first, cnt, n,
+                                                            t_base, prev, g0, sparse, res);
     return cudaGetLastError();
 }
 

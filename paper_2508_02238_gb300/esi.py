@@ -25,6 +25,7 @@ ESI_ESTATE = -8
 
 # esi_params.method
 ESI_METHOD_ALG2, ESI_METHOD_ALG1, ESI_METHOD_EQ3_EXP = 0, 1, 2
+ESI_PACK_T_SHIFT = 33   # packed events: time offset in bits 33..63
 
 
 class esi_params(ctypes.Structure):
@@ -112,6 +113,7 @@ _i32, _i64, _sz = ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
 SIGNATURES = {
     "esi_create": (_i32, [_i32, _i32, ctypes.POINTER(esi_params), _P, ctypes.POINTER(_P)]),
     "esi_push_events": (_i32, [_P, _P, _sz, _i32]),
+    "esi_push_packed": (_i32, [_P, _P, _sz, _i64, _i32]),
     "esi_render_frame": (_i32, [_P, _i64, _P, _i32]),
     "esi_render_frames": (_i32, [_P, _P, _sz, _P, _i32]),
     "esi_get_state": (_i32, [_P, _P, _P, _i32]),
@@ -213,6 +215,11 @@ def esi_create(width: int, height: int, params: esi_params, cuda_stream=0):
 
 def esi_push_events(h, ev, n: int, ev_on_device: int) -> int:
     return _fn("esi_push_events")(h, _P(ptr(ev) or None), int(n), int(ev_on_device))
+
+
+def esi_push_packed(h, pk, n: int, t_base_us: int, pk_on_device: int) -> int:
+    return _fn("esi_push_packed")(h, _P(ptr(pk) or None), int(n), int(t_base_us),
+                                  int(pk_on_device))
 
 
 def esi_render_frame(h, t_frame_us: int, out, out_on_device: int) -> int:

@@ -344,3 +344,18 @@ def mixed_arrivals(ws, duration_s: float = 0.25, seed: int = 1004):
     D = int(round(duration_s * 1e6))
     return [_arrivals(rng, w["t_join_us"], w["t_leave_us"] if w["t_leave_us"] is not None else D)
             for w in ws]
+
+
+def pack_events(ev: np.ndarray, t_base_us: int) -> np.ndarray:
+    """The 8-byte packed form of 16-byte events (the layout of esi.h's
+    ESI_PACK_EVENT): x in bits 0..15, y in 16..31, polarity (p > 0) in bit
+    32, t - t_base_us in bits 33..63.  Every time must lie in
+    [t_base_us, t_base_us + 2^31)."""
+    dt = ev["t"].astype(np.int64) - np.int64(t_base_us)
+    if len(dt) and (dt.min() < 0 or dt.max() >= 2**31):
+        raise ValueError("event times outside [t_base, t_base + 2^31)")
+    w = ev["x"].astype(np.uint64)
+    w |= ev["y"].astype(np.uint64) << np.uint64(16)
+    w |= (ev["p"] > 0).astype(np.uint64) << np.uint64(32)
+    w |= dt.astype(np.uint64) << np.uint64(33)
+    return w

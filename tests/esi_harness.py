@@ -96,6 +96,16 @@ class GpuStream:
             return rc
         return self.esi.esi_push_events(self.h, ev, len(ev), 0)
 
+    def push_packed(self, words, t_base, on_device=False):
+        """esi_push_packed of uint64 words (8-byte packed events)."""
+        w = np.ascontiguousarray(words, dtype=np.uint64)
+        if on_device:
+            dev = self.torch.from_numpy(w.view(np.int64).copy()).cuda()
+            rc = self.esi.esi_push_packed(self.h, dev, len(w), int(t_base), 1)
+            self.torch.cuda.synchronize()
+            return rc
+        return self.esi.esi_push_packed(self.h, w, len(w), int(t_base), 0)
+
     def render_frames(self, t_frames, on_device=False):
         tf = np.ascontiguousarray(t_frames, dtype=np.int64)
         M = len(tf)

@@ -76,6 +76,7 @@ def test_null_handle_calls_are_rejected():
     assert esi.esi_autotune(None, None, 0, None, 0)[0] == esi.ESI_EINVAL
     assert esi.esi_noise_map(None, None, 0) == esi.ESI_EINVAL
     assert esi.esi_count_events(None, None, 0, 0, None, 0) == esi.ESI_EINVAL
+    assert esi.esi_push_packed(None, None, 0, 0, 0) == esi.ESI_EINVAL
     assert esi.esi_event_states(None, None, 0, 0)[0] == esi.ESI_EINVAL
     esi.esi_destroy(None)  # no-op
 
@@ -85,9 +86,35 @@ def test_method_constants_match_the_header():
     import re
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "esi.h")).read()
     for name in ("ESI_METHOD_ALG2", "ESI_METHOD_ALG1", "ESI_METHOD_EQ3_EXP",
-                 "ESI_APPLY_EVERY_TICK", "ESI_APPLY_AT_FRAMES"):
+                 "ESI_APPLY_EVERY_TICK", "ESI_APPLY_AT_FRAMES", "ESI_PACK_T_SHIFT"):
         m = re.search(r"#define\s+%s\s+(\d+)" % name, hdr)
         assert m and int(m.group(1)) == getattr(esi, name), name
+
+
+def test_pack_macro_layout(tmp_path):
+    # the header's packing macro, compiled as plain C, against the bit layout
+    # its comment states (x: bits 0-15, y: 16-31, polarity: 32, dt: 33-63)
+    import os
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        import pytest
+        pytest.skip("no gcc")
+    inc = os.path.join(os.path.dirname(__file__), "..", "include")
+    src = tmp_path / "pack.c"
+    src.write_text('#include <stdio.h>\n#include "esi.h"\nint main(void) {\n'
+                   '  printf("%llu %llu %llu\\n",\n'
+                   '    (unsigned long long)ESI_PACK_EVENT(5, 7, 1, 123),\n'
+                   '    (unsigned long long)ESI_PACK_EVENT(65535, 65535, 0, 2147483647),\n'
+                   '    (unsigned long long)ESI_PACK_EVENT(0, 1, -1, 0));\n  return 0;\n}\n')
+    exe = tmp_path / "pack"
+    subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert got[0] == 5 + 7 * 2**16 + 2**32 + 123 * 2**33
+    assert got[1] == (2**16 - 1) + (2**16 - 1) * 2**16 + (2**31 - 1) * 2**33
+    assert got[2] == 2**16 + 2**32     # any non-zero polarity argument is +1
+    assert got[1] < 2**64
 
 
 def test_server_options_are_checked_before_touching_cuda():

@@ -19,7 +19,7 @@ def test_summary_survives_failed_legs():
             "serving": {"error": "z"}, "serving_mixed": None, "parity": {"error": "w"}}
     s = bench.summary(line)
     assert s["Gev_s"][bench.HEADLINE] == 25.0
-    assert s["e2e_Gev_s"] is None
+    assert s["e2e_Gev_s"] is None and s["e2e_events16_Gev_s"] is None
     assert s["serving"] == {"c3": {"error": "z"}}
     assert s["parity(err,err1e-3C,ulpsC,lsb,off,frames)"] == {}
 

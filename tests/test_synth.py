@@ -88,3 +88,21 @@ def test_mixed_serving_workload_shape():
     again = synth.mixed_serving(duration_s=0.1)
     assert [(w["rate"], w["t_join_us"], w["t_leave_us"]) for w in again] == \
         [(w["rate"], w["t_join_us"], w["t_leave_us"]) for w in ws]
+
+
+def test_pack_events_layout():
+    ev = np.zeros(3, dtype=synth.EVENT_DTYPE)
+    ev["t"] = [100, 101, 100 + 2**31 - 1]
+    ev["x"] = [5, 65535, 0]
+    ev["y"] = [7, 65535, 1]
+    ev["p"] = [1, -1, 0]
+    w = synth.pack_events(ev, 100)
+    assert w.dtype == np.uint64
+    assert int(w[0]) == 5 + 7 * 2**16 + 2**32
+    assert int(w[1]) == 65535 + 65535 * 2**16 + 1 * 2**33
+    assert int(w[2]) == 2**16 + (2**31 - 1) * 2**33
+    import pytest
+    with pytest.raises(ValueError):
+        synth.pack_events(ev, 101)           # a time before the base
+    with pytest.raises(ValueError):
+        synth.pack_events(ev, 99)            # an offset of 2^31

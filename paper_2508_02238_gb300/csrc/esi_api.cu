@@ -325,6 +325,11 @@ static int lower_t(esi_handle *h, unsigned long long a, long long *t)
 static int upper_bound_t(esi_handle *h, unsigned long long lo, unsigned long long hi, long long v,
                          unsigned long long *res)
 {
+    // no pending time exceeds the last pushed one: nothing to read back
+    if (h->last_event_t <= v) {
+        *res = hi;
+        return ESI_OK;
+    }
     unsigned long long blo = lo, bhi = hi;
     const unsigned long long G0 = (lo + kSparse - 1) / kSparse * kSparse;
     if (G0 < hi) {

@@ -452,9 +452,12 @@ def e2e_leg(esi, torch, r, steps):
     Inputs: 8-byte packed events (esi_push_packed, the reported value) and
     16-byte events (esi_push_events, beside it), three pinned buffers of
     each.  A step's 16-byte buffer is refilled (times shifted) between the
-    timed runs, outside the timed region; a packed buffer needs no refill
-    (the shift moves only the push's time base).  Each variant is timed in
-    five runs of three steps after two warm-up runs; the median run is
+    timed runs, outside the timed region, so a 16-byte run is three steps.
+    A packed buffer needs no refill (the shift moves only the push's time
+    base) and is free again once its push returns, so a packed run is
+    max(3, min(steps, 30)) steps over the three buffers in turn.  Each run ends with
+    one esi_synchronize, so it includes the drain of its last render.  Each
+    variant is timed in five runs after two warm-up runs; the median run is
     reported (the host link of a shared box varies from run to run), all
     five beside it."""
     import synth
@@ -472,6 +475,8 @@ def e2e_leg(esi, torch, r, steps):
     del words
     host_out = [torch.empty((M, sc.H, sc.W), dtype=torch.uint8, pin_memory=True) for _ in range(2)]
     k = [k0]
+    # steps per run, by input kind (packed runs capped to keep the leg short)
+    per_run = {True: max(nb, min(int(steps), 30)), False: nb}
 
     def fill(packed):
         if packed:
@@ -481,10 +486,11 @@ def e2e_leg(esi, torch, r, steps):
             views[i]["t"] += (k[0] + i) * span
 
     def run(mode, packed):
+        ns = per_run[packed]
         ts = time.perf_counter()
-        for i in range(nb):
+        for i in range(ns):
             if packed:
-                esi.check(esi.esi_push_packed(h, host_pk[i], n_ev, t0 + (k[0] + i) * span, 0),
+                esi.check(esi.esi_push_packed(h, host_pk[i % nb], n_ev, t0 + (k[0] + i) * span, 0),
                           "push")
             else:
                 esi.check(esi.esi_push_events(h, host_in[i], n_ev, 0), "push")
@@ -492,7 +498,7 @@ def e2e_leg(esi, torch, r, steps):
                                             host_out[i % 2], mode), "render")
         esi.check(esi.esi_synchronize(h), "sync")
         dt = time.perf_counter() - ts
-        k[0] += nb
+        k[0] += ns
         return dt
 
     def timed(mode, packed):
@@ -500,7 +506,7 @@ def e2e_leg(esi, torch, r, steps):
         for _ in range(5):
             fill(packed)
             dts.append(run(mode, packed))
-        return statistics.median(dts), [round(n_ev * nb / x) for x in dts]
+        return statistics.median(dts), [round(n_ev * per_run[packed] / x) for x in dts]
 
     for packed in (False, True):
         for _ in range(2):   # warm (the handle sizes its ring for the overlap here)
@@ -517,15 +523,15 @@ def e2e_leg(esi, torch, r, steps):
 
     def variant(packed, mode, text):
         dt, runs = res[packed, mode]
-        return {"value": n_ev * nb / dt, "unit": "events/s", "runs_events_per_s": runs,
-                "mode": text}
+        return {"value": n_ev * per_run[packed] / dt, "unit": "events/s",
+                "runs_events_per_s": runs, "steps_per_run": per_run[packed], "mode": text}
 
     out = variant(True, 2, pipe)
     out.update({"input": "8-byte packed events from pinned host memory (esi_push_packed)",
                 "ring": {"capacity_events": int(st.ring_capacity), "grows": int(st.ring_grows),
                          "push_waits": int(st.push_waits)},
                 "h2d_bytes_per_step": n_ev * 8, "d2h_bytes_per_step": M * sc.W * sc.H,
-                "frames_per_s": M * nb / res[True, 2][0], "steps": nb,
+                "frames_per_s": M * per_run[True] / res[True, 2][0], "steps": per_run[True],
                 "synchronous": variant(True, 0, sync),
                 "events16": dict(variant(False, 2, pipe), h2d_bytes_per_step=n_ev * 16,
                                  input="16-byte events from pinned host memory (esi_push_events)",

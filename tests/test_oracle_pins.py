@@ -381,6 +381,58 @@ def test_bruteforce_clamped_affine_fold(b, bounds):
     assert checked == 9  # 1 + 1 + 2 + 5 bracketings for pixel sequences of 1..4 events
 
 
+# --------------------------------------------- brute force on a 4x4 sensor
+@pytest.mark.parametrize("bounds", [(-BIG, BIG), (-0.3, 0.45)])
+def test_bruteforce_every_event_pair_on_a_4x4_sensor(bounds):
+    # every ordered pair of events on its own 4x4 sensor: first event at any
+    # pixel, either polarity, at t = 0 or 30 us; second at any pixel, either
+    # polarity, 0, 40 or 600 us later (k = 2e3 /s: 600 us is past the decay's
+    # cutoff of 500 us).  Each pixel's S and T against its own events composed
+    # as clamped-affine maps, and the decay-view frame at the last event's
+    # time against Eq. 14 applied to that, for every one of the 16 positions
+    # (x, y swapped or an index off by one fails here).
+    k, b, C = 2e3, 2.0, 0.35
+    L, Hb = bounds
+    p = OracleParams(C=C, k_per_s=k, b=b, s_min=L, s_max=Hb)
+    firsts = list(itertools.product(range(16), (1, -1), (0, 30)))
+    seconds = list(itertools.product(range(16), (1, -1), (0, 40, 600)))
+    cases = [(f,) for f in firsts] + [(f, s) for f in firsts for s in seconds]
+    for case in cases:
+        rows, t = [], 0
+        for j, ev in enumerate(case):
+            q, pol, dt = ev
+            t = dt if j == 0 else t + dt
+            rows.append((t, q % 4, q // 4, pol))
+        st = OracleState(4, 4, p)
+        st.integrate(make_events(rows))
+        t_f = rows[-1][0]
+        frame = st.render(t_f, render_decay=1).ravel()
+        for q in range(16):
+            mine = [(t, pol) for (t, x, y, pol) in rows if y * 4 + x == q]
+            if not mine:
+                assert st.S[q] == 0.0 and st.T[q] == 0
+                expect_s, expect_t = 0.0, 0
+            else:
+                ts = np.array([0] + [e[0] for e in mine], dtype=np.int64)
+                a = d_np(np.diff(ts), k, b)
+                maps = [(a[i], a[i] * mine[i][1] * C, L, Hb) for i in range(len(mine))]
+                m = maps[0]
+                for g in maps[1:]:
+                    m = compose(g, m)
+                expect_s = float(np.clip(m[0] * 0.0 + m[1], m[2], m[3]))
+                expect_t = mine[-1][0]
+                assert st.S[q] == pytest.approx(expect_s, rel=1e-12, abs=1e-15), (case, q)
+                assert st.T[q] == expect_t, (case, q)
+            if Hb < BIG:
+                view = expect_s * float(d_np(t_f - expect_t, k, b))
+                u = 255.0 * (view - L) / (Hb - L)
+                if abs(u - np.floor(u) - 0.5) > 1e-9:     # away from a rounding tie
+                    assert frame[q] == np.clip(np.rint(u), 0, 255), (case, q)
+                else:
+                    assert abs(int(frame[q]) - float(u)) <= 0.5 + 1e-9, (case, q)
+    assert len(cases) == 64 + 64 * 96
+
+
 # ------------------------------------------- Alg. 1 and Eq. 3 as methods
 def eq3_direct(ev_pix, t, k, C):
     """Eq. 3 with d(t) = exp(-k t), summed term by term at time t (events t_i <= t)."""
